@@ -1,0 +1,160 @@
+"""Closed-form and brute-force pins of the full oracle solve (paper Sec. 3-6).
+
+Each case integrates the oracle through several RK3 steps and compares with
+a solution known independently of the scheme: exact translation and rotation
+of the level-set equation, the Hopf-Lax solution of an expanding sphere, the
+swept-disk solution of the Dubins car without controls, the double-integrator
+reachable set by brute force over bang-bang controls, and the mirror symmetry
+of the air3D game.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2507_11542_gb300 import workloads as W
+
+
+def _advect_1d(N, brt):
+    g = W.GridSpec((N,), (0.0,), (1.0,), (0,))
+    x = g.axis(0)
+    V0 = np.sin(2 * np.pi * x) + 0.3 * np.cos(4 * np.pi * x)
+    c, tau = 1.0, 0.37
+    m = O.method(scheme=O.WENO5, dynamics=O.DYN_ADVECT, params=(c,), brt=brt)
+    S, _, _ = O.solve(g, m, V0, [tau])
+    f = lambda y: np.sin(2 * np.pi * y) + 0.3 * np.cos(4 * np.pi * y)
+    if brt == O.BRT_NONE:
+        exact = f(x - c * tau)
+    else:
+        s = np.linspace(0.0, tau, 4001)
+        exact = np.min(f(x[:, None] - c * s[None, :]), axis=1)
+    return S[0], exact
+
+
+def test_translation_is_exact_in_the_limit():
+    errs = []
+    for N in (32, 64, 128):
+        V, exact = _advect_1d(N, O.BRT_NONE)
+        errs.append(np.max(np.abs(V - exact)))
+    assert errs[-1] < 5e-5
+    assert math.log2(errs[0] / errs[1]) > 2.5 and math.log2(errs[1] / errs[2]) > 2.5, errs
+
+
+def test_translation_with_brt_is_the_running_minimum():
+    errs = []
+    for N in (64, 128, 256):
+        V, exact = _advect_1d(N, O.BRT_MIN0)
+        errs.append(np.max(np.abs(V - exact)))
+    assert errs[-1] < 2e-3 and errs[2] < errs[1] < errs[0], errs
+
+
+def test_rotation_full_turn_returns_the_initial_surface():
+    errs = []
+    for N in (41, 81):
+        g = W.GridSpec((N, N), (-1.0, -1.0), (1.0, 1.0))
+        V0 = W.sphere(g, (0.4, 0.0), 0.3)
+        m = O.method(scheme=O.WENO5, dynamics=O.DYN_ROTATE, params=(1.0,), brt=O.BRT_NONE)
+        S, _, t = O.solve(g, m, V0, [2 * math.pi])
+        band = np.abs(V0) < 0.1
+        errs.append(np.max(np.abs(S[0] - V0)[band]))
+        # a quarter turn moves the disk to (0, 0.4)
+        Sq, _, _ = O.solve(g, m, V0, [math.pi / 2])
+        Vq = W.sphere(g, (0.0, 0.4), 0.3)
+        band_q = np.abs(Vq) < 0.1
+        assert np.max(np.abs(Sq[0] - Vq)[band_q]) < 2 * (2.0 / (N - 1))
+    assert errs[1] < errs[0] and errs[1] < 0.25 * (2.0 / 80), errs
+
+
+@pytest.mark.parametrize("D,N", [(2, 41), (2, 81), (3, 33)])
+def test_expanding_sphere_hopf_lax(D, N):
+    # v_t + |grad v| = 0 with V0 = |x| - r0 has V = max(|x| - tau, 0) - r0
+    r0, tau = 0.25, 0.5
+    g = W.GridSpec((N,) * D, (-1.0,) * D, (1.0,) * D)
+    V0 = W.sphere(g, (0.0,) * D, r0)
+    m = O.method(scheme=O.WENO5, dynamics=O.DYN_NORM, params=(1.0,), brt=O.BRT_NONE)
+    S, _, _ = O.solve(g, m, V0, [tau])
+    R = np.sqrt(sum(X ** 2 for X in g.mesh()))
+    exact = np.maximum(R - tau, 0.0) - r0
+    dx = 2.0 / (N - 1)
+    # around the zero set at radius r0 + tau, away from the kink at radius tau
+    band = (np.abs(exact) < 3 * dx) & (R > tau + 4 * dx)
+    assert np.max(np.abs(S[0] - exact)[band]) < 0.1 * dx
+    outer = (R > tau + 3 * dx) & (R < 1.0 - 4 * dx)   # |grad V| = 1 away from the center
+    assert np.max(np.abs(S[0] - exact)[outer]) < 0.2 * dx
+
+
+def _segment_distance(px, py, ux, uy, cx, cy, tau):
+    # distance from (cx, cy) to the segment {p + s u : s in [0, tau]}
+    dx_, dy_ = cx - px, cy - py
+    uu = ux * ux + uy * uy
+    s = np.where(uu > 0, (dx_ * ux + dy_ * uy) / np.where(uu > 0, uu, 1.0), 0.0)
+    s = np.clip(s, 0.0, tau)
+    return np.hypot(px + s * ux - cx, py + s * uy - cy)
+
+
+def test_dubins_without_controls_sweeps_the_disk():
+    # wmax = accmax = 0: V(x, tau) = min_{s in [0, tau]} V0(x + s v (cos th, sin th))
+    g = W.GridSpec((41, 41, 8, 3), (-5.0, -5.0, 0.0, 0.0), (5.0, 5.0, 2 * math.pi, 2.0), (2,))
+    cx, cy, r, tau = 0.5, -0.3, 1.0, 1.0
+    V0 = W.sphere(g, (cx, cy), r, dims=(0, 1))
+    m = O.method(scheme=O.WENO5, dynamics=O.DYN_DUBINS4D, params=(0.0, 0.0), brt=O.BRT_MIN0)
+    S, steps, _ = O.solve(g, m, V0, [tau])
+    X, Y, TH, VV = g.mesh()
+    exact = _segment_distance(X, Y, VV * np.cos(TH), VV * np.sin(TH), cx, cy, tau) - r
+    dx = 10.0 / 40
+    band = np.abs(exact) < 2 * dx
+    assert np.max(np.abs(S[0] - exact)[band]) < 0.3 * dx
+    # v = 0 slices do not move at all
+    np.testing.assert_allclose(S[0][..., 0], V0[..., 0], atol=1e-13)
+
+
+def _di_reachable(x1, x2, tau, r):
+    """Min distance to the origin over bang-bang controls with at most one switch."""
+    t = np.linspace(0.0, tau, 201)
+    best = np.full(x1.shape, np.inf)
+    for sigma in (1.0, -1.0):
+        for ts in np.linspace(0.0, tau, 101):
+            # u = sigma on [0, ts), -sigma afterwards
+            a = np.minimum(t, ts)
+            b = np.maximum(t - ts, 0.0)
+            v_s = x2[:, None] + sigma * ts
+            p1 = x1[:, None] + x2[:, None] * a[None] + 0.5 * sigma * a[None] ** 2
+            p2 = x2[:, None] + sigma * a[None]
+            q1 = np.where(t[None] > ts, p1 + v_s * b[None] - 0.5 * sigma * b[None] ** 2, p1)
+            q2 = np.where(t[None] > ts, p2 - sigma * b[None], p2)
+            best = np.minimum(best, np.min(np.hypot(q1, q2), axis=1))
+    return best
+
+
+def test_double_integrator_matches_bang_bang_reachability():
+    g, V0 = W.double_integrator(61)
+    m = O.method(scheme=O.WENO5, dynamics=O.DYN_DOUBLE_INTEGRATOR, params=(1.0,), brt=O.BRT_MIN0)
+    tau, r = 1.0, 0.5
+    S, _, _ = O.solve(g, m, V0, [tau])
+    V = S[0].ravel(order="F")
+    X1, X2 = [a.ravel(order="F") for a in g.mesh()]
+    dmin = _di_reachable(X1, X2, tau, r)
+    margin = 0.08
+    inside = V < -margin
+    outside = V > margin
+    assert inside.sum() > 200 and outside.sum() > 200
+    assert np.all(dmin[inside] <= r + 0.02)
+    assert np.all(dmin[outside] >= r - 0.02)
+    # the set grew: V is monotone non-increasing in tau
+    assert np.all(S[0] <= V0 + 1e-14)
+
+
+def test_air3d_mirror_symmetry_and_monotone_brt():
+    g, V0 = W.air3d(25)
+    m = O.method(scheme=O.WENO5, dynamics=O.DYN_AIR3D, params=(5.0, 5.0, 1.0, 1.0), brt=O.BRT_MIN0)
+    ts = [0.0, 0.15, 0.3]
+    S, steps, _ = O.solve(g, m, V0, ts)
+    assert steps > 5
+    V = S[-1]
+    n = g.n[2]
+    mirror = V[:, ::-1, :][:, :, (-np.arange(n)) % n]     # (x, -y, -psi)
+    scale = np.max(np.abs(V))
+    assert np.max(np.abs(V - mirror)) < 1e-11 * scale
+    assert np.all(S[1] <= S[0] + 1e-13 * scale) and np.all(S[2] <= S[1] + 1e-13 * scale)
+    assert np.min(S[2] - S[0]) < -0.1     # the tube actually grew

@@ -1,0 +1,248 @@
+"""Pins of the oracle's Hamiltonians, Lax-Friedrichs term, CFL bound, TVD-RK3
+step and time loop (paper Sec. 4, 5 and 6.1).
+
+The Hamiltonians are checked against brute-force optimisation over a grid of
+controls of the dynamics as stated in the workload table; the scheme pieces
+against textbook special cases (LF with alpha = |c| is the upwind scheme;
+Shu-Osher RK3 of a linear operator is its third-order Taylor polynomial) and
+against hand-derived step counts.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+
+U = np.linspace(-1.0, 1.0, 41)  # controls, endpoints included
+
+
+def _brute_hg(dyn, params, x, p):
+    if dyn == O.DYN_DOUBLE_INTEGRATOR:
+        (umax,) = params
+        return min(p[0] * x[1] + p[1] * (umax * u) for u in U)
+    if dyn == O.DYN_AIR3D:
+        va, vb, amax, bmax = params
+        X, Y, psi = x
+        best = -np.inf
+        for a in amax * U:          # evader maximises
+            worst = np.inf
+            for b in bmax * U:      # pursuer minimises
+                f = (-va + vb * math.cos(psi) + a * Y, vb * math.sin(psi) - a * X, b - a)
+                worst = min(worst, float(np.dot(p, f)))
+            best = max(best, worst)
+        return best
+    if dyn == O.DYN_DUBINS4D:
+        wmax, accmax = params
+        X, Y, th, v = x
+        return min(float(np.dot(p, (v * math.cos(th), v * math.sin(th), w, acc)))
+                   for w in wmax * U for acc in accmax * U)
+    raise AssertionError
+
+
+def _brute_alpha(dyn, params, x):
+    if dyn == O.DYN_DOUBLE_INTEGRATOR:
+        (umax,) = params
+        return [abs(x[1]), max(abs(umax * u) for u in U)]
+    if dyn == O.DYN_AIR3D:
+        va, vb, amax, bmax = params
+        X, Y, psi = x
+        fs = [(-va + vb * math.cos(psi) + a * Y, vb * math.sin(psi) - a * X, b - a)
+              for a in amax * U for b in bmax * U]
+        return list(np.max(np.abs(np.array(fs)), axis=0))
+    if dyn == O.DYN_DUBINS4D:
+        wmax, accmax = params
+        X, Y, th, v = x
+        fs = [(v * math.cos(th), v * math.sin(th), w, acc) for w in wmax * U for acc in accmax * U]
+        return list(np.max(np.abs(np.array(fs)), axis=0))
+    raise AssertionError
+
+
+CASES = [
+    (O.DYN_DOUBLE_INTEGRATOR, (1.0,), 2),
+    (O.DYN_AIR3D, (5.0, 5.0, 1.0, 1.0), 3),
+    (O.DYN_AIR3D, (3.0, 4.0, 0.7, 1.3), 3),
+    (O.DYN_DUBINS4D, (1.0, 0.5), 4),
+]
+
+
+@pytest.mark.parametrize("dyn,params,D", CASES)
+def test_hamiltonian_is_the_control_optimum(dyn, params, D):
+    rng = np.random.default_rng(11)
+    m = O.method(dynamics=dyn, params=params)
+    for _ in range(25):
+        x = rng.uniform(-4, 4, size=D)
+        p = rng.normal(size=D)
+        assert O.hamiltonian(m, x, p) == pytest.approx(_brute_hg(dyn, params, x, p), abs=1e-12)
+
+
+@pytest.mark.parametrize("dyn,params,D", CASES)
+def test_alpha_is_the_max_speed(dyn, params, D):
+    rng = np.random.default_rng(12)
+    m = O.method(dynamics=dyn, params=params)
+    for _ in range(25):
+        x = rng.uniform(-4, 4, size=D)
+        np.testing.assert_allclose(O.alpha(m, x), _brute_alpha(dyn, params, x), atol=1e-12)
+        # alpha bounds every partial derivative of Hg in p (LF stability)
+        p = rng.normal(size=D)
+        h = 1e-6
+        for d in range(D):
+            e = np.zeros(D)
+            e[d] = h
+            slope = (O.hamiltonian(m, x, p + e) - O.hamiltonian(m, x, p - e)) / (2 * h)
+            assert abs(slope) <= O.alpha(m, x)[d] + 1e-6
+
+
+def test_level_set_hamiltonians():
+    # -c|p| (normal motion), -c.p (advection), rotation field omega(-y, x)
+    m = O.method(dynamics=O.DYN_NORM, params=(2.0,))
+    assert O.hamiltonian(m, [0.3, 0.1], [3.0, 4.0]) == pytest.approx(-10.0)
+    np.testing.assert_allclose(O.alpha(m, [0.3, 0.1]), [2.0, 2.0])
+    assert O.hamiltonian(m, [0.0, 0.0], [0.0, 0.0]) == 0.0
+    m = O.method(dynamics=O.DYN_ADVECT, params=(1.5, -2.0))
+    assert O.hamiltonian(m, [9.0, 9.0], [1.0, 1.0]) == pytest.approx(0.5)
+    m = O.method(dynamics=O.DYN_ROTATE, params=(2.0,))
+    # F(x=1, y=0) = (0, 2): Hg = -p.F
+    assert O.hamiltonian(m, [1.0, 0.0], [0.0, 1.0]) == pytest.approx(-2.0)
+    np.testing.assert_allclose(O.alpha(m, [1.0, -3.0]), [6.0, 2.0])
+
+
+class Line:
+    def __init__(self, n, lo=0.0, hi=1.0, periodic=True):
+        self.n = (n,)
+        self.lo = (lo,)
+        self.hi = (hi,)
+        self.periodic = (0,) if periodic else ()
+
+
+@pytest.mark.parametrize("c", [1.3, -0.7])
+def test_lax_friedrichs_with_alpha_c_is_upwind(c):
+    # Hg = -c p, alpha = |c|: Hg(pbar) + |c|(p+ - p-)/2 = -c p- (c > 0) or -c p+ (c < 0)
+    g = Line(40)
+    rng = np.random.default_rng(2)
+    V = rng.normal(size=40)
+    dx = 1.0 / 40
+    m = O.method(scheme=O.ENO1, dynamics=O.DYN_ADVECT, params=(c,), brt=O.BRT_NONE)
+    back = (V - np.roll(V, 1)) / dx
+    fwd = (np.roll(V, -1) - V) / dx
+    expect = -c * back if c > 0 else -c * fwd
+    np.testing.assert_allclose(O.term(g, m, V), expect, rtol=1e-13, atol=1e-12)
+
+
+def test_term_on_linear_data_equals_hamiltonian():
+    # p- = p+ = grad V for linear V, so the dissipation vanishes and
+    # ydot = Hg(x, grad V); with the BRT clamp, min(0, Hg)
+    class G:
+        n = (9, 11)
+        lo = (-1.0, -1.0)
+        hi = (1.0, 1.0)
+        periodic = ()
+    X, Y = np.meshgrid(np.linspace(-1, 1, 9), np.linspace(-1, 1, 11), indexing="ij")
+    a, b = 0.7, -1.9
+    V = np.asfortranarray(a * X + b * Y + 5.0)   # positive and interior-exact
+    for brt in (O.BRT_NONE, O.BRT_MIN0):
+        m = O.method(scheme=O.WENO5, dynamics=O.DYN_DOUBLE_INTEGRATOR, params=(1.0,), brt=brt)
+        yd = O.term(G, m, V)
+        expect = a * Y - abs(b)
+        if brt == O.BRT_MIN0:
+            expect = np.minimum(0.0, expect)
+        inner = (slice(3, -3), slice(3, -3))
+        np.testing.assert_allclose(yd[inner], expect[inner], atol=1e-12)
+
+
+def test_brt_min0_is_the_clamped_term():
+    class G:
+        n = (13, 12, 10)
+        lo = (-6.0, -10.0, 0.0)
+        hi = (20.0, 10.0, 2 * math.pi)
+        periodic = (2,)
+    rng = np.random.default_rng(8)
+    V = np.asfortranarray(rng.normal(size=G.n))
+    free = O.term(G, O.method(dynamics=O.DYN_AIR3D, params=(5, 5, 1, 1), brt=O.BRT_NONE), V)
+    clamped = O.term(G, O.method(dynamics=O.DYN_AIR3D, params=(5, 5, 1, 1), brt=O.BRT_MIN0), V)
+    np.testing.assert_array_equal(clamped, np.minimum(free, 0.0))
+    assert (free > 0).any() and (free < 0).any()
+
+
+def test_rk3_of_linear_operator_is_taylor_polynomial():
+    # Shu-Osher RK3 applied to V' = L V (L linear) equals
+    # (I + dt L + dt^2 L^2 / 2 + dt^3 L^3 / 6) V exactly.
+    n, c, dt = 24, 0.9, 0.013
+    g = Line(n)
+    dx = 1.0 / n
+    L = -c * (np.eye(n) - np.roll(np.eye(n), -1, axis=1)) / dx  # first-order upwind, periodic
+    rng = np.random.default_rng(4)
+    V = rng.normal(size=n)
+    m = O.method(scheme=O.ENO1, dynamics=O.DYN_ADVECT, params=(c,), brt=O.BRT_NONE)
+    np.testing.assert_allclose(O.term(g, m, V), L @ V, rtol=1e-12, atol=1e-12)
+    A = dt * L
+    taylor = V + A @ V + A @ (A @ V) / 2 + A @ (A @ (A @ V)) / 6
+    np.testing.assert_allclose(O.rk3_step(g, m, V, dt), taylor, rtol=1e-12, atol=1e-12)
+
+
+def test_brt_minv_keeps_the_pointwise_minimum():
+    g = Line(30)
+    rng = np.random.default_rng(6)
+    V = rng.normal(size=30)
+    free = O.rk3_step(g, O.method(scheme=O.WENO5, dynamics=O.DYN_ADVECT, params=(0.5,), brt=O.BRT_NONE), V, 0.01)
+    minv = O.rk3_step(g, O.method(scheme=O.WENO5, dynamics=O.DYN_ADVECT, params=(0.5,), brt=O.BRT_MINV), V, 0.01)
+    np.testing.assert_array_equal(minv, np.minimum(free, V))
+
+
+def test_step_bound_closed_forms():
+    class DI:
+        n = (101, 101)
+        lo = (-1.0, -1.0)
+        hi = (1.0, 1.0)
+        periodic = ()
+    # max_x |x1|/dx0 + umax/dx1 = 1/0.02 + 1/0.02
+    sbi = O.step_bound_inv(DI, O.method(dynamics=O.DYN_DOUBLE_INTEGRATOR, params=(1.0,)))
+    assert sbi == pytest.approx(100.0, rel=1e-14)
+    g = Line(50)
+    sbi = O.step_bound_inv(g, O.method(dynamics=O.DYN_ADVECT, params=(-2.0,)))
+    assert sbi == pytest.approx(2.0 * 50, rel=1e-14)
+
+
+def test_time_loop_lands_on_slices():
+    # advection with |c| = 2 on 50 periodic cells: stepBoundInv = 100, so
+    # dt = 0.8/100 = 0.008 and a slice of length T takes ceil(T/0.008) steps
+    g = Line(50)
+    m = O.method(scheme=O.WENO5, dynamics=O.DYN_ADVECT, params=(2.0,), brt=O.BRT_NONE, cfl=0.8)
+    V0 = np.sin(2 * np.pi * np.arange(50) / 50)
+    ts = [0.0, 0.02, 0.05, 0.05, 0.1]
+    slices, steps, reached = O.solve(g, m, V0, ts)
+    np.testing.assert_array_equal(slices[0], V0)          # tau = 0: no step
+    np.testing.assert_array_equal(slices[2], slices[3])   # repeated slice time: no step
+    # 0 -> 0.02: 3 steps (0.008, 0.008, 0.004); 0.02 -> 0.05: 4 steps; 0.05 -> 0.1: 7 steps
+    assert steps == 3 + 4 + 7
+    np.testing.assert_allclose(reached, ts, rtol=0, atol=1e-15)
+    # max_step caps dt
+    _, steps2, _ = O.solve(g, O.method(scheme=O.WENO5, dynamics=O.DYN_ADVECT, params=(2.0,),
+                                       brt=O.BRT_NONE, max_step=0.005), V0, [0.1])
+    assert steps2 == 20
+
+
+def test_solve_equals_repeated_steps():
+    g = Line(32)
+    m = O.method(scheme=O.WENO5, dynamics=O.DYN_ADVECT, params=(1.0,), brt=O.BRT_MIN0)
+    V0 = np.cos(2 * np.pi * np.arange(32) / 32)
+    slices, steps, _ = O.solve(g, m, V0, [0.1])
+    V = V0.copy()
+    dt_full = 0.8 / 32.0
+    t = 0.0
+    for k in range(steps):
+        dt = min(0.1 - t, dt_full)
+        V = O.rk3_step(g, m, V, dt)
+        t += dt
+    np.testing.assert_array_equal(slices[0], V)
+
+
+def test_invalid_arguments_are_rejected():
+    g = Line(10)
+    m = O.method(dynamics=O.DYN_AIR3D, params=(5, 5, 1, 1))
+    with pytest.raises(ValueError):
+        O.term(g, m, np.zeros(10))          # air3D needs 3 dims
+    with pytest.raises(ValueError):
+        O.solve(g, O.method(dynamics=O.DYN_ADVECT, params=(1.0,)), np.zeros(10), [0.2, 0.1])
+    with pytest.raises(ValueError):
+        O.upwind_line(np.zeros(10), 0.1, scheme=4)
