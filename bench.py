@@ -1,0 +1,350 @@
+#!/usr/bin/env python
+"""Benchmark of the fused TVD-RK3 level-set step (LevelSetPy, arXiv 2507.11542) on GB300.
+
+Workload: the air3D pursuit-evasion game on a 101^3 grid over
+[-6,20]x[-10,10]x[0,2pi) (psi periodic), va = vb = 5, |a|,|b| <= 1,
+V0 = sqrt(x^2+y^2) - 5, WENO5 + Lax-Friedrichs + TVD-RK3, CFL 0.8, BRT
+min(0, H). One step = one full RK3 step (three fused stage kernels) over the
+whole grid; the metric is cell-updates/s (one node advanced one RK3 step).
+
+  value  : FP32 device-resident throughput, L2 flushed between timed steps
+  fp64   : the same in FP64
+  e2e    : hj_solve through the C ABI with pinned host buffers: V0 uploaded,
+           the first time slice (tau = 0.28) integrated, V downloaded, per step
+  cpu_baseline / --impl reference : the FP64 CPU oracle on the host cores
+
+Run: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+(N > 1 under torch.distributed.run: independent replicas, one per GPU.)
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_CELLS = 101 ** 3
+HORIZON = 2.8
+E2E_TAU = 0.28
+# Algorithmic work of one fused stage launch per node (air3D, WENO5), derived
+# operation by operation in the design notes: FP ops (an FMA counts 2) and
+# HBM words (stage 1 reads V and writes V1: 2 words; stages 2 and 3 read the
+# stage input and V^n and write one array: 3 words).
+FLOPS_PER_NODE_STAGE = 475
+WORDS_PER_NODE_STEP = 8
+# GB300 unit counts: 152 SMs, 128 FP32 lanes and 2 FP64 lanes per SM, FMA = 2 flops, max SM clock 2070 MHz
+SM_COUNT, SM_MAX_MHZ = 152, 2070.0
+FP32_PEAK_TFLOPS = SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
+FP64_PEAK_TFLOPS = SM_COUNT * 2 * 2 * SM_MAX_MHZ * 1e6 / 1e12
+L2_FLUSH_BYTES = 256 << 20
+
+
+def measured_hbm_gbs():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if parts[5 + k].lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def workload():
+    from paper_2507_11542_gb300 import workloads as W
+    spec, V0 = W.air3d(101)
+    return spec, V0
+
+
+def run_steps(ctx, spec, m, V, bufs, dt, K, flush, events):
+    """K RK3 steps (three hj_rk3_stage calls each) with an L2 flush before every
+    step. Returns per-step and per-stage-launch durations in ms."""
+    import ctypes
+    import torch
+    from paper_2507_11542_gb300 import _lib
+    u1, u2 = bufs
+    lib = _lib.load()
+    g = ctypes.byref(_lib.make_grid(spec))
+    mm = ctypes.byref(m)
+    code = _lib.dtype_code(V.dtype)
+    h, pv, p1, p2 = ctypes.c_void_p(ctx.handle), ctypes.c_void_p(V.data_ptr()), ctypes.c_void_p(u1.data_ptr()), \
+        ctypes.c_void_p(u2.data_ptr())
+    calls = [(1, pv, None, p1), (2, p1, pv, p2), (3, p2, pv, pv)]
+    step_ms, stage_ms = [], []
+    for k in range(K):
+        if flush is not None:
+            flush.zero_()
+        ev = events[k] if events is not None else None
+        if ev:
+            ev[0].record()
+        for s, (stage, u, vn, out) in enumerate(calls):
+            st = lib.hj_rk3_stage(h, g, mm, code, stage, u, vn, out, dt)
+            if st != 0:
+                raise _lib.HJError(st, _lib.hj_ctx_last_error(ctx.handle))
+            if ev:
+                ev[s + 1].record()
+    torch.cuda.synchronize()
+    if events is not None:
+        for k in range(K):
+            ev = events[k]
+            step_ms.append(ev[0].elapsed_time(ev[3]))
+            stage_ms.extend([ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3])])
+    return step_ms, stage_ms
+
+
+def bench_dtype(ctx, spec, V0, dtype, K, W_, world, flush):
+    import torch
+    from paper_2507_11542_gb300 import solver
+    m = solver.method(dynamics=2, params=(5.0, 5.0, 1.0, 1.0), brt=1)
+    sbi = solver.step_bound(ctx, spec, m)
+    dt = 0.8 / sbi
+    tdt = getattr(torch, dtype)
+    V = torch.from_numpy(np.ascontiguousarray(V0.ravel(order="F"))).to("cuda", tdt)
+    u1, u2 = torch.empty_like(V), torch.empty_like(V)
+    run_steps(ctx, spec, m, V, (u1, u2), dt, W_, flush, None)
+    events = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+    barrier(world)
+    torch.cuda.synchronize()
+    step_ms, stage_ms = run_steps(ctx, spec, m, V, (u1, u2), dt, K, flush, events)
+    torch.cuda.synchronize()
+    barrier(world)
+    assert torch.isfinite(V).all().item()
+    total_ms = max_over_ranks(sum(step_ms), world)
+    return {"total_ms": total_ms, "ms_per_step": total_ms / K, "stage_ms": stage_ms,
+            "launch_ms_mean": sum(stage_ms) / len(stage_ms), "launches": 3 * K, "dt": dt}
+
+
+def bench_e2e(ctx, spec, V0, dtype, K, W_, world):
+    """hj_solve with pinned host input/output: H2D of V0, the steps to tau = 0.28, D2H of V."""
+    import torch
+    from paper_2507_11542_gb300 import solver
+    m = solver.method(dynamics=2, params=(5.0, 5.0, 1.0, 1.0), brt=1)
+    tdt = getattr(torch, dtype)
+    v0 = torch.from_numpy(np.ascontiguousarray(V0.ravel(order="F"))).to(tdt).pin_memory()
+    out = torch.empty((1, v0.numel()), dtype=tdt).pin_memory()
+    for _ in range(W_):
+        solver.solve(ctx, spec, m, v0, [E2E_TAU], out=out)
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    steps = launches = 0
+    for _ in range(K):
+        _, _, st = solver.solve(ctx, spec, m, v0, [E2E_TAU], out=out)
+        steps += st["steps"]
+        launches += st["kernel_launches"]
+    torch.cuda.synchronize()
+    el = max_over_ranks(time.perf_counter() - t0, world)
+    return {"value": world * steps * N_CELLS / el, "unit": "cell-updates/s",
+            "h2d_bytes_per_step": int(v0.numel() * v0.element_size()),
+            "d2h_bytes_per_step": int(out.numel() * out.element_size()),
+            "rk3_steps_per_step": steps // K, "launches": launches}
+
+
+def cpu_oracle_rate(spec, V0, steps: int):
+    """The FP64 oracle, single-threaded, on the full 101^3 grid for `steps` RK3 steps."""
+    from oracle import oracle as O
+    m = O.method(scheme=O.WENO5, dynamics=O.DYN_AIR3D, params=(5.0, 5.0, 1.0, 1.0), brt=O.BRT_MIN0)
+    dt = 0.8 / O.step_bound_inv(spec, m)
+    V = V0
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        V = O.rk3_step(spec, m, V, dt)
+    el = time.perf_counter() - t0
+    return steps * N_CELLS / el, el
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    spec, V0 = workload()
+    from oracle import oracle as O
+    O.build()
+    m = O.method(scheme=O.WENO5, dynamics=O.DYN_AIR3D, params=(5.0, 5.0, 1.0, 1.0), brt=O.BRT_MIN0)
+    dt = 0.8 / O.step_bound_inv(spec, m)
+    V = V0
+    for _ in range(args.warmup):
+        V = O.rk3_step(spec, m, V, dt)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        V = O.rk3_step(spec, m, V, dt)
+    el = time.perf_counter() - t0
+    value = args.steps * N_CELLS / el
+    line = {"impl": "reference", "metric": "cell-updates/s (air3D 101^3 WENO5 TVD-RK3 step)", "value": value,
+            "unit": "cell-updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "air3d-101^3 WENO5 LF TVD-RK3 CFL0.8 BRT-min0", "cells": N_CELLS,
+                       "l2": "host run (no GPU)"},
+            "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+                             "sample": "%d RK3 steps of the full 101^3 grid, single thread" % args.steps},
+            "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-steps", type=int, default=12, help="oracle steps for the cpu_baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    import torch
+    from paper_2507_11542_gb300 import _lib, build, solver
+    if world == 1 and build.stale():
+        build.build()
+    torch.cuda.set_device(local)
+    spec, V0 = workload()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    ctx = solver.Context(local)
+    K, W_ = args.steps, max(args.warmup, 3)
+    with ClockSampler(local) as clk:
+        r32 = bench_dtype(ctx, spec, V0, "float32", K, W_, world, flush)
+    r64 = bench_dtype(ctx, spec, V0, "float64", max(3, K // 4), 3, world, flush)
+    e2e = bench_e2e(ctx, spec, V0, "float32", max(3, K // 4), 2, world)
+    value = world * K * N_CELLS / (r32["total_ms"] / 1e3)
+    hbm, hbm_kind = measured_hbm_gbs()
+    launch_s = r32["launch_ms_mean"] / 1e3
+    achieved_tflops = FLOPS_PER_NODE_STAGE * N_CELLS / launch_s / 1e12
+    words_per_launch = WORDS_PER_NODE_STEP / 3.0
+    achieved_gbs = words_per_launch * 4 * N_CELLS / launch_s / 1e9
+    launch64_s = r64["launch_ms_mean"] / 1e3
+    line = {
+        "metric": "cell-updates/s (air3D 101^3 WENO5 TVD-RK3 step)",
+        "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": K, "warmup": W_,
+        "ms_per_step": r32["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "air3d-101^3 WENO5 LF TVD-RK3 CFL0.8 BRT-min0", "cells": N_CELLS,
+                   "l2": "flushed (256 MiB write) before every timed step",
+                   "time": "FP64 t, dt and CFL bound", "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved_tflops / FP32_PEAK_TFLOPS, "traffic": None,
+                     "kernel": "stage_kernel<float,3,WENO5>",
+                     "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (unit counts x max clock)",
+                     "hbm_achieved_gbs": achieved_gbs, "hbm_peak_gbs": hbm, "hbm_peak_source": hbm_kind,
+                     "hbm_frac": achieved_gbs / hbm},
+        "fp64": {"value": world * N_CELLS / (r64["ms_per_step"] / 1e3), "unit": "cell-updates/s",
+                 "ms_per_step": r64["ms_per_step"], "steps": len(r64["stage_ms"]) // 3,
+                 "roofline": {"bound": "alu", "achieved": FLOPS_PER_NODE_STAGE * N_CELLS / launch64_s / 1e12,
+                              "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                              "frac": FLOPS_PER_NODE_STAGE * N_CELLS / launch64_s / 1e12 / FP64_PEAK_TFLOPS,
+                              "peak_source": "152 SMs x 2 FP64 lanes x 2 x 2070 MHz"}},
+        "e2e": {k: e2e[k] for k in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step")},
+        "gpu_launches": r32["launches"],
+        "clocks": clk.summary(),
+    }
+    line["e2e"]["rk3_steps_per_call"] = e2e["rk3_steps_per_step"]
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, el = cpu_oracle_rate(spec, V0, args.cpu_steps)
+        line["cpu_baseline"] = {"value": rate, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+                                "sample": "%d RK3 steps of the full 101^3 air3D grid, FP64, single thread (%.1f s)"
+                                          % (args.cpu_steps, el)}
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,194 @@
+/*
+ * hj.h -- C ABI of the GB300 (sm_103a) level-set library: one TVD-RK3 step of
+ * the Hamilton-Jacobi(-Isaacs) value-function update on a dense Cartesian
+ * grid, and the time loop around it, after LevelSetPy (arXiv 2507.11542).
+ *
+ * General rules for every entry point:
+ *  - Calls return an hj_status; no C++ exception ever crosses this boundary.
+ *    hj_ctx_last_error() gives a one-line description of the last failure.
+ *  - Every compute call is enqueued on the context's stream. Calls that take
+ *    or return host memory synchronise that stream before they return; calls
+ *    on device memory only do not, unless stated.
+ *  - Grid arrays hold prod(n) elements, dimension 0 fastest ("column-major",
+ *    Sec. 2.1): flat index i0 + n0*(i1 + n1*(i2 + n2*i3)). Element type is
+ *    given by an hj_dtype. Inputs are never modified unless stated; on an
+ *    error the contents of outputs are unspecified.
+ *  - Device pointers must be allocated on the context's device and aligned to
+ *    the element size. The caller owns every buffer it passes in.
+ *  - Time is time-to-go tau >= 0: V_tau = Hg_LF (Sec. 4), the tau-form of the
+ *    paper's v_t + H = 0; a backward reachable tube clamps it at zero (Sec. 6.1).
+ */
+#ifndef HJ_H
+#define HJ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum hj_status {
+    HJ_OK = 0,
+    HJ_EINVAL = 1,      /* a malformed argument; nothing was enqueued */
+    HJ_ENOMEM = 2,      /* a device or host allocation failed */
+    HJ_ECUDA = 3,       /* a CUDA runtime call failed (see hj_ctx_last_error) */
+    HJ_ENONFINITE = 4,  /* the initial value function or a result holds NaN/Inf */
+    HJ_ETIMEOUT = 5,    /* a bounded wait ran out */
+    HJ_ECANCELLED = 6,  /* a served request was cancelled */
+    HJ_EBUSY = 7        /* no slot or memory for a request right now */
+} hj_status;
+
+/* Upwind derivative schemes (Sec. 3.1 first order; Sec. 3.2 ENO2/ENO3,
+ * Listing 4; Sec. 3.3 WENO5). */
+enum { HJ_ENO1 = 1, HJ_ENO2 = 2, HJ_ENO3 = 3, HJ_WENO5 = 5 };
+
+/* Dynamics / Hamiltonians Hg(x, p). Reachability dynamics take the optimum of
+ * p . f over bounded controls (Sec. 6.1); the level-set test Hamiltonians are
+ * the equations of Sec. 3 (v_t + F . grad v = 0) and normal motion.
+ *   DOUBLE_INTEGRATOR (2-D)  params {umax}:              Hg = p0 x1 - umax |p1|
+ *   AIR3D (3-D)              params {va, vb, amax, bmax}: Hg = p0(-va + vb cos x2)
+ *                            + p1 vb sin x2 + amax|p0 x1 - p1 x0 - p2| - bmax|p2|
+ *   DUBINS4D (4-D)           params {wmax, accmax}:      Hg = x3(p0 cos x2 + p1 sin x2)
+ *                            - wmax|p2| - accmax|p3|
+ *   NORM (1..3-D)            params {c}:                 Hg = -c |p|
+ *   ADVECT (1..3-D)          params {c0, c1, c2}:        Hg = -c . p
+ *   ROTATE (2..3-D)          params {omega}:             Hg = -p . omega(-x1, x0, 0)
+ * The dissipation alpha_d(x) is the maximum of |f_d| over the controls
+ * (Sec. 4, "alpha = max |H_p|"), evaluated per node. */
+enum {
+    HJ_DYN_DOUBLE_INTEGRATOR = 1,
+    HJ_DYN_AIR3D = 2,
+    HJ_DYN_DUBINS4D = 3,
+    HJ_DYN_NORM = 4,
+    HJ_DYN_ADVECT = 5,
+    HJ_DYN_ROTATE = 6
+};
+
+/* Backward-reachable-tube rule (Sec. 6.1): none, V_tau = min(0, Hg_LF) at each
+ * RK stage, or V <- min(V_new, V_old) after each full step. */
+enum { HJ_BRT_NONE = 0, HJ_BRT_MIN0 = 1, HJ_BRT_MINV = 2 };
+
+/* Element type of grid arrays. FP32 arrays still use FP64 time, dt and CFL
+ * reduction. */
+enum { HJ_F32 = 1, HJ_F64 = 2 };
+
+/* Extrapolated (non-periodic) ghost cells (Sec. 2.1 "boundary values"): the
+ * outermost slope continued away from the zero level set,
+ * g_m = v_0 + m |v_0 - v_1| sign(v_0), or the plain signed slope v_0 - v_1. */
+enum { HJ_EXTRAP_AWAY_FROM_ZERO = 0, HJ_EXTRAP_LINEAR = 1 };
+
+/* A dense Cartesian grid (Sec. 2.1, Listing 1: createGrid(min, max, N, pdim)).
+ * ndim in 1..4; n[d] >= 2 for an extrapolated dimension, >= 1 for a periodic
+ * one. A periodic dimension covers [lo, hi) with spacing (hi-lo)/n, any other
+ * [lo, hi] with spacing (hi-lo)/(n-1). Node coordinate lo[d] + i*dx[d]. */
+typedef struct hj_grid {
+    int32_t ndim;
+    int64_t n[4];
+    double lo[4];
+    double hi[4];
+    uint32_t periodic_mask; /* bit d set: dimension d is periodic */
+} hj_grid;
+
+/* The numerical method (the paper's schemeData / finite_diff_data, Listing 7). */
+typedef struct hj_method {
+    int32_t scheme;    /* HJ_ENO1 .. HJ_WENO5 */
+    int32_t dynamics;  /* HJ_DYN_* */
+    double params[8];  /* dynamics parameters, see above */
+    int32_t brt;       /* HJ_BRT_* */
+    int32_t extrap;    /* HJ_EXTRAP_* */
+    double cfl;        /* CFL factor in (0, 1]; Sec. 4-5 (0.8 in the workloads) */
+    double max_step;   /* upper bound on dt; +inf for none (Listing 6 maxStep) */
+} hj_method;
+
+/* One reachability / level-set solve (Sec. 5, Listing 6: odeCFL3(func, tspan, v0)). */
+typedef struct hj_problem {
+    hj_grid grid;
+    hj_method method;
+    int32_t dtype;             /* HJ_F32 or HJ_F64: element type of v0 and of the output */
+    const void* v0;            /* initial value function, prod(n) elements */
+    int32_t v0_on_device;      /* 1: v0 is device memory, 0: host memory */
+    int32_t n_slices;          /* >= 1 output times */
+    const double* slice_times; /* host array, non-decreasing, >= 0 */
+} hj_problem;
+
+typedef struct hj_stats {
+    int64_t steps;           /* RK3 steps taken */
+    int64_t cell_updates;    /* steps * prod(n) */
+    int64_t kernel_launches; /* kernels of this library launched by the call */
+    double step_bound_inv;   /* max_x sum_d alpha_d(x)/dx_d (Sec. 4 CFL bound) */
+    double t_final;          /* time reached at the last slice */
+    double elapsed_ms;       /* wall time of the call */
+} hj_stats;
+
+typedef struct hj_ctx hj_ctx;
+
+/* Context: owns device scratch (RK stage buffers, reduction words, angle
+ * tables) for one device and one stream. `cuda_stream` is a cudaStream_t
+ * borrowed from the caller (NULL = legacy default stream); it must outlive the
+ * context. Not thread-safe: use one context per host thread.
+ * Errors: HJ_EINVAL (bad device or NULL out), HJ_ECUDA, HJ_ENOMEM. */
+hj_status hj_ctx_create(int32_t device, void* cuda_stream, hj_ctx** out);
+/* Frees the context's device memory after synchronising its stream. NULL is a no-op. */
+void hj_ctx_destroy(hj_ctx* ctx);
+const char* hj_status_str(hj_status status);
+/* Last error message of this context ("" if none); owned by the context. */
+const char* hj_ctx_last_error(const hj_ctx* ctx);
+/* The library's version string, e.g. "hj-gb300 0.1 sm_103a". */
+const char* hj_version(void);
+
+/* Rows of the hot path, one call each, on device arrays. ---------------- */
+
+/* Upwind left/right derivatives p-, p+ along dimension `dim` at every node
+ * (Sec. 3.1-3.3) from V with ghost cells per the grid (Sec. 2.1). Reads v,
+ * writes pm and pp (device, prod(n) elements of `dtype` each). Asynchronous.
+ * Errors: HJ_EINVAL (grid, scheme, dim, dtype or a NULL pointer), HJ_ECUDA. */
+hj_status hj_upwind(hj_ctx* ctx, const hj_grid* grid, const hj_method* method, int32_t dtype,
+                    const void* v, int32_t dim, void* pm, void* pp);
+
+/* Lax-Friedrichs term ydot = Hg(x, (p- + p+)/2) + sum_d alpha_d (p+_d - p-_d)/2
+ * (Sec. 4, Listing 5), clamped to min(0, ydot) when method->brt is
+ * HJ_BRT_MIN0 (Sec. 6.1). Reads v, writes ydot (device). Asynchronous.
+ * Errors: HJ_EINVAL, HJ_ECUDA. */
+hj_status hj_term(hj_ctx* ctx, const hj_grid* grid, const hj_method* method, int32_t dtype,
+                  const void* v, void* ydot);
+
+/* CFL bound max over nodes of sum_d alpha_d(x)/dx_d in FP64 (Sec. 4), written
+ * to *out (host). For every supported dynamics alpha depends on x only, so
+ * the value is the same at every step. Synchronises the stream.
+ * Errors: HJ_EINVAL, HJ_ECUDA. */
+hj_status hj_step_bound(hj_ctx* ctx, const hj_grid* grid, const hj_method* method, double* out);
+
+/* One TVD-RK3 step of size dt (Sec. 5, Listing 6), in place on the device
+ * array v: three fused stage kernels (upwind + Hamiltonian + dissipation +
+ * BRT rule + stage combination). Stage buffers come from the context.
+ * Asynchronous. Errors: HJ_EINVAL (dt < 0 or not finite, ...), HJ_ENOMEM, HJ_ECUDA. */
+hj_status hj_rk3_step(hj_ctx* ctx, const hj_grid* grid, const hj_method* method, int32_t dtype,
+                      void* v, double dt);
+
+/* One fused stage of the TVD-RK3 step (Sec. 5, Listing 6), with
+ * w = u + dt * L(u) and L the Lax-Friedrichs term above:
+ *   stage 1: out = w
+ *   stage 2: out = 3/4 vn + 1/4 w
+ *   stage 3: out = 1/3 vn + 2/3 w, then min(out, vn) when method->brt is HJ_BRT_MINV.
+ * u, vn, out are device arrays; vn is unused (may be NULL) in stage 1. out must
+ * not alias u; it may alias vn. Asynchronous.
+ * Errors: HJ_EINVAL (stage not 1..3, aliasing, ...), HJ_ECUDA. */
+hj_status hj_rk3_stage(hj_ctx* ctx, const hj_grid* grid, const hj_method* method, int32_t dtype, int32_t stage,
+                       const void* u, const void* vn, void* out, double dt);
+
+/* Whole solve (Sec. 5, Listing 6): V(tau = 0) = v0, then for each slice time
+ * t_s, RK3 steps with dt = min(t_s - t, max_step, cfl / stepBoundInv) while
+ * t_s - t >= 100 * DBL_EPSILON * t_s; V at each slice goes to
+ * out_slices + s * prod(n) (device memory if out_on_device, else host).
+ * out_times (host, n_slices doubles, may be NULL) receives the time reached at
+ * each slice; stats may be NULL. Synchronises the stream before returning.
+ * Errors: HJ_EINVAL, HJ_ENOMEM, HJ_ENONFINITE (v0 or the result holds
+ * NaN/Inf), HJ_ECUDA. */
+hj_status hj_solve(hj_ctx* ctx, const hj_problem* problem, void* out_slices, int32_t out_on_device,
+                   double* out_times, hj_stats* stats);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HJ_H */

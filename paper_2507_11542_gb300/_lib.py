@@ -1,0 +1,240 @@
+"""Thin ctypes binding of libhj.so (include/hj.h), with the same names.
+
+Argument marshalling only: every step of the level-set update runs in the
+CUDA kernels of libhj.so. There is no fallback; loading fails loudly when the
+library has not been built (``python -m paper_2507_11542_gb300.build``).
+
+Grid arrays cross the boundary as flat, contiguous torch tensors (or host
+numpy arrays for host-side inputs/outputs) of prod(n) elements with
+dimension 0 fastest. ``to_flat`` / ``from_flat`` convert from/to numpy arrays
+of shape (n0, ..., n_{D-1}) in Fortran order.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import threading
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libhj.so")
+
+HJ_OK, HJ_EINVAL, HJ_ENOMEM, HJ_ECUDA, HJ_ENONFINITE, HJ_ETIMEOUT, HJ_ECANCELLED, HJ_EBUSY = range(8)
+HJ_ENO1, HJ_ENO2, HJ_ENO3, HJ_WENO5 = 1, 2, 3, 5
+(HJ_DYN_DOUBLE_INTEGRATOR, HJ_DYN_AIR3D, HJ_DYN_DUBINS4D, HJ_DYN_NORM, HJ_DYN_ADVECT,
+ HJ_DYN_ROTATE) = 1, 2, 3, 4, 5, 6
+HJ_BRT_NONE, HJ_BRT_MIN0, HJ_BRT_MINV = 0, 1, 2
+HJ_F32, HJ_F64 = 1, 2
+HJ_EXTRAP_AWAY_FROM_ZERO, HJ_EXTRAP_LINEAR = 0, 1
+
+# every function include/hj.h declares (checked by the test-suite against the .so)
+EXPORTS = ["hj_ctx_create", "hj_ctx_destroy", "hj_status_str", "hj_ctx_last_error", "hj_version",
+           "hj_upwind", "hj_term", "hj_step_bound", "hj_rk3_step", "hj_rk3_stage", "hj_solve"]
+
+
+class hj_grid(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int32), ("n", ctypes.c_int64 * 4), ("lo", ctypes.c_double * 4),
+                ("hi", ctypes.c_double * 4), ("periodic_mask", ctypes.c_uint32)]
+
+
+class hj_method(ctypes.Structure):
+    _fields_ = [("scheme", ctypes.c_int32), ("dynamics", ctypes.c_int32), ("params", ctypes.c_double * 8),
+                ("brt", ctypes.c_int32), ("extrap", ctypes.c_int32), ("cfl", ctypes.c_double),
+                ("max_step", ctypes.c_double)]
+
+
+class hj_problem(ctypes.Structure):
+    _fields_ = [("grid", hj_grid), ("method", hj_method), ("dtype", ctypes.c_int32), ("v0", ctypes.c_void_p),
+                ("v0_on_device", ctypes.c_int32), ("n_slices", ctypes.c_int32),
+                ("slice_times", ctypes.POINTER(ctypes.c_double))]
+
+
+class hj_stats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int64), ("cell_updates", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
+                ("step_bound_inv", ctypes.c_double), ("t_final", ctypes.c_double), ("elapsed_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class HJError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s (%d): %s" % (_STATUS.get(status, "?"), status, message))
+        self.status = status
+
+
+_STATUS = {HJ_OK: "HJ_OK", HJ_EINVAL: "HJ_EINVAL", HJ_ENOMEM: "HJ_ENOMEM", HJ_ECUDA: "HJ_ECUDA",
+           HJ_ENONFINITE: "HJ_ENONFINITE", HJ_ETIMEOUT: "HJ_ETIMEOUT", HJ_ECANCELLED: "HJ_ECANCELLED",
+           HJ_EBUSY: "HJ_EBUSY"}
+
+_lock = threading.Lock()
+_lib = None
+_P = ctypes.POINTER
+_vp = ctypes.c_void_p
+
+
+def load():
+    """Load libhj.so; raises if it is missing (no CPU or eager fallback exists)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError("libhj.so is not built at %s; run paper_2507_11542_gb300.build.build()" % LIB_PATH)
+            L = ctypes.CDLL(LIB_PATH)
+            L.hj_ctx_create.argtypes = [ctypes.c_int32, _vp, _P(_vp)]
+            L.hj_ctx_destroy.argtypes = [_vp]
+            L.hj_ctx_destroy.restype = None
+            L.hj_status_str.argtypes = [ctypes.c_int]
+            L.hj_status_str.restype = ctypes.c_char_p
+            L.hj_ctx_last_error.argtypes = [_vp]
+            L.hj_ctx_last_error.restype = ctypes.c_char_p
+            L.hj_version.restype = ctypes.c_char_p
+            L.hj_upwind.argtypes = [_vp, _P(hj_grid), _P(hj_method), ctypes.c_int32, _vp, ctypes.c_int32, _vp, _vp]
+            L.hj_term.argtypes = [_vp, _P(hj_grid), _P(hj_method), ctypes.c_int32, _vp, _vp]
+            L.hj_step_bound.argtypes = [_vp, _P(hj_grid), _P(hj_method), _P(ctypes.c_double)]
+            L.hj_rk3_step.argtypes = [_vp, _P(hj_grid), _P(hj_method), ctypes.c_int32, _vp, ctypes.c_double]
+            L.hj_rk3_stage.argtypes = [_vp, _P(hj_grid), _P(hj_method), ctypes.c_int32, ctypes.c_int32, _vp, _vp, _vp,
+                                       ctypes.c_double]
+            L.hj_solve.argtypes = [_vp, _P(hj_problem), _vp, ctypes.c_int32, _P(ctypes.c_double), _P(hj_stats)]
+            _lib = L
+    return _lib
+
+
+def _check(ctx, status):
+    if status != HJ_OK:
+        msg = load().hj_ctx_last_error(ctx).decode() if ctx else ""
+        raise HJError(status, msg)
+
+
+# ---------------------------------------------------------------------------
+# struct builders
+# ---------------------------------------------------------------------------
+
+def make_grid(spec) -> hj_grid:
+    """spec: any object with n, lo, hi (sequences) and periodic (dimension indices)."""
+    g = hj_grid()
+    g.ndim = len(spec.n)
+    for d in range(g.ndim):
+        g.n[d] = int(spec.n[d])
+        g.lo[d] = float(spec.lo[d])
+        g.hi[d] = float(spec.hi[d])
+    mask = 0
+    for d in spec.periodic:
+        mask |= 1 << int(d)
+    g.periodic_mask = mask
+    return g
+
+
+def make_method(scheme=HJ_WENO5, dynamics=HJ_DYN_DOUBLE_INTEGRATOR, params=(), brt=HJ_BRT_MIN0,
+                extrap=HJ_EXTRAP_AWAY_FROM_ZERO, cfl=0.8, max_step=math.inf) -> hj_method:
+    m = hj_method()
+    m.scheme = scheme
+    m.dynamics = dynamics
+    for i, p in enumerate(params):
+        m.params[i] = float(p)
+    m.brt = brt
+    m.extrap = extrap
+    m.cfl = float(cfl)
+    m.max_step = float(max_step)
+    return m
+
+
+def dtype_code(torch_dtype) -> int:
+    import torch
+    if torch_dtype == torch.float64:
+        return HJ_F64
+    if torch_dtype == torch.float32:
+        return HJ_F32
+    raise ValueError("grid arrays must be float32 or float64")
+
+
+def to_flat(V: np.ndarray) -> np.ndarray:
+    """(n0, ..., n_{D-1}) array -> flat array with dimension 0 fastest."""
+    return np.asarray(V).ravel(order="F")
+
+
+def from_flat(flat, n) -> np.ndarray:
+    return np.asarray(flat).reshape(tuple(n), order="F")
+
+
+# ---------------------------------------------------------------------------
+# entry points (same names as the C ABI)
+# ---------------------------------------------------------------------------
+
+def hj_version() -> str:
+    return load().hj_version().decode()
+
+
+def hj_status_str(status: int) -> str:
+    return load().hj_status_str(status).decode()
+
+
+def hj_ctx_create(device: int = 0, stream: int | None = None) -> int:
+    """stream: a raw cudaStream_t (e.g. torch.cuda.current_stream().cuda_stream)."""
+    out = _vp()
+    st = load().hj_ctx_create(int(device), _vp(stream or 0), ctypes.byref(out))
+    if st != HJ_OK:
+        raise HJError(st, "hj_ctx_create(device=%d)" % device)
+    return out.value
+
+
+def hj_ctx_destroy(ctx: int) -> None:
+    load().hj_ctx_destroy(_vp(ctx))
+
+
+def hj_ctx_last_error(ctx: int) -> str:
+    return load().hj_ctx_last_error(_vp(ctx)).decode()
+
+
+def _ptr(t) -> int:
+    return 0 if t is None else int(t.data_ptr())
+
+
+def hj_upwind(ctx, grid: hj_grid, method: hj_method, dtype: int, v, dim: int, pm, pp) -> None:
+    _check(ctx, load().hj_upwind(_vp(ctx), ctypes.byref(grid), ctypes.byref(method), dtype, _vp(_ptr(v)), dim,
+                                 _vp(_ptr(pm)), _vp(_ptr(pp))))
+
+
+def hj_term(ctx, grid: hj_grid, method: hj_method, dtype: int, v, ydot) -> None:
+    _check(ctx, load().hj_term(_vp(ctx), ctypes.byref(grid), ctypes.byref(method), dtype, _vp(_ptr(v)),
+                               _vp(_ptr(ydot))))
+
+
+def hj_step_bound(ctx, grid: hj_grid, method: hj_method) -> float:
+    out = ctypes.c_double(0.0)
+    _check(ctx, load().hj_step_bound(_vp(ctx), ctypes.byref(grid), ctypes.byref(method), ctypes.byref(out)))
+    return out.value
+
+
+def hj_rk3_step(ctx, grid: hj_grid, method: hj_method, dtype: int, v, dt: float) -> None:
+    _check(ctx, load().hj_rk3_step(_vp(ctx), ctypes.byref(grid), ctypes.byref(method), dtype, _vp(_ptr(v)),
+                                   float(dt)))
+
+
+def hj_rk3_stage(ctx, grid: hj_grid, method: hj_method, dtype: int, stage: int, u, vn, out, dt: float) -> None:
+    _check(ctx, load().hj_rk3_stage(_vp(ctx), ctypes.byref(grid), ctypes.byref(method), dtype, int(stage),
+                                    _vp(_ptr(u)), _vp(_ptr(vn)), _vp(_ptr(out)), float(dt)))
+
+
+def hj_solve(ctx, problem: hj_problem, out_slices_ptr: int, out_on_device: bool, out_times: np.ndarray | None):
+    stats = hj_stats()
+    tp = None if out_times is None else out_times.ctypes.data_as(_P(ctypes.c_double))
+    _check(ctx, load().hj_solve(_vp(ctx), ctypes.byref(problem), _vp(out_slices_ptr), int(bool(out_on_device)), tp,
+                                ctypes.byref(stats)))
+    return stats
+
+
+def make_problem(spec, method: hj_method, dtype: int, v0_ptr: int, v0_on_device: bool, slice_times: np.ndarray):
+    """Returns (problem, keepalive) -- keep the second value alive while the problem is in use."""
+    ts = np.ascontiguousarray(slice_times, dtype=np.float64)
+    p = hj_problem()
+    p.grid = make_grid(spec)
+    p.method = method
+    p.dtype = dtype
+    p.v0 = v0_ptr
+    p.v0_on_device = int(bool(v0_on_device))
+    p.n_slices = ts.size
+    p.slice_times = ts.ctypes.data_as(_P(ctypes.c_double))
+    return p, ts

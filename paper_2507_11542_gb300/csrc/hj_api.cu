@@ -1,0 +1,546 @@
+// hj_api.cu -- the C ABI of include/hj.h: context, argument validation, the
+// per-row entry points and the time loop of Sec. 5 (Listing 6).
+#include <cfloat>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/hj.h"
+#include "hj_internal.h"
+
+struct hj_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    void* work[2] = {nullptr, nullptr};   // RK stage buffers (V1, V2)
+    size_t work_bytes = 0;
+    void* state = nullptr;                // the solve's own copy of V
+    size_t state_bytes = 0;
+    unsigned long long* aux = nullptr;    // [0] step-bound accumulator, [1] non-finite flag
+    double* trig_d = nullptr;             // cos/sin tables of the dimension-2 coordinate
+    float* trig_f = nullptr;
+    size_t trig_cap = 0;
+    double trig_key[3] = {0.0, 0.0, 0.0};  // (n, lo, dx) of the uploaded tables
+    bool trig_valid = false;
+    std::string last_error;
+    long long launches = 0;
+};
+
+namespace {
+
+using namespace hj;
+
+hj_status fail(hj_ctx* ctx, hj_status st, const char* fmt, ...) {
+    if (ctx) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        ctx->last_error = buf;
+    }
+    return st;
+}
+
+hj_status cuda_fail(hj_ctx* ctx, cudaError_t e, const char* what) {
+    return fail(ctx, e == cudaErrorMemoryAllocation ? HJ_ENOMEM : HJ_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define HJ_CUDA(ctx, call)                                       \
+    do {                                                         \
+        cudaError_t e_ = (call);                                 \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+size_t elem_size(int dtype) { return dtype == HJ_F64 ? 8 : (dtype == HJ_F32 ? 4 : 0); }
+
+hj_status check_grid(hj_ctx* ctx, const hj_grid* g) {
+    if (!g) return fail(ctx, HJ_EINVAL, "grid is NULL");
+    if (g->ndim < 1 || g->ndim > 4) return fail(ctx, HJ_EINVAL, "ndim %d not in 1..4", g->ndim);
+    long long total = 1;
+    for (int d = 0; d < g->ndim; ++d) {
+        const bool periodic = (g->periodic_mask >> d) & 1u;
+        if (g->n[d] < (periodic ? 1 : 2)) return fail(ctx, HJ_EINVAL, "n[%d] = %lld too small", d, (long long)g->n[d]);
+        if (g->n[d] > (1ll << 30)) return fail(ctx, HJ_EINVAL, "n[%d] too large", d);
+        if (!std::isfinite(g->lo[d]) || !std::isfinite(g->hi[d]) || !(g->hi[d] > g->lo[d]))
+            return fail(ctx, HJ_EINVAL, "bounds of dimension %d are not finite with hi > lo", d);
+        total *= g->n[d];
+        if (total > (1ll << 40)) return fail(ctx, HJ_EINVAL, "grid too large");
+    }
+    if (g->periodic_mask >> g->ndim) return fail(ctx, HJ_EINVAL, "periodic_mask names a dimension >= ndim");
+    return HJ_OK;
+}
+
+hj_status check_method(hj_ctx* ctx, const hj_grid* g, const hj_method* m) {
+    if (!m) return fail(ctx, HJ_EINVAL, "method is NULL");
+    if (m->scheme != HJ_ENO1 && m->scheme != HJ_ENO2 && m->scheme != HJ_ENO3 && m->scheme != HJ_WENO5)
+        return fail(ctx, HJ_EINVAL, "unknown scheme %d", m->scheme);
+    if (m->brt < HJ_BRT_NONE || m->brt > HJ_BRT_MINV) return fail(ctx, HJ_EINVAL, "unknown brt mode %d", m->brt);
+    if (m->extrap != HJ_EXTRAP_AWAY_FROM_ZERO && m->extrap != HJ_EXTRAP_LINEAR)
+        return fail(ctx, HJ_EINVAL, "unknown extrapolation %d", m->extrap);
+    for (int k = 0; k < 8; ++k)
+        if (!std::isfinite(m->params[k])) return fail(ctx, HJ_EINVAL, "params[%d] is not finite", k);
+    const int D = g->ndim;
+    const double* q = m->params;
+    switch (m->dynamics) {
+    case HJ_DYN_DOUBLE_INTEGRATOR:
+        if (D != 2) return fail(ctx, HJ_EINVAL, "double integrator needs ndim 2");
+        if (q[0] < 0) return fail(ctx, HJ_EINVAL, "umax < 0");
+        break;
+    case HJ_DYN_AIR3D:
+        if (D != 3) return fail(ctx, HJ_EINVAL, "air3D needs ndim 3");
+        if (q[2] < 0 || q[3] < 0) return fail(ctx, HJ_EINVAL, "control bounds < 0");
+        break;
+    case HJ_DYN_DUBINS4D:
+        if (D != 4) return fail(ctx, HJ_EINVAL, "Dubins4D needs ndim 4");
+        if (q[0] < 0 || q[1] < 0) return fail(ctx, HJ_EINVAL, "control bounds < 0");
+        break;
+    case HJ_DYN_NORM:
+        if (D > 3) return fail(ctx, HJ_EINVAL, "norm Hamiltonian supports ndim 1..3");
+        if (q[0] < 0) return fail(ctx, HJ_EINVAL, "speed < 0");
+        break;
+    case HJ_DYN_ADVECT:
+        if (D > 3) return fail(ctx, HJ_EINVAL, "advection supports ndim 1..3");
+        break;
+    case HJ_DYN_ROTATE:
+        if (D < 2 || D > 3) return fail(ctx, HJ_EINVAL, "rotation supports ndim 2..3");
+        break;
+    default:
+        return fail(ctx, HJ_EINVAL, "unknown dynamics %d", m->dynamics);
+    }
+    return HJ_OK;
+}
+
+hj_status check_solver_settings(hj_ctx* ctx, const hj_method* m) {
+    if (!(m->cfl > 0.0) || !(m->cfl <= 1.0)) return fail(ctx, HJ_EINVAL, "cfl must be in (0, 1]");
+    if (!(m->max_step > 0.0)) return fail(ctx, HJ_EINVAL, "max_step must be > 0");
+    return HJ_OK;
+}
+
+GridDev make_grid(const hj_grid* g, int extrap) {
+    GridDev G;
+    std::memset(&G, 0, sizeof G);
+    G.ndim = g->ndim;
+    long long stride = 1;
+    for (int d = 0; d < 4; ++d) {
+        if (d < g->ndim) {
+            const bool periodic = (g->periodic_mask >> d) & 1u;
+            G.n[d] = (int)g->n[d];
+            G.stride[d] = stride;
+            stride *= g->n[d];
+            G.lo[d] = g->lo[d];
+            G.dx[d] = (g->hi[d] - g->lo[d]) / (periodic ? (double)g->n[d] : (double)(g->n[d] - 1));
+            G.inv_dx[d] = 1.0 / G.dx[d];
+        } else {
+            G.n[d] = 1;
+            G.stride[d] = stride;
+            G.dx[d] = 1.0;
+            G.inv_dx[d] = 1.0;
+        }
+    }
+    G.total = stride;
+    G.periodic_mask = g->periodic_mask;
+    G.extrap = extrap;
+    return G;
+}
+
+// WENO5 epsilon floor in raw-difference units: FP64 uses 1e-99 (on derivatives,
+// so scaled by the smallest dx^2); FP32 uses 1e-18 directly so that the
+// squared sums stay normal numbers.
+double weno_floor(const GridDev& g, int dtype) {
+    if (dtype == HJ_F32) return 1e-18;
+    double m = g.dx[0];
+    for (int d = 1; d < g.ndim; ++d) m = std::fmin(m, g.dx[d]);
+    return 1e-99 * m * m;
+}
+
+hj_status ensure(hj_ctx* ctx, void** p, size_t* cap, size_t bytes) {
+    if (*cap >= bytes && *p) return HJ_OK;
+    if (*p) {
+        HJ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        cudaFree(*p);
+        *p = nullptr;
+        *cap = 0;
+    }
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return cuda_fail(ctx, e, "cudaMalloc");
+    }
+    *cap = bytes;
+    return HJ_OK;
+}
+
+hj_status ensure_work(hj_ctx* ctx, size_t bytes) {
+    if (ctx->work_bytes >= bytes && ctx->work[0]) return HJ_OK;
+    if (ctx->work[0]) {
+        HJ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        cudaFree(ctx->work[0]);
+        cudaFree(ctx->work[1]);
+        ctx->work[0] = ctx->work[1] = nullptr;
+        ctx->work_bytes = 0;
+    }
+    for (int k = 0; k < 2; ++k) {
+        cudaError_t e = cudaMalloc(&ctx->work[k], bytes);
+        if (e != cudaSuccess) {
+            cudaFree(ctx->work[0]);
+            ctx->work[0] = ctx->work[1] = nullptr;
+            return cuda_fail(ctx, e, "cudaMalloc(stage buffers)");
+        }
+    }
+    ctx->work_bytes = bytes;
+    return HJ_OK;
+}
+
+// cos/sin of the dimension-2 coordinate (the heading angle of air3D and
+// Dubins4D), from the host math library, in both precisions.
+hj_status upload_trig(hj_ctx* ctx, const hj_grid* g, int dynamics) {
+    if (dynamics != HJ_DYN_AIR3D && dynamics != HJ_DYN_DUBINS4D) return HJ_OK;
+    const int n = (int)g->n[2];
+    const bool periodic = (g->periodic_mask >> 2) & 1u;
+    const double dx = (g->hi[2] - g->lo[2]) / (periodic ? (double)n : (double)(n - 1));
+    if (ctx->trig_valid && ctx->trig_key[0] == (double)n && ctx->trig_key[1] == g->lo[2] && ctx->trig_key[2] == dx)
+        return HJ_OK;  // the tables on the device already hold these angles
+    std::vector<double> hd(2 * (size_t)n);
+    std::vector<float> hf(2 * (size_t)n);
+    for (int i = 0; i < n; ++i) {
+        const double x = g->lo[2] + (double)i * dx;
+        hd[i] = std::cos(x);
+        hd[n + i] = std::sin(x);
+        hf[i] = (float)hd[i];
+        hf[n + i] = (float)hd[n + i];
+    }
+    const size_t need = 2 * (size_t)n;
+    if (ctx->trig_cap < need) {
+        HJ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        cudaFree(ctx->trig_d);
+        cudaFree(ctx->trig_f);
+        ctx->trig_d = nullptr;
+        ctx->trig_f = nullptr;
+        ctx->trig_cap = 0;
+        HJ_CUDA(ctx, cudaMalloc(&ctx->trig_d, need * sizeof(double)));
+        HJ_CUDA(ctx, cudaMalloc(&ctx->trig_f, need * sizeof(float)));
+        ctx->trig_cap = need;
+    }
+    // copies ordered after earlier kernels on the stream; waited for because the host vectors die at return
+    ctx->trig_valid = false;
+    HJ_CUDA(ctx, cudaMemcpyAsync(ctx->trig_d, hd.data(), need * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    HJ_CUDA(ctx, cudaMemcpyAsync(ctx->trig_f, hf.data(), need * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    HJ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    ctx->trig_key[0] = (double)n;
+    ctx->trig_key[1] = g->lo[2];
+    ctx->trig_key[2] = dx;
+    ctx->trig_valid = true;
+    return HJ_OK;
+}
+
+StageParams stage_params(hj_ctx* ctx, const GridDev& G, const hj_method* m, int dtype) {
+    StageParams P;
+    std::memset(&P, 0, sizeof P);
+    P.g = G;
+    P.dynamics = m->dynamics;
+    for (int k = 0; k < 8; ++k) P.params[k] = m->params[k];
+    P.brt_min0 = (m->brt == HJ_BRT_MIN0);
+    P.trig_d = ctx->trig_d;
+    P.trig_f = ctx->trig_f;
+    P.weno_floor = weno_floor(G, dtype);
+    return P;
+}
+
+cudaError_t launch_stage(hj_ctx* ctx, const StageParams& P, int scheme, int dtype) {
+    ctx->launches += 1;
+    return dtype == HJ_F64 ? launch_stage_f64(P, scheme, ctx->stream) : launch_stage_f32(P, scheme, ctx->stream);
+}
+
+// Three fused stage launches of one TVD-RK3 step (Listing 6):
+//   V1 = V + dt L(V);  V2 = 3/4 V + 1/4 (V1 + dt L(V1));  V <- 1/3 V + 2/3 (V2 + dt L(V2))
+// with V <- min(V_new, V_old) in the last stage for the BRT min-V rule.
+hj_status rk3_launch(hj_ctx* ctx, StageParams P, int scheme, int dtype, int brt, void* v, double dt) {
+    P.mode = kStage;
+    P.dt = dt;
+    P.u = v; P.vn = nullptr; P.out = ctx->work[0]; P.cv = 0.0; P.cu = 1.0; P.minv_after = 0;
+    cudaError_t e = launch_stage(ctx, P, scheme, dtype);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "stage 1 launch");
+    P.u = ctx->work[0]; P.vn = v; P.out = ctx->work[1]; P.cv = 0.75; P.cu = 0.25;
+    e = launch_stage(ctx, P, scheme, dtype);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "stage 2 launch");
+    P.u = ctx->work[1]; P.vn = v; P.out = v; P.cv = 1.0 / 3.0; P.cu = 2.0 / 3.0;
+    P.minv_after = (brt == HJ_BRT_MINV);
+    e = launch_stage(ctx, P, scheme, dtype);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "stage 3 launch");
+    return HJ_OK;
+}
+
+hj_status step_bound(hj_ctx* ctx, const hj_grid* g, const hj_method* m, double* out) {
+    hj_status st = upload_trig(ctx, g, m->dynamics);
+    if (st) return st;
+    const GridDev G = make_grid(g, m->extrap);
+    HJ_CUDA(ctx, cudaMemsetAsync(ctx->aux, 0, sizeof(unsigned long long), ctx->stream));
+    cudaError_t e = launch_step_bound(G, m->dynamics, m->params, ctx->trig_d, ctx->aux, ctx->stream);
+    ctx->launches += 1;
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "step bound launch");
+    unsigned long long bits = 0;
+    HJ_CUDA(ctx, cudaMemcpyAsync(&bits, ctx->aux, sizeof bits, cudaMemcpyDeviceToHost, ctx->stream));
+    HJ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    double v;
+    std::memcpy(&v, &bits, sizeof v);
+    *out = v;
+    return HJ_OK;
+}
+
+hj_status nonfinite(hj_ctx* ctx, const void* v, long long n, int dtype, bool* bad) {
+    int* flag = reinterpret_cast<int*>(ctx->aux + 1);
+    HJ_CUDA(ctx, cudaMemsetAsync(flag, 0, sizeof(int), ctx->stream));
+    cudaError_t e = dtype == HJ_F64 ? launch_nonfinite_f64(static_cast<const double*>(v), n, flag, ctx->stream)
+                                    : launch_nonfinite_f32(static_cast<const float*>(v), n, flag, ctx->stream);
+    ctx->launches += 1;
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "non-finite check launch");
+    int h = 0;
+    HJ_CUDA(ctx, cudaMemcpyAsync(&h, flag, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
+    HJ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    *bad = h != 0;
+    return HJ_OK;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+const char* hj_version(void) { return "hj-gb300 0.1 sm_103a"; }
+
+const char* hj_status_str(hj_status s) {
+    switch (s) {
+    case HJ_OK: return "ok";
+    case HJ_EINVAL: return "invalid argument";
+    case HJ_ENOMEM: return "out of memory";
+    case HJ_ECUDA: return "CUDA error";
+    case HJ_ENONFINITE: return "non-finite value";
+    case HJ_ETIMEOUT: return "timed out";
+    case HJ_ECANCELLED: return "cancelled";
+    case HJ_EBUSY: return "busy";
+    default: return "unknown status";
+    }
+}
+
+const char* hj_ctx_last_error(const hj_ctx* ctx) { return ctx ? ctx->last_error.c_str() : "context is NULL"; }
+
+hj_status hj_ctx_create(int32_t device, void* cuda_stream, hj_ctx** out) {
+    if (!out) return HJ_EINVAL;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess) return HJ_ECUDA;
+    if (device < 0 || device >= count) return HJ_EINVAL;
+    hj_ctx* ctx = new (std::nothrow) hj_ctx();
+    if (!ctx) return HJ_ENOMEM;
+    ctx->device = device;
+    ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+    DeviceGuard guard(device);
+    if (cudaMalloc(&ctx->aux, 256) != cudaSuccess) {
+        delete ctx;
+        return HJ_ENOMEM;
+    }
+    *out = ctx;
+    return HJ_OK;
+}
+
+void hj_ctx_destroy(hj_ctx* ctx) {
+    if (!ctx) return;
+    DeviceGuard guard(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(ctx->work[0]);
+    cudaFree(ctx->work[1]);
+    cudaFree(ctx->state);
+    cudaFree(ctx->aux);
+    cudaFree(ctx->trig_d);
+    cudaFree(ctx->trig_f);
+    delete ctx;
+}
+
+hj_status hj_upwind(hj_ctx* ctx, const hj_grid* grid, const hj_method* method, int32_t dtype, const void* v,
+                    int32_t dim, void* pm, void* pp) {
+    if (!ctx) return HJ_EINVAL;
+    hj_status st = check_grid(ctx, grid);
+    if (st) return st;
+    if (!method) return fail(ctx, HJ_EINVAL, "method is NULL");
+    if (!elem_size(dtype)) return fail(ctx, HJ_EINVAL, "unknown dtype %d", dtype);
+    if (method->scheme != HJ_ENO1 && method->scheme != HJ_ENO2 && method->scheme != HJ_ENO3 &&
+        method->scheme != HJ_WENO5)
+        return fail(ctx, HJ_EINVAL, "unknown scheme %d", method->scheme);
+    if (method->extrap != HJ_EXTRAP_AWAY_FROM_ZERO && method->extrap != HJ_EXTRAP_LINEAR)
+        return fail(ctx, HJ_EINVAL, "unknown extrapolation %d", method->extrap);
+    if (dim < 0 || dim >= grid->ndim) return fail(ctx, HJ_EINVAL, "dim %d out of range", dim);
+    if (!v || !pm || !pp) return fail(ctx, HJ_EINVAL, "NULL array");
+    DeviceGuard guard(ctx->device);
+    UpwindParams P;
+    std::memset(&P, 0, sizeof P);
+    P.g = make_grid(grid, method->extrap);
+    P.dim = dim;
+    P.u = v;
+    P.pm = pm;
+    P.pp = pp;
+    P.weno_floor = weno_floor(P.g, dtype);
+    ctx->launches += 1;
+    cudaError_t e = dtype == HJ_F64 ? launch_upwind_f64(P, method->scheme, ctx->stream)
+                                    : launch_upwind_f32(P, method->scheme, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "upwind launch");
+    return HJ_OK;
+}
+
+hj_status hj_term(hj_ctx* ctx, const hj_grid* grid, const hj_method* method, int32_t dtype, const void* v,
+                  void* ydot) {
+    if (!ctx) return HJ_EINVAL;
+    hj_status st = check_grid(ctx, grid);
+    if (st) return st;
+    if ((st = check_method(ctx, grid, method))) return st;
+    if (!elem_size(dtype)) return fail(ctx, HJ_EINVAL, "unknown dtype %d", dtype);
+    if (!v || !ydot) return fail(ctx, HJ_EINVAL, "NULL array");
+    DeviceGuard guard(ctx->device);
+    if ((st = upload_trig(ctx, grid, method->dynamics))) return st;
+    StageParams P = stage_params(ctx, make_grid(grid, method->extrap), method, dtype);
+    P.mode = kTerm;
+    P.u = v;
+    P.out = ydot;
+    cudaError_t e = launch_stage(ctx, P, method->scheme, dtype);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "term launch");
+    return HJ_OK;
+}
+
+hj_status hj_step_bound(hj_ctx* ctx, const hj_grid* grid, const hj_method* method, double* out) {
+    if (!ctx) return HJ_EINVAL;
+    hj_status st = check_grid(ctx, grid);
+    if (st) return st;
+    if ((st = check_method(ctx, grid, method))) return st;
+    if (!out) return fail(ctx, HJ_EINVAL, "out is NULL");
+    DeviceGuard guard(ctx->device);
+    return step_bound(ctx, grid, method, out);
+}
+
+hj_status hj_rk3_step(hj_ctx* ctx, const hj_grid* grid, const hj_method* method, int32_t dtype, void* v,
+                      double dt) {
+    if (!ctx) return HJ_EINVAL;
+    hj_status st = check_grid(ctx, grid);
+    if (st) return st;
+    if ((st = check_method(ctx, grid, method))) return st;
+    if (!elem_size(dtype)) return fail(ctx, HJ_EINVAL, "unknown dtype %d", dtype);
+    if (!v) return fail(ctx, HJ_EINVAL, "NULL array");
+    if (!(dt >= 0.0) || !std::isfinite(dt)) return fail(ctx, HJ_EINVAL, "dt must be finite and >= 0");
+    DeviceGuard guard(ctx->device);
+    const GridDev G = make_grid(grid, method->extrap);
+    if ((st = ensure_work(ctx, (size_t)G.total * elem_size(dtype)))) return st;
+    if ((st = upload_trig(ctx, grid, method->dynamics))) return st;
+    StageParams P = stage_params(ctx, G, method, dtype);
+    return rk3_launch(ctx, P, method->scheme, dtype, method->brt, v, dt);
+}
+
+hj_status hj_rk3_stage(hj_ctx* ctx, const hj_grid* grid, const hj_method* method, int32_t dtype, int32_t stage,
+                       const void* u, const void* vn, void* out, double dt) {
+    if (!ctx) return HJ_EINVAL;
+    hj_status st = check_grid(ctx, grid);
+    if (st) return st;
+    if ((st = check_method(ctx, grid, method))) return st;
+    if (!elem_size(dtype)) return fail(ctx, HJ_EINVAL, "unknown dtype %d", dtype);
+    if (stage < 1 || stage > 3) return fail(ctx, HJ_EINVAL, "stage %d not in 1..3", stage);
+    if (!u || !out || (stage > 1 && !vn)) return fail(ctx, HJ_EINVAL, "NULL array");
+    if (out == u) return fail(ctx, HJ_EINVAL, "out must not alias u");
+    if (!(dt >= 0.0) || !std::isfinite(dt)) return fail(ctx, HJ_EINVAL, "dt must be finite and >= 0");
+    DeviceGuard guard(ctx->device);
+    if ((st = upload_trig(ctx, grid, method->dynamics))) return st;
+    StageParams P = stage_params(ctx, make_grid(grid, method->extrap), method, dtype);
+    P.mode = kStage;
+    P.dt = dt;
+    P.u = u;
+    P.vn = vn;
+    P.out = out;
+    P.cv = stage == 1 ? 0.0 : (stage == 2 ? 0.75 : 1.0 / 3.0);
+    P.cu = stage == 1 ? 1.0 : (stage == 2 ? 0.25 : 2.0 / 3.0);
+    P.minv_after = (stage == 3 && method->brt == HJ_BRT_MINV);
+    cudaError_t e = launch_stage(ctx, P, method->scheme, dtype);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "stage launch");
+    return HJ_OK;
+}
+
+hj_status hj_solve(hj_ctx* ctx, const hj_problem* pr, void* out_slices, int32_t out_on_device, double* out_times,
+                   hj_stats* stats) {
+    if (!ctx) return HJ_EINVAL;
+    const auto t0 = std::chrono::steady_clock::now();
+    if (!pr) return fail(ctx, HJ_EINVAL, "problem is NULL");
+    hj_status st = check_grid(ctx, &pr->grid);
+    if (st) return st;
+    if ((st = check_method(ctx, &pr->grid, &pr->method))) return st;
+    if ((st = check_solver_settings(ctx, &pr->method))) return st;
+    const size_t es = elem_size(pr->dtype);
+    if (!es) return fail(ctx, HJ_EINVAL, "unknown dtype %d", pr->dtype);
+    if (!pr->v0 || !out_slices) return fail(ctx, HJ_EINVAL, "NULL v0 or output");
+    if (pr->n_slices < 1 || !pr->slice_times) return fail(ctx, HJ_EINVAL, "need at least one slice time");
+    for (int s = 0; s < pr->n_slices; ++s) {
+        const double ts = pr->slice_times[s];
+        if (!(ts >= 0.0) || !std::isfinite(ts)) return fail(ctx, HJ_EINVAL, "slice time %d invalid", s);
+        if (s > 0 && ts < pr->slice_times[s - 1]) return fail(ctx, HJ_EINVAL, "slice times must not decrease");
+    }
+    DeviceGuard guard(ctx->device);
+    const GridDev G = make_grid(&pr->grid, pr->method.extrap);
+    const size_t bytes = (size_t)G.total * es;
+    const long long launches0 = ctx->launches;
+    if ((st = ensure_work(ctx, bytes))) return st;
+    if ((st = ensure(ctx, &ctx->state, &ctx->state_bytes, bytes))) return st;
+    void* V = ctx->state;
+    HJ_CUDA(ctx, cudaMemcpyAsync(V, pr->v0, bytes, pr->v0_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                 ctx->stream));
+    bool bad = false;
+    if ((st = nonfinite(ctx, V, G.total, pr->dtype, &bad))) return st;
+    if (bad) return fail(ctx, HJ_ENONFINITE, "v0 holds NaN or Inf");
+    double sbi = 0.0;
+    if ((st = step_bound(ctx, &pr->grid, &pr->method, &sbi))) return st;  // also uploads the angle tables
+    StageParams P = stage_params(ctx, G, &pr->method, pr->dtype);
+    // Listing 6: dt = min(t_f - t, maxStep, cfl * stepBound), stepBound = 1/stepBoundInv;
+    // alpha depends on x only, so stepBound is the same at every step.
+    const double step_bound_v = 1.0 / sbi;
+    const double eps = 100.0 * DBL_EPSILON;
+    double t = 0.0;
+    long long steps = 0;
+    const cudaMemcpyKind out_kind = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    for (int s = 0; s < pr->n_slices; ++s) {
+        const double ts = pr->slice_times[s];
+        while (ts > t && ts - t >= eps * ts) {
+            double dt = ts - t;
+            if (pr->method.max_step < dt) dt = pr->method.max_step;
+            if (pr->method.cfl * step_bound_v < dt) dt = pr->method.cfl * step_bound_v;
+            if ((st = rk3_launch(ctx, P, pr->method.scheme, pr->dtype, pr->method.brt, V, dt))) return st;
+            t += dt;
+            ++steps;
+        }
+        HJ_CUDA(ctx, cudaMemcpyAsync(static_cast<char*>(out_slices) + (size_t)s * bytes, V, bytes, out_kind,
+                                     ctx->stream));
+        if (out_times) out_times[s] = t;
+    }
+    if ((st = nonfinite(ctx, V, G.total, pr->dtype, &bad))) return st;  // synchronises the stream
+    if (bad) return fail(ctx, HJ_ENONFINITE, "the solution became non-finite");
+    if (stats) {
+        stats->steps = steps;
+        stats->cell_updates = steps * G.total;
+        stats->kernel_launches = ctx->launches - launches0;
+        stats->step_bound_inv = sbi;
+        stats->t_final = t;
+        stats->elapsed_ms =
+            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return HJ_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,72 @@
+// hj_internal.h -- host/device shared declarations of the GB300 level-set
+// library (not part of the public ABI; the ABI is include/hj.h).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace hj {
+
+constexpr int kMaxDim = 4;
+
+// Grid as the kernels see it. Spacing and its inverse are computed once on
+// the host from the hj_grid (periodic: (hi-lo)/n, else (hi-lo)/(n-1)).
+struct GridDev {
+    int ndim;
+    int n[kMaxDim];
+    long long stride[kMaxDim];
+    long long total;
+    double lo[kMaxDim];
+    double dx[kMaxDim];
+    double inv_dx[kMaxDim];
+    unsigned periodic_mask;
+    int extrap;  // HJ_EXTRAP_*
+};
+
+// What one launch of the fused stage kernel computes at every node:
+//   w   = U + dt * ydot(U)            (mode kStage*)  or  w = ydot(U)  (mode kTerm)
+//   out = cv * Vn + cu * w            (cv == 0: out = w)
+//   out = min(out, Vn)                (minv_after: BRT "min(V, V_prev)" rule)
+enum StageMode { kTerm = 0, kStage = 1 };
+
+struct StageParams {
+    GridDev g;
+    int dynamics;
+    double params[8];
+    int brt_min0;     // clamp ydot at zero (BRT min(0, H))
+    int minv_after;   // out = min(out, Vn)
+    int mode;         // StageMode
+    double dt;
+    double cv, cu;    // stage combination coefficients
+    const void* u;    // stencil input
+    const void* vn;   // V^n (read at the node only); may be null when cv == 0 and !minv_after
+    void* out;
+    const double* trig_d;  // cos, sin of the dimension-2 coordinate: [cos(0..n2-1), sin(0..n2-1)]
+    const float* trig_f;
+    double weno_floor;     // additive floor of the WENO5 epsilon, in raw-difference units
+};
+
+struct UpwindParams {
+    GridDev g;
+    int dim;
+    const void* u;
+    void* pm;
+    void* pp;
+    double weno_floor;
+};
+
+// Launchers (one translation unit per element type). Return the launch error.
+cudaError_t launch_stage_f64(const StageParams& p, int scheme, cudaStream_t s);
+cudaError_t launch_stage_f32(const StageParams& p, int scheme, cudaStream_t s);
+cudaError_t launch_upwind_f64(const UpwindParams& p, int scheme, cudaStream_t s);
+cudaError_t launch_upwind_f32(const UpwindParams& p, int scheme, cudaStream_t s);
+
+// max over nodes of sum_d alpha_d(x)/dx_d, as the FP64 bit pattern, atomically
+// max-ed into *acc (which the caller zeroes first).
+cudaError_t launch_step_bound(const GridDev& g, int dynamics, const double* params, const double* trig_d,
+                              unsigned long long* acc, cudaStream_t s);
+// Sets *flag to 1 if any of the n elements is NaN or +-Inf.
+cudaError_t launch_nonfinite_f64(const double* v, long long n, int* flag, cudaStream_t s);
+cudaError_t launch_nonfinite_f32(const float* v, long long n, int* flag, cudaStream_t s);
+
+}  // namespace hj

@@ -1,0 +1,125 @@
+// reduce.cu -- grid-wide reductions: the FP64 CFL bound (Sec. 4) and the
+// non-finite check of value functions.
+#include <cstdint>
+
+#include "../../include/hj.h"
+#include "hj_internal.h"
+
+namespace hj {
+
+// alpha_d(x)/dx_d summed over d, in FP64, with every product and sum rounded
+// separately in the order alpha_0/dx_0 + alpha_1/dx_1 + ..., so that the bound
+// equals the plain left-to-right evaluation bit for bit.
+__device__ double node_bound(const GridDev& g, int dyn, const double* q, const double* trig, const int* idx) {
+    double x[4];
+    for (int d = 0; d < g.ndim; ++d) x[d] = __dadd_rn(g.lo[d], __dmul_rn((double)idx[d], g.dx[d]));
+    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    switch (dyn) {
+    case HJ_DYN_DOUBLE_INTEGRATOR:
+        a[0] = fabs(x[1]);
+        a[1] = q[0];
+        break;
+    case HJ_DYN_AIR3D: {
+        const double c = trig[idx[2]], s = trig[g.n[2] + idx[2]];
+        a[0] = __dadd_rn(fabs(__dadd_rn(-q[0], __dmul_rn(q[1], c))), __dmul_rn(q[2], fabs(x[1])));
+        a[1] = __dadd_rn(fabs(__dmul_rn(q[1], s)), __dmul_rn(q[2], fabs(x[0])));
+        a[2] = __dadd_rn(q[2], q[3]);
+        break;
+    }
+    case HJ_DYN_DUBINS4D: {
+        const double c = trig[idx[2]], s = trig[g.n[2] + idx[2]];
+        a[0] = fabs(__dmul_rn(x[3], c));
+        a[1] = fabs(__dmul_rn(x[3], s));
+        a[2] = q[0];
+        a[3] = q[1];
+        break;
+    }
+    case HJ_DYN_NORM:
+        for (int d = 0; d < g.ndim; ++d) a[d] = q[0];
+        break;
+    case HJ_DYN_ADVECT:
+        for (int d = 0; d < g.ndim; ++d) a[d] = fabs(q[d]);
+        break;
+    case HJ_DYN_ROTATE:
+        a[0] = fabs(__dmul_rn(q[0], x[1]));
+        a[1] = fabs(__dmul_rn(q[0], x[0]));
+        break;
+    default:
+        break;
+    }
+    double s = 0.0;
+    for (int d = 0; d < g.ndim; ++d) s = __dadd_rn(s, __ddiv_rn(a[d], g.dx[d]));
+    return s;
+}
+
+struct BoundArgs {
+    GridDev g;
+    int dyn;
+    double q[8];
+    const double* trig;
+    unsigned long long* acc;
+};
+
+__global__ void __launch_bounds__(256) step_bound_kernel(const BoundArgs A) {
+    double best = 0.0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long flat = (long long)blockIdx.x * blockDim.x + threadIdx.x; flat < A.g.total; flat += stride) {
+        int idx[4] = {0, 0, 0, 0};
+        long long r = flat;
+        for (int d = 0; d < A.g.ndim; ++d) { idx[d] = (int)(r % A.g.n[d]); r /= A.g.n[d]; }
+        best = fmax(best, node_bound(A.g, A.dyn, A.q, A.trig, idx));
+    }
+    for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
+    __shared__ double warp_best[8];
+    if ((threadIdx.x & 31) == 0) warp_best[threadIdx.x >> 5] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = warp_best[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) b = fmax(b, warp_best[w]);
+        // non-negative doubles order like their bit patterns
+        atomicMax(A.acc, (unsigned long long)__double_as_longlong(b));
+    }
+}
+
+cudaError_t launch_step_bound(const GridDev& g, int dynamics, const double* params, const double* trig_d,
+                              unsigned long long* acc, cudaStream_t s) {
+    BoundArgs A;
+    A.g = g;
+    A.dyn = dynamics;
+    for (int k = 0; k < 8; ++k) A.q[k] = params[k];
+    A.trig = trig_d;
+    A.acc = acc;
+    long long blocks = (g.total + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) blocks = 1;
+    step_bound_kernel<<<(unsigned)blocks, 256, 0, s>>>(A);
+    return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) nonfinite_kernel(const T* __restrict__ v, long long n, int* flag) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    int bad = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        bad |= !isfinite(v[i]);
+    bad = __syncthreads_or(bad);
+    if (bad && threadIdx.x == 0) atomicOr(flag, 1);
+}
+
+template <typename T>
+static cudaError_t launch_nonfinite(const T* v, long long n, int* flag, cudaStream_t s) {
+    long long blocks = (n + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks < 1) blocks = 1;
+    nonfinite_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(v, n, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_nonfinite_f64(const double* v, long long n, int* flag, cudaStream_t s) {
+    return launch_nonfinite<double>(v, n, flag, s);
+}
+cudaError_t launch_nonfinite_f32(const float* v, long long n, int* flag, cudaStream_t s) {
+    return launch_nonfinite<float>(v, n, flag, s);
+}
+
+}  // namespace hj

@@ -1,0 +1,271 @@
+// stencil.cuh -- device building blocks of the fused level-set stage kernel:
+// ghost-aware 7-point line gathers (Sec. 2.1), upwind derivatives ENO1/2/3
+// and WENO5 (Sec. 3.1-3.3), Hamiltonians with Lax-Friedrichs dissipation
+// (Sec. 4) for each supported dynamics.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/hj.h"
+#include "hj_internal.h"
+
+namespace hj {
+
+template <typename T> __device__ __forceinline__ T ld(const T* p) { return __ldg(p); }
+
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+
+template <typename T> __device__ __forceinline__ T sgn(T v) {
+    return (v > T(0)) ? T(1) : ((v < T(0)) ? T(-1) : T(0));
+}
+
+// Values at nodes i-3 .. i+3 along one grid line (stride s, n nodes, node i
+// at flat index idx). Off-grid nodes come from the ghost rule of the
+// dimension: periodic wrap, or the outermost slope continued outward
+// (away from the zero level set by default).
+template <typename T>
+__device__ __forceinline__ void gather7(const T* __restrict__ u, long long idx, int i, int n, long long s,
+                                        bool periodic, int extrap, T v[7]) {
+    if (i >= 3 && i + 3 < n) {
+#pragma unroll
+        for (int k = 0; k < 7; ++k) v[k] = ld(u + idx + (long long)(k - 3) * s);
+        return;
+    }
+    const long long base = idx - (long long)i * s;
+    if (periodic) {
+#pragma unroll
+        for (int k = 0; k < 7; ++k) {
+            int j = (i + k - 3) % n;
+            if (j < 0) j += n;
+            v[k] = ld(u + base + (long long)j * s);
+        }
+        return;
+    }
+    const T e0 = ld(u + base), e1 = ld(u + base + s);
+    const T f0 = ld(u + base + (long long)(n - 1) * s), f1 = ld(u + base + (long long)(n - 2) * s);
+    const T slo = (extrap == HJ_EXTRAP_LINEAR) ? (e0 - e1) : fabs(e0 - e1) * sgn(e0);
+    const T shi = (extrap == HJ_EXTRAP_LINEAR) ? (f0 - f1) : fabs(f0 - f1) * sgn(f0);
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+        const int j = i + k - 3;
+        // product and sum rounded separately (no contraction), as in edge + m * slope
+        if (j < 0) v[k] = add_rn(e0, mul_rn(T(-j), slo));
+        else if (j >= n) v[k] = add_rn(f0, mul_rn(T(j - n + 1), shi));
+        else v[k] = ld(u + base + (long long)j * s);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// WENO5 (Sec. 3.3; Jiang & Peng 2000). Inputs are raw one-sided differences
+// r_j = v_{j+1} - v_j (not yet divided by dx) around node i:
+//   r0 = v_{i-2}-v_{i-3}, ..., r5 = v_{i+3}-v_{i+2}.
+// p- uses (r0, r1, r2, r3, r4); p+ the mirrored (r5, r4, r3, r2, r1). The
+// weights are homogeneous of degree zero in the differences, so working on
+// raw differences and dividing by dx once at the end is the same scheme when
+// the epsilon floor is scaled by dx^2 (weno_floor).
+// The two sides share the second differences of windows (r1,r2,r3) and
+// (r2,r3,r4) and two of their candidate stencils.
+// ---------------------------------------------------------------------------
+// FP64: weights c_k/(S_k+eps)^2 normalised with one division,
+//   p = sum_k c_k q_k prod_{j!=k} d_j / sum_k c_k prod_{j!=k} d_j,  d_k = (S_k+eps)^2.
+// On exactly flat data every d_k underflows and every q_k is zero: return q2.
+__device__ __forceinline__ double weno_combine(double q1, double q2, double q3, double s1, double s2, double s3,
+                                               double eps, double scale) {
+    const double d1 = (s1 + eps) * (s1 + eps);
+    const double d2 = (s2 + eps) * (s2 + eps);
+    const double d3 = (s3 + eps) * (s3 + eps);
+    const double w1 = 0.1 * (d2 * d3);
+    const double w2 = 0.6 * (d1 * d3);
+    const double w3 = 0.3 * (d1 * d2);
+    const double num = w1 * q1 + w2 * q2 + w3 * q3;
+    const double den = w1 + w2 + w3;
+    return (den > 0.0) ? num / (den * scale) : q2 / scale;
+}
+
+// FP32: the epsilon floor keeps (S+eps)^2 >= 1e-36 (normal), so the direct
+// form with fast reciprocals cannot overflow or divide by zero.
+__device__ __forceinline__ float weno_combine(float q1, float q2, float q3, float s1, float s2, float s3,
+                                              float eps, float scale) {
+    const float a1 = 0.1f * __fdividef(1.0f, (s1 + eps) * (s1 + eps));
+    const float a2 = 0.6f * __fdividef(1.0f, (s2 + eps) * (s2 + eps));
+    const float a3 = 0.3f * __fdividef(1.0f, (s3 + eps) * (s3 + eps));
+    const float num = a1 * q1 + a2 * q2 + a3 * q3;
+    return num * __fdividef(1.0f, (a1 + a2 + a3) * scale);
+}
+
+template <typename T>
+__device__ __forceinline__ void weno5_pair(const T v[7], T dx, T floor_raw, T& pm, T& pp) {
+    const T r0 = v[1] - v[0], r1 = v[2] - v[1], r2 = v[3] - v[2];
+    const T r3 = v[4] - v[3], r4 = v[5] - v[4], r5 = v[6] - v[5];
+    const T c13 = T(13) / T(12);
+    // second differences of the four windows
+    const T tA = r0 - T(2) * r1 + r2;  // (r0, r1, r2)
+    const T tB = r1 - T(2) * r2 + r3;  // (r1, r2, r3)
+    const T tC = r2 - T(2) * r3 + r4;  // (r2, r3, r4)
+    const T tD = r3 - T(2) * r4 + r5;  // (r3, r4, r5)
+    // left side: v1..v5 = r0..r4
+    const T uL1 = r0 - T(4) * r1 + T(3) * r2;
+    const T uL2 = r1 - r3;
+    const T uL3 = T(3) * r2 - T(4) * r3 + r4;
+    const T sL1 = c13 * tA * tA + T(0.25) * uL1 * uL1;
+    const T sL2 = c13 * tB * tB + T(0.25) * uL2 * uL2;
+    const T sL3 = c13 * tC * tC + T(0.25) * uL3 * uL3;
+    // right side: v1..v5 = r5..r1
+    const T uR1 = r5 - T(4) * r4 + T(3) * r3;
+    const T uR2 = r4 - r2;
+    const T uR3 = T(3) * r3 - T(4) * r2 + r1;
+    const T sR1 = c13 * tD * tD + T(0.25) * uR1 * uR1;
+    const T sR2 = c13 * tC * tC + T(0.25) * uR2 * uR2;
+    const T sR3 = c13 * tB * tB + T(0.25) * uR3 * uR3;
+    // candidates, times 6
+    const T qL1 = T(2) * r0 - T(7) * r1 + T(11) * r2;
+    const T qL2 = -r1 + T(5) * r2 + T(2) * r3;   // = qR3
+    const T qL3 = T(2) * r2 + T(5) * r3 - r4;    // = qR2
+    const T qR1 = T(2) * r5 - T(7) * r4 + T(11) * r3;
+    // epsilon = 1e-6 max(v_k^2) + floor
+    const T m14 = fmax(fmax(r1 * r1, r2 * r2), fmax(r3 * r3, r4 * r4));
+    const T epsL = T(1e-6) * fmax(m14, r0 * r0) + floor_raw;
+    const T epsR = T(1e-6) * fmax(m14, r5 * r5) + floor_raw;
+    const T scale = T(6) * dx;  // undo the candidates' factor 6 and divide by dx
+    pm = weno_combine(qL1, qL2, qL3, sL1, sL2, sL3, epsL, scale);
+    pp = weno_combine(qR1, qL3, qL2, sR1, sR2, sR3, epsR, scale);
+}
+
+// ---------------------------------------------------------------------------
+// ENO1/2/3 (Sec. 3.1-3.2; Osher & Fedkiw Sec. 3.3) from the divided
+// differences D1_{j+1/2} = (v_{j+1}-v_j)/dx, D2_j = (D1_{j+1/2}-D1_{j-1/2})/(2dx),
+// D3_{j+1/2} = (D2_{j+1}-D2_j)/(3dx). Divisions (not reciprocal products)
+// keep the stencil choices identical to the plain definition; a tie picks
+// the left candidate.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void eno_pair(const T v[7], T dx, int order, T& pm, T& pp) {
+    T D1[6];  // D1[k] = D^1_{i-5/2+k}
+#pragma unroll
+    for (int k = 0; k < 6; ++k) D1[k] = (v[k + 1] - v[k]) / dx;
+    if (order == 1) { pm = D1[2]; pp = D1[3]; return; }
+    T D2[5];  // D2[k] = D^2_{i-2+k}
+#pragma unroll
+    for (int k = 0; k < 5; ++k) D2[k] = (D1[k + 1] - D1[k]) / (T(2) * dx);
+    T D3[4];  // D3[k] = D^3_{i-3/2+k}
+#pragma unroll
+    for (int k = 0; k < 4; ++k) D3[k] = (D2[k + 1] - D2[k]) / (T(3) * dx);
+    // left: stencil start k = i-1, so D2_k = D2[1], D2_{k+1} = D2[2]
+    {
+        const bool left = fabs(D2[1]) <= fabs(D2[2]);
+        const T c = left ? D2[1] : D2[2];
+        T p = D1[2] + c * dx;
+        if (order == 3) {
+            // k* = i-2 (left) or i-1; D3_{k*+1/2} = D3[k*-(i-2)], coefficient 3r^2-6r+2 at r = i-k*
+            const T a = left ? D3[0] : D3[1];
+            const T b = left ? D3[1] : D3[2];
+            const T cs = (fabs(a) <= fabs(b)) ? a : b;
+            const T coef = left ? T(2) : T(-1);
+            p += cs * coef * dx * dx;
+        }
+        pm = p;
+    }
+    // right: stencil start k = i, D2_k = D2[2], D2_{k+1} = D2[3]
+    {
+        const bool left = fabs(D2[2]) <= fabs(D2[3]);
+        const T c = left ? D2[2] : D2[3];
+        T p = D1[3] - c * dx;
+        if (order == 3) {
+            // k* = i-1 (left) or i
+            const T a = left ? D3[1] : D3[2];
+            const T b = left ? D3[2] : D3[3];
+            const T cs = (fabs(a) <= fabs(b)) ? a : b;
+            const T coef = left ? T(-1) : T(2);
+            p += cs * coef * dx * dx;
+        }
+        pp = p;
+    }
+}
+
+template <typename T, int SCHEME>
+__device__ __forceinline__ void upwind_pair(const T v[7], double dx, double inv_dx, T floor_raw, T& pm, T& pp) {
+    if constexpr (SCHEME == HJ_WENO5) {
+        weno5_pair<T>(v, T(dx), floor_raw, pm, pp);
+    } else {
+        eno_pair<T>(v, T(dx), SCHEME, pm, pp);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Hamiltonian + Lax-Friedrichs dissipation (Sec. 4):
+//   ydot = Hg(x, (p- + p+)/2) + sum_d alpha_d(x) (p+_d - p-_d)/2
+// ---------------------------------------------------------------------------
+template <typename T> struct Trig;
+template <> struct Trig<double> { static __device__ __forceinline__ const double* get(const StageParams& P) { return P.trig_d; } };
+template <> struct Trig<float>  { static __device__ __forceinline__ const float*  get(const StageParams& P) { return P.trig_f; } };
+
+template <typename T, int D>
+__device__ __forceinline__ T lf_term(const StageParams& P, const int* idx, const T* pm, const T* pp) {
+    T pb[D], dd[D], x[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        pb[d] = T(0.5) * (pm[d] + pp[d]);
+        dd[d] = T(0.5) * (pp[d] - pm[d]);
+        x[d] = T(P.g.lo[d] + (double)idx[d] * P.g.dx[d]);
+    }
+    const double* q = P.params;
+    T y = T(0);
+    switch (P.dynamics) {
+    case HJ_DYN_DOUBLE_INTEGRATOR:
+        if constexpr (D == 2) {
+            const T umax = T(q[0]);
+            y = pb[0] * x[1] - umax * fabs(pb[1]) + fabs(x[1]) * dd[0] + umax * dd[1];
+        }
+        break;
+    case HJ_DYN_AIR3D:
+        if constexpr (D == 3) {
+            const T* tr = Trig<T>::get(P);
+            const T c = tr[idx[2]], s = tr[P.g.n[2] + idx[2]];
+            const T va = T(q[0]), vb = T(q[1]), amax = T(q[2]), bmax = T(q[3]);
+            const T f0 = -va + vb * c, f1 = vb * s;
+            y = pb[0] * f0 + pb[1] * f1 + amax * fabs(pb[0] * x[1] - pb[1] * x[0] - pb[2]) - bmax * fabs(pb[2]);
+            y += (fabs(f0) + amax * fabs(x[1])) * dd[0] + (fabs(f1) + amax * fabs(x[0])) * dd[1] +
+                 (amax + bmax) * dd[2];
+        }
+        break;
+    case HJ_DYN_DUBINS4D:
+        if constexpr (D == 4) {
+            const T* tr = Trig<T>::get(P);
+            const T c = tr[idx[2]], s = tr[P.g.n[2] + idx[2]];
+            const T wmax = T(q[0]), accmax = T(q[1]);
+            const T f0 = x[3] * c, f1 = x[3] * s;
+            y = pb[0] * f0 + pb[1] * f1 - wmax * fabs(pb[2]) - accmax * fabs(pb[3]);
+            y += fabs(f0) * dd[0] + fabs(f1) * dd[1] + wmax * dd[2] + accmax * dd[3];
+        }
+        break;
+    case HJ_DYN_NORM: {
+        const T c = T(q[0]);
+        T s2 = T(0), diss = T(0);
+#pragma unroll
+        for (int d = 0; d < D; ++d) { s2 += pb[d] * pb[d]; diss += dd[d]; }
+        y = -c * sqrt(s2) + c * diss;
+        break;
+    }
+    case HJ_DYN_ADVECT: {
+#pragma unroll
+        for (int d = 0; d < D; ++d) { const T c = T(q[d]); y += -c * pb[d] + fabs(c) * dd[d]; }
+        break;
+    }
+    case HJ_DYN_ROTATE:
+        if constexpr (D >= 2) {
+            const T w = T(q[0]);
+            const T f0 = -w * x[1], f1 = w * x[0];
+            y = -(pb[0] * f0 + pb[1] * f1) + fabs(f0) * dd[0] + fabs(f1) * dd[1];
+        }
+        break;
+    default:
+        break;
+    }
+    return y;
+}
+
+}  // namespace hj

@@ -1,0 +1,110 @@
+"""Torch-tensor convenience layer over the C ABI (argument marshalling only).
+
+Grid arrays are flat contiguous tensors of prod(n) elements, dimension 0
+fastest. Every call runs in libhj.so on the context's stream.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import _lib as L
+
+
+class Context:
+    """An hj_ctx bound to one device and a torch stream (default: the current one)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+        self.device = int(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.handle = L.hj_ctx_create(self.device, self.stream.cuda_stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            L.hj_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def method(scheme=L.HJ_WENO5, dynamics=L.HJ_DYN_DOUBLE_INTEGRATOR, params=(), brt=L.HJ_BRT_MIN0,
+           extrap=L.HJ_EXTRAP_AWAY_FROM_ZERO, cfl=0.8, max_step=math.inf) -> L.hj_method:
+    return L.make_method(scheme, dynamics, params, brt, extrap, cfl, max_step)
+
+
+def _check_tensor(t, spec, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or not t.is_contiguous():
+        raise ValueError("%s must be a contiguous CUDA tensor" % name)
+    if t.numel() != int(np.prod(spec.n)):
+        raise ValueError("%s has %d elements, the grid %d" % (name, t.numel(), int(np.prod(spec.n))))
+
+
+def upwind(ctx: Context, spec, m: L.hj_method, V, dim: int):
+    import torch
+    _check_tensor(V, spec, "V")
+    pm, pp = torch.empty_like(V), torch.empty_like(V)
+    L.hj_upwind(ctx.handle, L.make_grid(spec), m, L.dtype_code(V.dtype), V, dim, pm, pp)
+    return pm, pp
+
+
+def term(ctx: Context, spec, m: L.hj_method, V):
+    import torch
+    _check_tensor(V, spec, "V")
+    y = torch.empty_like(V)
+    L.hj_term(ctx.handle, L.make_grid(spec), m, L.dtype_code(V.dtype), V, y)
+    return y
+
+
+def step_bound(ctx: Context, spec, m: L.hj_method) -> float:
+    return L.hj_step_bound(ctx.handle, L.make_grid(spec), m)
+
+
+def rk3_step(ctx: Context, spec, m: L.hj_method, V, dt: float):
+    """One TVD-RK3 step in place on V."""
+    _check_tensor(V, spec, "V")
+    L.hj_rk3_step(ctx.handle, L.make_grid(spec), m, L.dtype_code(V.dtype), V, dt)
+    return V
+
+
+def rk3_stage(ctx: Context, spec, m: L.hj_method, stage: int, u, vn, out, dt: float):
+    """One fused RK3 stage: out = cv*vn + cu*(u + dt*L(u)) (stage 1: out = u + dt*L(u))."""
+    _check_tensor(u, spec, "u")
+    _check_tensor(out, spec, "out")
+    L.hj_rk3_stage(ctx.handle, L.make_grid(spec), m, L.dtype_code(u.dtype), stage, u, vn, out, dt)
+    return out
+
+
+def solve(ctx: Context, spec, m: L.hj_method, V0, slice_times, out=None):
+    """Integrate V0 through the slice times.
+
+    V0: flat CUDA tensor, or a host tensor (pinned memory recommended).
+    out: optional tensor [n_slices, prod(n)] of V0's dtype (device or host).
+    Returns (out, times_reached, stats_dict).
+    """
+    import torch
+    ts = np.ascontiguousarray(slice_times, dtype=np.float64)
+    N = int(np.prod(spec.n))
+    if V0.numel() != N or not V0.is_contiguous():
+        raise ValueError("V0 must be contiguous with prod(n) elements")
+    if out is None:
+        out = torch.empty((ts.size, N), dtype=V0.dtype, device=V0.device)
+    if out.dtype != V0.dtype or out.numel() != ts.size * N or not out.is_contiguous():
+        raise ValueError("out must be a contiguous [n_slices, prod(n)] tensor of V0's dtype")
+    prob, keep = L.make_problem(spec, m, L.dtype_code(V0.dtype), int(V0.data_ptr()), V0.is_cuda, ts)
+    times = np.zeros(ts.size)
+    stats = L.hj_solve(ctx.handle, prob, int(out.data_ptr()), out.is_cuda, times)
+    del keep
+    return out, times, stats.as_dict()

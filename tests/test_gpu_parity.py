@@ -1,0 +1,280 @@
+"""GPU parity of every hot-path row against the FP64 CPU oracle, through the C ABI.
+
+FP64 bar: max|GPU - oracle| / max|oracle| <= 1e-12 (bit-exact where the value
+is an exact max, e.g. the CFL bound). FP32 bar: zero level set within 0.1
+cell of the FP64 oracle; max|dV| is checked against a stated bound.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2507_11542_gb300 import workloads as W
+
+from helpers import (ADVECT, AIR3D, DI, DUBINS, NORM, PARAMS, ROTATE, lib_method, oracle_method,
+                     oracle_window_step, rel_err, to_dev, to_host, zero_set_displacement)
+
+pytestmark = pytest.mark.gpu
+TOL64 = 1e-12
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    from paper_2507_11542_gb300 import build, solver
+    build.build()
+    assert torch.cuda.is_available()
+    c = solver.Context(0)
+    yield c
+    c.close()
+
+
+# ragged grids spanning several thread blocks, every boundary kind
+SPECS = {
+    DI: W.GridSpec((37, 29), (-1.0, -1.0), (1.0, 1.0)),
+    AIR3D: W.GridSpec((35, 19, 16), (-6.0, -10.0, 0.0), (20.0, 10.0, 2 * math.pi), (2,)),
+    DUBINS: W.GridSpec((13, 11, 9, 7), (-5.0, -5.0, 0.0, 0.0), (5.0, 5.0, 2 * math.pi, 2.0), (2,)),
+    NORM: W.GridSpec((21, 18, 9), (-1.0, -1.0, -1.0), (1.0, 1.0, 1.0), (1,)),
+    ADVECT: W.GridSpec((70,), (0.0,), (1.0,), (0,)),
+    ROTATE: W.GridSpec((33, 40), (-1.0, -1.0), (1.0, 1.0)),
+}
+
+
+def _field(spec, seed):
+    # generic smooth data plus a distance function: tie-free for the ENO selectors
+    X = spec.mesh()
+    V = W.random_field(spec, seed) + 0.3 * np.sqrt(sum((x - 0.1) ** 2 for x in X))
+    return np.asfortranarray(V)
+
+
+@pytest.mark.parametrize("scheme", [1, 2, 3, 5])
+@pytest.mark.parametrize("extrap", [0, 1])
+def test_upwind_parity_fp64(ctx, scheme, extrap):
+    from paper_2507_11542_gb300 import solver
+    spec = W.GridSpec((45, 17, 11), (-1.0, 0.0, 0.0), (2.0, 1.0, 2 * math.pi), (2,))
+    V = _field(spec, 3)
+    m_o = oracle_method(scheme=scheme, dynamics=NORM, extrap=extrap)
+    m_l = lib_method(scheme=scheme, dynamics=NORM, extrap=extrap)
+    Vd = to_dev(V)
+    for d in range(3):
+        pm_o, pp_o = O.upwind(spec, m_o, V, d)
+        pm, pp = solver.upwind(ctx, spec, m_l, Vd, d)
+        assert rel_err(to_host(pm, spec.n), pm_o) <= TOL64
+        assert rel_err(to_host(pp, spec.n), pp_o) <= TOL64
+
+
+@pytest.mark.parametrize("scheme", [1, 2, 3, 5])
+def test_upwind_parity_fp32(ctx, scheme):
+    from paper_2507_11542_gb300 import solver
+    spec = W.GridSpec((64, 33), (-1.0, -1.0), (1.0, 1.0), (1,))
+    V = _field(spec, 4)
+    V32 = V.astype(np.float32).astype(np.float64)   # the oracle sees the same rounded input
+    pm_o, pp_o = O.upwind(spec, oracle_method(scheme=scheme, dynamics=NORM), V32, 0)
+    pm, pp = solver.upwind(ctx, spec, lib_method(scheme=scheme, dynamics=NORM), to_dev(V32, "float32"), 0)
+    # differences of O(1) data lose ~1e-7 relative; derivatives scale by 1/dx
+    assert rel_err(to_host(pm, spec.n), pm_o) < 2e-4
+    assert rel_err(to_host(pp, spec.n), pp_o) < 2e-4
+
+
+@pytest.mark.parametrize("dyn", [DI, AIR3D, DUBINS, NORM, ADVECT, ROTATE])
+@pytest.mark.parametrize("scheme", [2, 5])
+@pytest.mark.parametrize("brt", [0, 1])
+def test_term_parity_fp64(ctx, dyn, scheme, brt):
+    from paper_2507_11542_gb300 import solver
+    spec = SPECS[dyn]
+    V = _field(spec, dyn)
+    y_o = O.term(spec, oracle_method(scheme=scheme, dynamics=dyn, brt=brt), V)
+    y = solver.term(ctx, spec, lib_method(scheme=scheme, dynamics=dyn, brt=brt), to_dev(V))
+    assert rel_err(to_host(y, spec.n), y_o) <= TOL64
+
+
+@pytest.mark.parametrize("dyn", [DI, AIR3D, DUBINS, NORM, ADVECT, ROTATE])
+def test_step_bound_is_bit_exact(ctx, dyn):
+    from paper_2507_11542_gb300 import solver
+    spec = SPECS[dyn]
+    assert solver.step_bound(ctx, spec, lib_method(dynamics=dyn)) == O.step_bound_inv(spec, oracle_method(dynamics=dyn))
+
+
+@pytest.mark.parametrize("dyn", [DI, AIR3D, DUBINS, NORM, ROTATE])
+@pytest.mark.parametrize("brt", [0, 1, 2])
+def test_rk3_step_parity_fp64(ctx, dyn, brt):
+    from paper_2507_11542_gb300 import solver
+    spec = SPECS[dyn]
+    V = _field(spec, 10 + dyn)
+    dt = 0.8 / O.step_bound_inv(spec, oracle_method(dynamics=dyn))
+    ref = O.rk3_step(spec, oracle_method(dynamics=dyn, brt=brt), V, dt)
+    Vd = to_dev(V)
+    solver.rk3_step(ctx, spec, lib_method(dynamics=dyn, brt=brt), Vd, dt)
+    assert rel_err(to_host(Vd, spec.n), ref) <= TOL64
+
+
+def _solve_both(ctx, spec, V0, dyn, ts, dtype="float64", scheme=5, brt=1, host_io=False):
+    from paper_2507_11542_gb300 import solver
+    import torch
+    ref, steps_o, times_o = O.solve(spec, oracle_method(scheme=scheme, dynamics=dyn, brt=brt), V0, ts)
+    m = lib_method(scheme=scheme, dynamics=dyn, brt=brt)
+    if host_io:
+        v0 = torch.from_numpy(np.ascontiguousarray(V0.ravel(order="F"))).to(getattr(torch, dtype)).pin_memory()
+        out = torch.empty((len(ts), v0.numel()), dtype=v0.dtype).pin_memory()
+        out, times, stats = solver.solve(ctx, spec, m, v0, ts, out=out)
+    else:
+        out, times, stats = solver.solve(ctx, spec, m, to_dev(V0, dtype), ts)
+    got = np.stack([to_host(out[k], spec.n) for k in range(len(ts))])
+    return got, ref, stats, steps_o, times, times_o
+
+
+def test_solve_double_integrator_full_config_fp64(ctx):
+    # 101^2 on [-1,1]^2, WENO5 + LF + TVD-RK3, CFL 0.8, horizon 1, BRT min(0, H), 11 slices
+    spec, V0 = W.double_integrator(101)
+    ts = W.slice_times(1.0)
+    got, ref, stats, steps_o, times, times_o = _solve_both(ctx, spec, V0, DI, ts)
+    assert stats["steps"] == steps_o
+    np.testing.assert_array_equal(times, times_o)
+    for k in range(len(ts)):
+        assert rel_err(got[k], ref[k]) <= TOL64, k
+
+
+def test_solve_air3d_full_horizon_fp64(ctx):
+    spec, V0 = W.air3d(31)
+    ts = W.slice_times(2.8, 5)
+    got, ref, stats, steps_o, times, times_o = _solve_both(ctx, spec, V0, AIR3D, ts)
+    assert stats["steps"] == steps_o > 100
+    for k in range(len(ts)):
+        assert rel_err(got[k], ref[k]) <= TOL64, k
+
+
+def test_solve_dubins_full_horizon_fp64_host_io(ctx):
+    spec, V0 = W.dubins4d(15)
+    ts = W.slice_times(2.0, 3)
+    got, ref, stats, steps_o, times, times_o = _solve_both(ctx, spec, V0, DUBINS, ts, host_io=True)
+    assert stats["steps"] == steps_o
+    for k in range(len(ts)):
+        assert rel_err(got[k], ref[k]) <= TOL64, k
+
+
+@pytest.mark.parametrize("scheme", [1, 2, 3])
+def test_solve_eno_variants_fp64(ctx, scheme):
+    spec = W.GridSpec((41, 39), (-1.0, -1.0), (1.0, 1.0))
+    V0 = W.sphere(spec, (0.13, -0.07), 0.5)
+    got, ref, stats, steps_o, _, _ = _solve_both(ctx, spec, V0, DI, [0.0, 0.3], scheme=scheme)
+    assert stats["steps"] == steps_o
+    assert rel_err(got[-1], ref[-1]) <= TOL64
+
+
+def test_solve_sphere_and_brt_minv_fp64(ctx):
+    spec = W.GridSpec((33, 30, 27), (-1.0, -1.0, -1.0), (1.0, 1.0, 1.0))
+    V0 = W.sphere(spec, (0.05, 0.0, -0.1), 0.25)
+    got, ref, _, _, _, _ = _solve_both(ctx, spec, V0, NORM, [0.2, 0.4], brt=0)
+    assert rel_err(got[-1], ref[-1]) <= TOL64
+    got, ref, _, _, _, _ = _solve_both(ctx, spec, V0, NORM, [0.2, 0.4], brt=2)
+    assert rel_err(got[-1], ref[-1]) <= TOL64
+
+
+@pytest.mark.parametrize("which", ["di", "air3d"])
+def test_solve_fp32_zero_level_set_within_a_tenth_of_a_cell(ctx, which):
+    if which == "di":
+        spec, V0 = W.double_integrator(101)
+        dyn, ts = DI, W.slice_times(1.0, 3)
+    else:
+        spec, V0 = W.air3d(41)
+        dyn, ts = AIR3D, W.slice_times(2.8, 3)
+    got, ref, stats, steps_o, _, _ = _solve_both(ctx, spec, V0, dyn, ts, dtype="float32")
+    assert stats["steps"] == steps_o
+    for k in range(len(ts)):
+        assert zero_set_displacement(got[k], ref[k], spec) < 0.1
+        assert rel_err(got[k], ref[k]) < 1e-4
+
+
+# ---------------------------------------------------------------------------
+# full-size workloads, one RK3 step, sampled nodes checked against oracle windows
+# ---------------------------------------------------------------------------
+
+def _sample_nodes(spec, rng, k):
+    nodes = [tuple(0 for _ in spec.n), tuple(m - 1 for m in spec.n), tuple(m // 2 for m in spec.n),
+             tuple(1 if d == 0 else spec.n[d] - 2 for d in range(len(spec.n)))]
+    while len(nodes) < k:
+        nodes.append(tuple(int(rng.integers(0, m)) for m in spec.n))
+    return nodes
+
+
+@pytest.mark.parametrize("which,dtype", [("air3d", "float64"), ("air3d", "float32"),
+                                         ("dubins", "float64"), ("dubins", "float32"),
+                                         ("sphere", "float32")])
+def test_full_size_step_sampled(ctx, which, dtype):
+    from paper_2507_11542_gb300 import solver
+    if which == "air3d":
+        spec, V0 = W.air3d(101)
+        dyn, brt = AIR3D, 1
+    elif which == "dubins":
+        spec, V0 = W.dubins4d(81)
+        dyn, brt = DUBINS, 1
+    else:
+        spec, V0 = W.expanding_sphere(512)
+        dyn, brt = NORM, 0
+    V0 = np.asfortranarray(V0.astype(np.float32).astype(np.float64)) if dtype == "float32" else V0
+    m_l = lib_method(dynamics=dyn, brt=brt)
+    m_o = oracle_method(dynamics=dyn, brt=brt)
+    sbi = solver.step_bound(ctx, spec, m_l)
+    dt = 0.8 / sbi
+    Vd = to_dev(V0, dtype)
+    solver.rk3_step(ctx, spec, m_l, Vd, dt)
+    got = to_host(Vd, spec.n)
+    rng = np.random.default_rng(7)
+    tol = TOL64 if dtype == "float64" else 2e-6
+    scale = float(np.max(np.abs(V0)))
+    for node in _sample_nodes(spec, rng, 8):
+        want = oracle_window_step(spec, V0, node, m_o, dt)
+        assert abs(got[node] - want) <= tol * scale, (node, got[node], want)
+    # a property at every node: the BRT clamp never raises V
+    if brt == 1:
+        assert np.all(got <= V0 + (1e-12 if dtype == "float64" else 1e-5) * scale)
+
+
+# ---------------------------------------------------------------------------
+# edge cases and errors
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [(2,), (7,), (5, 3), (7, 2, 4)])
+def test_tiny_and_degenerate_grids(ctx, n):
+    D = len(n)
+    spec = W.GridSpec(n, (-1.0,) * D, (1.0,) * D, tuple(d for d in range(D) if d == D - 1 and n[d] >= 1 and D > 1))
+    V0 = _field(spec, 5)
+    got, ref, stats, steps_o, _, _ = _solve_both(ctx, spec, V0, NORM, [0.0, 0.05], brt=0)
+    assert stats["steps"] == steps_o
+    assert rel_err(got[-1], ref[-1]) <= TOL64
+
+
+def test_zero_horizon_and_repeated_slices(ctx):
+    spec, V0 = W.double_integrator(21)
+    got, ref, stats, steps_o, times, _ = _solve_both(ctx, spec, V0, DI, [0.0, 0.0, 0.1, 0.1])
+    np.testing.assert_array_equal(got[0], V0)
+    np.testing.assert_array_equal(got[1], V0)
+    np.testing.assert_array_equal(got[2], got[3])
+    assert times[0] == 0.0 and stats["steps"] == steps_o
+
+
+def test_errors_are_reported_not_raised_on_device(ctx):
+    import torch
+    from paper_2507_11542_gb300 import _lib as L, solver
+    spec, V0 = W.double_integrator(21)
+    bad = V0.copy()
+    bad[3, 4] = np.nan
+    with pytest.raises(L.HJError) as e:
+        solver.solve(ctx, spec, lib_method(dynamics=DI), to_dev(bad), [0.1])
+    assert e.value.status == L.HJ_ENONFINITE
+    with pytest.raises(L.HJError) as e:
+        solver.solve(ctx, spec, lib_method(dynamics=DI), to_dev(V0), [0.2, 0.1])
+    assert e.value.status == L.HJ_EINVAL
+    with pytest.raises(L.HJError) as e:
+        solver.solve(ctx, spec, lib_method(dynamics=AIR3D), to_dev(V0), [0.1])   # air3D on a 2-D grid
+    assert e.value.status == L.HJ_EINVAL
+    with pytest.raises(L.HJError) as e:
+        solver.rk3_step(ctx, spec, lib_method(dynamics=DI), to_dev(V0), -1.0)
+    assert e.value.status == L.HJ_EINVAL
+    with pytest.raises(L.HJError) as e:
+        solver.solve(ctx, spec, lib_method(dynamics=DI, cfl=1.5), to_dev(V0), [0.1])
+    assert e.value.status == L.HJ_EINVAL
+    # the context is still usable afterwards
+    out, _, stats = solver.solve(ctx, spec, lib_method(dynamics=DI), to_dev(V0), [0.05])
+    assert stats["steps"] > 0 and torch.isfinite(out).all()
