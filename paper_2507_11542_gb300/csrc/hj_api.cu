@@ -1,11 +1,14 @@
 // hj_api.cu -- the C ABI of include/hj.h: context, argument validation, the
 // per-row entry points and the time loop of Sec. 5 (Listing 6).
+#include <algorithm>
 #include <cfloat>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
 #include <new>
 #include <string>
 #include <vector>
@@ -28,6 +31,10 @@ struct hj_ctx {
     bool trig_valid = false;
     std::string last_error;
     long long launches = 0;
+    int sm_count = 0;
+    std::map<std::vector<long long>, hj::RowsCfg> rows_cache;  // tuned launch shapes per grid shape
+    void* tune_buf = nullptr;                                 // output scratch of tuning launches
+    size_t tune_bytes = 0;
 };
 
 namespace {
@@ -251,7 +258,160 @@ StageParams stage_params(hj_ctx* ctx, const GridDev& G, const hj_method* m, int 
     return P;
 }
 
+// ---------------------------------------------------------------------------
+// Row-tiled WENO5 kernel: eligibility, launch-shape tuning, dispatch
+// ---------------------------------------------------------------------------
+
+int rows_max_threads(int dtype) { return dtype == HJ_F64 ? 512 : 1024; }
+
+bool rows_eligible(const GridDev& G, int scheme, int dynamics, int dtype) {
+    if (scheme != HJ_WENO5 || !rows_supported(G.ndim, dynamics)) return false;
+    if (const char* env = std::getenv("HJ_ROWS"))  // HJ_ROWS=0: always the one-node-per-thread kernel
+        if (env[0] == '0') return false;
+    for (int d = 0; d < G.ndim; ++d)
+        if (G.n[d] < 4) return false;
+    if (G.n[0] + 1 > rows_max_threads(dtype)) return false;
+    if (G.ndim == 4 && G.n[2] > 65535) return false;
+    return true;
+}
+
+RowsCfg make_rows_cfg(const GridDev& G, int ty, int tz) {
+    RowsCfg c;
+    c.ty = ty;
+    c.row_tiles = (G.n[1] + ty - 1) / ty;
+    const int ns = G.ndim >= 3 ? G.n[G.ndim - 1] : 1;
+    c.tz = G.ndim >= 3 ? tz : 1;
+    c.nchunks = G.ndim >= 3 ? (ns + c.tz - 1) / c.tz : 1;
+    return c;
+}
+
+int rows_bps(const StageParams& P, const RowsCfg& c, int dtype) {
+    return dtype == HJ_F64 ? rows_blocks_per_sm_f64(P, c) : rows_blocks_per_sm_f32(P, c);
+}
+
+cudaError_t rows_launch(hj_ctx* ctx, const StageParams& P, const RowsCfg& c, int dtype) {
+    ctx->launches += 1;
+    return dtype == HJ_F64 ? launch_rows_f64(P, c, ctx->stream) : launch_rows_f32(P, c, ctx->stream);
+}
+
+// Candidate shapes ranked by a simple cost model: whole waves of resident
+// blocks times the work of a block (warps x planes, plus one plane of
+// prologue per chunk and the halo rows per plane).
+std::vector<RowsCfg> rows_candidates(hj_ctx* ctx, const StageParams& P, int dtype) {
+    const GridDev& G = P.g;
+    const int nx = G.n[0], ny = G.n[1];
+    const int D = G.ndim;
+    const int ns = D >= 3 ? G.n[D - 1] : 1;
+    const size_t es = dtype == HJ_F64 ? 8 : 4;
+    static const int tys[] = {1, 2, 3, 4, 5, 6, 8, 10, 12, 16, 24, 32};
+    static const int tzs[] = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64, 128, 256};
+    std::vector<std::pair<double, RowsCfg>> scored;
+    for (int ty : tys) {
+        if (ty > ny || (nx + 1) * ty > rows_max_threads(dtype)) continue;
+        if (es * ((size_t)(ty + 6) * nx + 2 * (size_t)ty * nx) > 200 * 1024) continue;
+        std::vector<int> zs;
+        if (D >= 3) {
+            for (int tz : tzs)
+                if (tz < ns) zs.push_back(tz);
+            zs.push_back(ns);
+        } else {
+            zs.push_back(1);
+        }
+        for (int tz : zs) {
+            RowsCfg c = make_rows_cfg(G, ty, tz);
+            if (c.nchunks > 65535 || c.row_tiles > (1 << 30)) continue;
+            const int bps = rows_bps(P, c, dtype);
+            if (bps <= 0) continue;
+            const double blocks = (double)c.row_tiles * c.nchunks * (D == 4 ? G.n[2] : 1);
+            const double slots = (double)ctx->sm_count * bps;
+            const double waves = std::ceil(blocks / slots);
+            const double warps = std::ceil((double)(nx + 1) * ty / 32.0);
+            const double rows_valid = std::min(ty, ny);
+            const double plane = warps * (1.0 + 0.1 * (6.0 + ty - rows_valid) / ty);
+            const double planes = D >= 3 ? (double)std::min(tz, ns) + 1.0 : 1.0;
+            scored.push_back({waves * std::min((double)bps, blocks) * plane * planes, c});
+        }
+    }
+    std::sort(scored.begin(), scored.end(),
+              [](const std::pair<double, RowsCfg>& a, const std::pair<double, RowsCfg>& b) { return a.first < b.first; });
+    std::vector<RowsCfg> out;
+    for (size_t k = 0; k < scored.size() && k < 8; ++k) out.push_back(scored[k].second);
+    return out;
+}
+
+// The launch shape for this grid: measured once per (shape, dtype, dynamics)
+// over the model's best candidates (stage kernel in term mode writing to a
+// scratch buffer), then cached in the context. HJ_TUNE=0 keeps the model's
+// first choice without timing.
+hj_status rows_config(hj_ctx* ctx, const StageParams& P, int dtype, RowsCfg* out) {
+    const GridDev& G = P.g;
+    // HJ_ROWS_CFG="ty,tz" pins the shape (used to check that results do not depend on it)
+    if (const char* pin = std::getenv("HJ_ROWS_CFG")) {
+        int ty = 0, tz = 0;
+        if (std::sscanf(pin, "%d,%d", &ty, &tz) == 2 && ty >= 1 && tz >= 1 && ty <= G.n[1] &&
+            (G.n[0] + 1) * ty <= rows_max_threads(dtype)) {
+            *out = make_rows_cfg(G, ty, tz);
+            if (out->nchunks <= 65535 && rows_bps(P, *out, dtype) > 0) return HJ_OK;
+        }
+        return fail(ctx, HJ_EINVAL, "HJ_ROWS_CFG=%s does not fit this grid", pin);
+    }
+    std::vector<long long> key = {G.ndim, P.dynamics, dtype, G.n[0], G.n[1], G.n[2], G.n[3]};
+    auto it = ctx->rows_cache.find(key);
+    if (it != ctx->rows_cache.end()) {
+        *out = it->second;
+        return HJ_OK;
+    }
+    std::vector<RowsCfg> cands = rows_candidates(ctx, P, dtype);
+    if (cands.empty()) return fail(ctx, HJ_EINVAL, "no launch shape fits the row kernel");
+    const char* env = std::getenv("HJ_TUNE");
+    RowsCfg best = cands[0];
+    if (!(env && env[0] == '0') && cands.size() > 1) {
+        const size_t bytes = (size_t)G.total * (dtype == HJ_F64 ? 8 : 4);
+        hj_status st = ensure(ctx, &ctx->tune_buf, &ctx->tune_bytes, bytes);
+        if (st) return st;
+        StageParams T = P;
+        T.mode = kTerm;
+        T.out = ctx->tune_buf;
+        cudaEvent_t e0, e1;
+        HJ_CUDA(ctx, cudaEventCreate(&e0));
+        HJ_CUDA(ctx, cudaEventCreate(&e1));
+        float best_ms = 1e30f;
+        for (const RowsCfg& c : cands) {
+            cudaError_t e = rows_launch(ctx, T, c, dtype);  // warm-up
+            float ms_min = 1e30f;
+            for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+                cudaEventRecord(e0, ctx->stream);
+                e = rows_launch(ctx, T, c, dtype);
+                cudaEventRecord(e1, ctx->stream);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float ms = 0.f;
+                if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+                ms_min = std::min(ms_min, ms);
+            }
+            if (e != cudaSuccess) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return cuda_fail(ctx, e, "tuning launch");
+            }
+            if (ms_min < best_ms) {
+                best_ms = ms_min;
+                best = c;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
+    ctx->rows_cache[key] = best;
+    *out = best;
+    return HJ_OK;
+}
+
 cudaError_t launch_stage(hj_ctx* ctx, const StageParams& P, int scheme, int dtype) {
+    if (rows_eligible(P.g, scheme, P.dynamics, dtype)) {
+        RowsCfg c;
+        if (rows_config(ctx, P, dtype, &c) != HJ_OK) return cudaErrorInvalidConfiguration;
+        return rows_launch(ctx, P, c, dtype);
+    }
     ctx->launches += 1;
     return dtype == HJ_F64 ? launch_stage_f64(P, scheme, ctx->stream) : launch_stage_f32(P, scheme, ctx->stream);
 }
@@ -351,6 +511,10 @@ hj_status hj_ctx_create(int32_t device, void* cuda_stream, hj_ctx** out) {
     ctx->device = device;
     ctx->stream = static_cast<cudaStream_t>(cuda_stream);
     DeviceGuard guard(device);
+    if (cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+        delete ctx;
+        return HJ_ECUDA;
+    }
     if (cudaMalloc(&ctx->aux, 256) != cudaSuccess) {
         delete ctx;
         return HJ_ENOMEM;
@@ -369,6 +533,7 @@ void hj_ctx_destroy(hj_ctx* ctx) {
     cudaFree(ctx->aux);
     cudaFree(ctx->trig_d);
     cudaFree(ctx->trig_f);
+    cudaFree(ctx->tune_buf);
     delete ctx;
 }
 

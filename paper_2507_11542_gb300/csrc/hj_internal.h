@@ -55,11 +55,28 @@ struct UpwindParams {
     double weno_floor;
 };
 
+// Launch configuration of the row-tiled WENO5 stage kernel (rows_kernel.cuh).
+struct RowsCfg {
+    int ty;         // rows per tile (blockDim.y); blockDim.x = n0 + 1
+    int tz;         // planes per chunk along the streamed (last) dimension
+    int nchunks;    // chunks along the streamed dimension
+    int row_tiles;  // ceil(n1 / ty)
+};
+
 // Launchers (one translation unit per element type). Return the launch error.
 cudaError_t launch_stage_f64(const StageParams& p, int scheme, cudaStream_t s);
 cudaError_t launch_stage_f32(const StageParams& p, int scheme, cudaStream_t s);
 cudaError_t launch_upwind_f64(const UpwindParams& p, int scheme, cudaStream_t s);
 cudaError_t launch_upwind_f32(const UpwindParams& p, int scheme, cudaStream_t s);
+
+// Row-tiled WENO5 stage kernel: defined for D = 2 (double integrator, norm,
+// advection, rotation), D = 3 (air3D, norm, advection, rotation), D = 4 (Dubins4D).
+bool rows_supported(int ndim, int dynamics);
+cudaError_t launch_rows_f64(const StageParams& p, const RowsCfg& c, cudaStream_t s);
+cudaError_t launch_rows_f32(const StageParams& p, const RowsCfg& c, cudaStream_t s);
+// resident blocks per SM of a configuration (0 if it cannot launch)
+int rows_blocks_per_sm_f64(const StageParams& p, const RowsCfg& c);
+int rows_blocks_per_sm_f32(const StageParams& p, const RowsCfg& c);
 
 // max over nodes of sum_d alpha_d(x)/dx_d, as the FP64 bit pattern, atomically
 // max-ed into *acc (which the caller zeroes first).

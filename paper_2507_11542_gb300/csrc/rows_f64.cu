@@ -1,0 +1,29 @@
+// FP64 instantiations of the row-tiled WENO5 stage kernel.
+#include "rows_kernel.cuh"
+
+namespace hj {
+bool rows_supported(int ndim, int dyn) {
+    switch (ndim * 16 + dyn) {
+    case 2 * 16 + HJ_DYN_DOUBLE_INTEGRATOR:
+    case 2 * 16 + HJ_DYN_NORM:
+    case 2 * 16 + HJ_DYN_ADVECT:
+    case 2 * 16 + HJ_DYN_ROTATE:
+    case 3 * 16 + HJ_DYN_AIR3D:
+    case 3 * 16 + HJ_DYN_NORM:
+    case 3 * 16 + HJ_DYN_ADVECT:
+    case 3 * 16 + HJ_DYN_ROTATE:
+    case 4 * 16 + HJ_DYN_DUBINS4D:
+        return true;
+    default:
+        return false;
+    }
+}
+cudaError_t launch_rows_f64(const StageParams& p, const RowsCfg& c, cudaStream_t s) {
+    HJ_ROWS_DISPATCH(launch_rows_dyn, double, p, c, s)
+    return cudaErrorInvalidValue;
+}
+int rows_blocks_per_sm_f64(const StageParams& p, const RowsCfg& c) {
+    HJ_ROWS_DISPATCH(rows_bps_dyn, double, p, c)
+    return 0;
+}
+}  // namespace hj

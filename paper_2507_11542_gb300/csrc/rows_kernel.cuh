@@ -1,0 +1,273 @@
+// rows_kernel.cuh -- the fused RK stage kernel for WENO5 on 2-4 dimensional
+// grids, tiled for GB300:
+//
+//  * A thread block owns TY full rows (all n0 nodes along dimension 0) of one
+//    plane of dimensions (0, 1); threadIdx = (x, row). The plane with three
+//    halo rows above and below lives in shared memory.
+//  * Along dimension 0, WENO5 is evaluated per interface (one interface gives
+//    p+ of a node and p- of the next; thread x computes the interface between
+//    nodes x-1 and x, the extra thread x = n0 the row's last one), so each
+//    node pays for about one interface instead of two.
+//  * Dimension 1 is differentiated two-sided from the shared-memory column.
+//  * For 3-D and 4-D grids the block streams along the last dimension through
+//    a chunk of planes: each thread keeps six values of its column in
+//    registers and carries the interface result p- to the next plane.
+//  * In 4-D, dimension 2 is differentiated two-sided from 7-point loads.
+//  * Ghost values (periodic wrap or slope continued away from zero, Sec. 2.1)
+//    are produced where values are read; no padded array exists.
+// Then: Hamiltonian + Lax-Friedrichs dissipation (Sec. 4), BRT clamp (Sec.
+// 6.1) and the TVD-RK3 stage combination (Sec. 5), one store per node.
+#pragma once
+
+#include "stencil.cuh"
+#include "weno_iface.cuh"
+
+namespace hj {
+
+// FP32 blocks may hold 1024 threads (<= 64 registers each); FP64 blocks at
+// most 512 (<= 128 registers), since the FP64 interface math needs more.
+template <typename T> struct RowsLimits;
+template <> struct RowsLimits<float> { static constexpr int kMaxThreads = 1024; };
+template <> struct RowsLimits<double> { static constexpr int kMaxThreads = 512; };
+
+template <typename T>
+__device__ __forceinline__ T ghost_value(T edge, T inner, int m, int extrap) {
+    const T s = (extrap == HJ_EXTRAP_LINEAR) ? (edge - inner) : fabs(edge - inner) * sgn(edge);
+    return add_rn(edge, mul_rn(T(m), s));
+}
+
+// Value at index i of a grid line (base pointer, n nodes, stride s), with the
+// line's ghost rule outside [0, n).
+template <typename T>
+__device__ __forceinline__ T line_value(const T* __restrict__ base, int i, int n, long long s, bool periodic,
+                                        int extrap) {
+    if (i >= 0 && i < n) return ld(base + (long long)i * s);
+    if (periodic) {
+        int j = i % n;
+        if (j < 0) j += n;
+        return ld(base + (long long)j * s);
+    }
+    if (i < 0) return ghost_value(ld(base), ld(base + s), -i, extrap);
+    return ghost_value(ld(base + (long long)(n - 1) * s), ld(base + (long long)(n - 2) * s), i - (n - 1), extrap);
+}
+
+// Value at index i of a shared-memory row of n nodes (ghosts from its ends).
+template <typename T>
+__device__ __forceinline__ T row_value(const T* row, int i, int n, bool periodic, int extrap) {
+    if (i >= 0 && i < n) return row[i];
+    if (periodic) {
+        int j = i % n;
+        if (j < 0) j += n;
+        return row[j];
+    }
+    if (i < 0) return ghost_value(row[0], row[1], -i, extrap);
+    return ghost_value(row[n - 1], row[n - 2], i - (n - 1), extrap);
+}
+
+template <typename T, int D, int DYN>
+__global__ void __launch_bounds__(RowsLimits<T>::kMaxThreads) rows_kernel(const StageParams P, const RowsCfg C) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const GridDev& g = P.g;
+    const int nx = g.n[0], ny = g.n[1];
+    const int TY = C.ty;
+    T* plane = reinterpret_cast<T*>(smem_raw);  // (TY + 6) rows x nx
+    T* pxm = plane + (size_t)(TY + 6) * nx;      // TY x nx : p- along dimension 0
+    T* pxp = pxm + (size_t)TY * nx;              // TY x nx : p+ along dimension 0
+
+    const T* __restrict__ u = static_cast<const T*>(P.u);
+    const T* __restrict__ vn = static_cast<const T*>(P.vn);
+    T* __restrict__ out = static_cast<T*>(P.out);
+    const T floor_raw = T(P.weno_floor);
+    const bool per0 = g.periodic_mask & 1u, per1 = (g.periodic_mask >> 1) & 1u;
+    const int extrap = g.extrap;
+
+    const int x = threadIdx.x;  // 0 .. nx (x == nx: last interface of the row only)
+    const int r = threadIdx.y;
+    const int y0 = blockIdx.x * TY;
+    const int y = y0 + r;
+    const int rows_valid = min(TY, ny - y0);
+    const bool node = (x < nx) && (r < rows_valid);
+
+    int i2 = 0, chunk = 0;
+    if (D == 3) chunk = blockIdx.y;
+    if (D == 4) { i2 = blockIdx.y; chunk = blockIdx.z; }
+    constexpr int SD = (D >= 3) ? D - 1 : 0;  // streamed dimension
+    const int ns = (D >= 3) ? g.n[SD] : 1;
+    const int zbeg = (D >= 3) ? chunk * C.tz : 0;
+    const int zend = (D >= 3) ? min(ns, zbeg + C.tz) : 1;
+    const long long sS = (D >= 3) ? g.stride[SD] : 0;
+    const bool perS = (D >= 3) ? ((g.periodic_mask >> SD) & 1u) : false;
+    const long long plane_base = (D == 4) ? (long long)i2 * g.stride[2] : 0;
+    const long long colbase = plane_base + (long long)min(x, nx - 1) + (long long)y * g.stride[1];
+
+    const T inv_dx0 = T(g.inv_dx[0]);
+    const T inv_dxs = T(g.inv_dx[SD]);
+    const T dx1 = T(g.dx[1]);
+
+    // Halo rows this thread loads every plane: rows -3..-1 and rows_valid..TY+2
+    // (past the grid edge: ghost rows), distributed over the thread rows.
+    const int n_extra = 3 + (TY + 3 - rows_valid);
+
+    // streamed-dimension queue: q[k] = V at plane z-2+k, k = 0..5; carry = p- at z
+    T q[6];
+    T carry = T(0);
+    if (D >= 3 && node) {
+        const T w0 = line_value(u + colbase, zbeg - 3, ns, sS, perS, extrap);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) q[k] = line_value(u + colbase, zbeg - 2 + k, ns, sS, perS, extrap);
+        T unused;
+        weno_iface(q[0] - w0, q[1] - q[0], q[2] - q[1], q[3] - q[2], q[4] - q[3], floor_raw, inv_dxs, unused, carry);
+    }
+
+    for (int z = zbeg; z < zend; ++z) {
+        const long long zoff = (D >= 3) ? (long long)z * sS : 0;
+        T center = T(0);
+        if (node) {
+            if (D >= 3) {
+                q[5] = line_value(u + colbase, z + 3, ns, sS, perS, extrap);
+                center = q[2];
+            } else {
+                center = ld(u + colbase);
+            }
+        }
+        __syncthreads();  // the previous plane is fully consumed
+        if (node) plane[(size_t)(r + 3) * nx + x] = center;
+        if (x < nx) {
+            for (int h = r; h < n_extra; h += TY) {
+                const int rr = (h < 3) ? h - 3 : rows_valid + (h - 3);
+                plane[(size_t)(rr + 3) * nx + x] =
+                    line_value(u + plane_base + zoff + x, y0 + rr, ny, g.stride[1], per1, extrap);
+            }
+        }
+        __syncthreads();
+        // interface between nodes x-1 and x of row r (x = nx: the row's last interface)
+        if (r < rows_valid) {
+            const T* row = plane + (size_t)(r + 3) * nx;
+            T a[6];
+            if (x >= 3 && x + 2 < nx) {
+#pragma unroll
+                for (int k = 0; k < 6; ++k) a[k] = row[x - 3 + k];
+            } else {
+#pragma unroll
+                for (int k = 0; k < 6; ++k) a[k] = row_value(row, x - 3 + k, nx, per0, extrap);
+            }
+            T ppj, pmj1;
+            weno_iface(a[1] - a[0], a[2] - a[1], a[3] - a[2], a[4] - a[3], a[5] - a[4], floor_raw, inv_dx0, ppj,
+                       pmj1);
+            if (x >= 1) pxp[(size_t)r * nx + x - 1] = ppj;
+            if (x < nx) pxm[(size_t)r * nx + x] = pmj1;
+        }
+        __syncthreads();
+        if (node) {
+            T pm[D], pp[D];
+            pm[0] = pxm[(size_t)r * nx + x];
+            pp[0] = pxp[(size_t)r * nx + x];
+            {
+                T v[7];
+#pragma unroll
+                for (int k = 0; k < 7; ++k) v[k] = plane[(size_t)(r + k) * nx + x];
+                weno5_pair<T>(v, dx1, floor_raw, pm[1], pp[1]);
+            }
+            if constexpr (D == 4) {
+                T v[7];
+                gather7<T>(u, colbase + zoff, i2, g.n[2], g.stride[2], (g.periodic_mask >> 2) & 1u, extrap, v);
+                weno5_pair<T>(v, T(g.dx[2]), floor_raw, pm[2], pp[2]);
+            }
+            if constexpr (D >= 3) {
+                T next;
+                weno_iface(q[1] - q[0], q[2] - q[1], q[3] - q[2], q[4] - q[3], q[5] - q[4], floor_raw, inv_dxs,
+                           pp[SD], next);
+                pm[SD] = carry;
+                carry = next;
+            }
+            int idx[4] = {x, y, 0, 0};
+            if (D == 3) idx[2] = z;
+            if (D == 4) { idx[2] = i2; idx[3] = z; }
+            T yd = lf_term_dyn<T, D, DYN>(P, idx, pm, pp);
+            if (P.brt_min0) yd = fmin(yd, T(0));
+            const long long flat = colbase + zoff;
+            T res;
+            if (P.mode == kTerm) {
+                res = yd;
+            } else {
+                const T w = center + T(P.dt) * yd;
+                res = w;
+                if (P.cv != 0.0) res = T(P.cv) * ld(vn + flat) + T(P.cu) * w;
+                if (P.minv_after) res = fmin(res, ld(vn + flat));
+            }
+            out[flat] = res;
+            if constexpr (D >= 3) {
+#pragma unroll
+                for (int k = 0; k < 5; ++k) q[k] = q[k + 1];
+            }
+        }
+    }
+}
+
+// Shared memory of a rows_kernel block.
+template <typename T>
+inline size_t rows_smem_bytes(int nx, int ty) {
+    return sizeof(T) * ((size_t)(ty + 6) * nx + 2 * (size_t)ty * nx);
+}
+
+template <typename T, int D, int DYN>
+inline void rows_shape(const StageParams& p, const RowsCfg& c, dim3& grid, dim3& block, size_t& smem) {
+    block = dim3((unsigned)(p.g.n[0] + 1), (unsigned)c.ty, 1);
+    grid = dim3((unsigned)c.row_tiles, 1, 1);
+    if (D == 3) grid.y = (unsigned)c.nchunks;
+    if (D == 4) { grid.y = (unsigned)p.g.n[2]; grid.z = (unsigned)c.nchunks; }
+    smem = rows_smem_bytes<T>(p.g.n[0], c.ty);
+}
+
+template <typename T, int D, int DYN>
+inline cudaError_t rows_prepare() {
+    static bool done = false;  // benign race: setting the attribute twice is harmless
+    if (!done) {
+        cudaError_t e = cudaFuncSetAttribute(rows_kernel<T, D, DYN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             200 * 1024);
+        if (e != cudaSuccess) return e;
+        done = true;
+    }
+    return cudaSuccess;
+}
+
+template <typename T, int D, int DYN>
+cudaError_t launch_rows_dyn(const StageParams& p, const RowsCfg& c, cudaStream_t s) {
+    dim3 grid, block;
+    size_t smem;
+    rows_shape<T, D, DYN>(p, c, grid, block, smem);
+    cudaError_t e = rows_prepare<T, D, DYN>();
+    if (e != cudaSuccess) return e;
+    rows_kernel<T, D, DYN><<<grid, block, smem, s>>>(p, c);
+    return cudaGetLastError();
+}
+
+template <typename T, int D, int DYN>
+int rows_bps_dyn(const StageParams& p, const RowsCfg& c) {
+    dim3 grid, block;
+    size_t smem;
+    rows_shape<T, D, DYN>(p, c, grid, block, smem);
+    if (rows_prepare<T, D, DYN>() != cudaSuccess) return 0;
+    int bps = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, rows_kernel<T, D, DYN>, (int)(block.x * block.y), smem) !=
+        cudaSuccess)
+        return 0;
+    return bps;
+}
+
+// Dispatch over the (dimension, dynamics) pairs the row kernel is built for.
+#define HJ_ROWS_DISPATCH(FN, T, ...)                                                   \
+    switch (p.g.ndim * 16 + p.dynamics) {                                              \
+    case 2 * 16 + HJ_DYN_DOUBLE_INTEGRATOR: return FN<T, 2, HJ_DYN_DOUBLE_INTEGRATOR>(__VA_ARGS__); \
+    case 2 * 16 + HJ_DYN_NORM: return FN<T, 2, HJ_DYN_NORM>(__VA_ARGS__);             \
+    case 2 * 16 + HJ_DYN_ADVECT: return FN<T, 2, HJ_DYN_ADVECT>(__VA_ARGS__);         \
+    case 2 * 16 + HJ_DYN_ROTATE: return FN<T, 2, HJ_DYN_ROTATE>(__VA_ARGS__);         \
+    case 3 * 16 + HJ_DYN_AIR3D: return FN<T, 3, HJ_DYN_AIR3D>(__VA_ARGS__);           \
+    case 3 * 16 + HJ_DYN_NORM: return FN<T, 3, HJ_DYN_NORM>(__VA_ARGS__);             \
+    case 3 * 16 + HJ_DYN_ADVECT: return FN<T, 3, HJ_DYN_ADVECT>(__VA_ARGS__);         \
+    case 3 * 16 + HJ_DYN_ROTATE: return FN<T, 3, HJ_DYN_ROTATE>(__VA_ARGS__);         \
+    case 4 * 16 + HJ_DYN_DUBINS4D: return FN<T, 4, HJ_DYN_DUBINS4D>(__VA_ARGS__);     \
+    default: break;                                                                    \
+    }
+
+}  // namespace hj

@@ -203,8 +203,8 @@ template <typename T> struct Trig;
 template <> struct Trig<double> { static __device__ __forceinline__ const double* get(const StageParams& P) { return P.trig_d; } };
 template <> struct Trig<float>  { static __device__ __forceinline__ const float*  get(const StageParams& P) { return P.trig_f; } };
 
-template <typename T, int D>
-__device__ __forceinline__ T lf_term(const StageParams& P, const int* idx, const T* pm, const T* pp) {
+template <typename T, int D, int DYN>
+__device__ __forceinline__ T lf_term_dyn(const StageParams& P, const int* idx, const T* pm, const T* pp) {
     T pb[D], dd[D], x[D];
 #pragma unroll
     for (int d = 0; d < D; ++d) {
@@ -214,58 +214,51 @@ __device__ __forceinline__ T lf_term(const StageParams& P, const int* idx, const
     }
     const double* q = P.params;
     T y = T(0);
-    switch (P.dynamics) {
-    case HJ_DYN_DOUBLE_INTEGRATOR:
-        if constexpr (D == 2) {
-            const T umax = T(q[0]);
-            y = pb[0] * x[1] - umax * fabs(pb[1]) + fabs(x[1]) * dd[0] + umax * dd[1];
-        }
-        break;
-    case HJ_DYN_AIR3D:
-        if constexpr (D == 3) {
-            const T* tr = Trig<T>::get(P);
-            const T c = tr[idx[2]], s = tr[P.g.n[2] + idx[2]];
-            const T va = T(q[0]), vb = T(q[1]), amax = T(q[2]), bmax = T(q[3]);
-            const T f0 = -va + vb * c, f1 = vb * s;
-            y = pb[0] * f0 + pb[1] * f1 + amax * fabs(pb[0] * x[1] - pb[1] * x[0] - pb[2]) - bmax * fabs(pb[2]);
-            y += (fabs(f0) + amax * fabs(x[1])) * dd[0] + (fabs(f1) + amax * fabs(x[0])) * dd[1] +
-                 (amax + bmax) * dd[2];
-        }
-        break;
-    case HJ_DYN_DUBINS4D:
-        if constexpr (D == 4) {
-            const T* tr = Trig<T>::get(P);
-            const T c = tr[idx[2]], s = tr[P.g.n[2] + idx[2]];
-            const T wmax = T(q[0]), accmax = T(q[1]);
-            const T f0 = x[3] * c, f1 = x[3] * s;
-            y = pb[0] * f0 + pb[1] * f1 - wmax * fabs(pb[2]) - accmax * fabs(pb[3]);
-            y += fabs(f0) * dd[0] + fabs(f1) * dd[1] + wmax * dd[2] + accmax * dd[3];
-        }
-        break;
-    case HJ_DYN_NORM: {
+    if constexpr (DYN == HJ_DYN_DOUBLE_INTEGRATOR && D == 2) {
+        const T umax = T(q[0]);
+        y = pb[0] * x[1] - umax * fabs(pb[1]) + fabs(x[1]) * dd[0] + umax * dd[1];
+    } else if constexpr (DYN == HJ_DYN_AIR3D && D == 3) {
+        const T* tr = Trig<T>::get(P);
+        const T c = tr[idx[2]], s = tr[P.g.n[2] + idx[2]];
+        const T va = T(q[0]), vb = T(q[1]), amax = T(q[2]), bmax = T(q[3]);
+        const T f0 = -va + vb * c, f1 = vb * s;
+        y = pb[0] * f0 + pb[1] * f1 + amax * fabs(pb[0] * x[1] - pb[1] * x[0] - pb[2]) - bmax * fabs(pb[2]);
+        y += (fabs(f0) + amax * fabs(x[1])) * dd[0] + (fabs(f1) + amax * fabs(x[0])) * dd[1] + (amax + bmax) * dd[2];
+    } else if constexpr (DYN == HJ_DYN_DUBINS4D && D == 4) {
+        const T* tr = Trig<T>::get(P);
+        const T c = tr[idx[2]], s = tr[P.g.n[2] + idx[2]];
+        const T wmax = T(q[0]), accmax = T(q[1]);
+        const T f0 = x[3] * c, f1 = x[3] * s;
+        y = pb[0] * f0 + pb[1] * f1 - wmax * fabs(pb[2]) - accmax * fabs(pb[3]);
+        y += fabs(f0) * dd[0] + fabs(f1) * dd[1] + wmax * dd[2] + accmax * dd[3];
+    } else if constexpr (DYN == HJ_DYN_NORM) {
         const T c = T(q[0]);
         T s2 = T(0), diss = T(0);
 #pragma unroll
         for (int d = 0; d < D; ++d) { s2 += pb[d] * pb[d]; diss += dd[d]; }
         y = -c * sqrt(s2) + c * diss;
-        break;
-    }
-    case HJ_DYN_ADVECT: {
+    } else if constexpr (DYN == HJ_DYN_ADVECT) {
 #pragma unroll
         for (int d = 0; d < D; ++d) { const T c = T(q[d]); y += -c * pb[d] + fabs(c) * dd[d]; }
-        break;
-    }
-    case HJ_DYN_ROTATE:
-        if constexpr (D >= 2) {
-            const T w = T(q[0]);
-            const T f0 = -w * x[1], f1 = w * x[0];
-            y = -(pb[0] * f0 + pb[1] * f1) + fabs(f0) * dd[0] + fabs(f1) * dd[1];
-        }
-        break;
-    default:
-        break;
+    } else if constexpr (DYN == HJ_DYN_ROTATE && D >= 2) {
+        const T w = T(q[0]);
+        const T f0 = -w * x[1], f1 = w * x[0];
+        y = -(pb[0] * f0 + pb[1] * f1) + fabs(f0) * dd[0] + fabs(f1) * dd[1];
     }
     return y;
+}
+
+template <typename T, int D>
+__device__ __forceinline__ T lf_term(const StageParams& P, const int* idx, const T* pm, const T* pp) {
+    switch (P.dynamics) {
+    case HJ_DYN_DOUBLE_INTEGRATOR: return lf_term_dyn<T, D, HJ_DYN_DOUBLE_INTEGRATOR>(P, idx, pm, pp);
+    case HJ_DYN_AIR3D: return lf_term_dyn<T, D, HJ_DYN_AIR3D>(P, idx, pm, pp);
+    case HJ_DYN_DUBINS4D: return lf_term_dyn<T, D, HJ_DYN_DUBINS4D>(P, idx, pm, pp);
+    case HJ_DYN_NORM: return lf_term_dyn<T, D, HJ_DYN_NORM>(P, idx, pm, pp);
+    case HJ_DYN_ADVECT: return lf_term_dyn<T, D, HJ_DYN_ADVECT>(P, idx, pm, pp);
+    case HJ_DYN_ROTATE: return lf_term_dyn<T, D, HJ_DYN_ROTATE>(P, idx, pm, pp);
+    default: return T(0);
+    }
 }
 
 }  // namespace hj

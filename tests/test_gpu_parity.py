@@ -282,3 +282,40 @@ def test_errors_are_reported_not_raised_on_device(ctx):
     # the context is still usable afterwards
     out, _, stats = solver.solve(ctx, spec, lib_method(dynamics=DI), to_dev(V0), [0.05])
     assert stats["steps"] > 0 and torch.isfinite(out).all()
+
+
+# ---------------------------------------------------------------------------
+# the row-tiled WENO5 kernel: results independent of the launch shape
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dyn,shape,cfgs", [
+    (AIR3D, (37, 29, 23), ["1,1", "2,5", "4,23", "7,3", "13,8"]),
+    (DUBINS, (13, 11, 9, 7), ["1,1", "3,2", "11,7"]),
+    (DI, (37, 29), ["1,1", "5,1", "29,1"]),
+])
+@pytest.mark.parametrize("dtype", ["float64", "float32"])
+def test_row_kernel_is_independent_of_tiling(ctx, monkeypatch, dyn, shape, cfgs, dtype):
+    from paper_2507_11542_gb300 import solver
+    base = SPECS[dyn]
+    spec = W.GridSpec(shape, base.lo, base.hi, base.periodic)
+    V = _field(spec, 21)
+    m = lib_method(dynamics=dyn, brt=1)
+    dt = 0.8 / O.step_bound_inv(spec, oracle_method(dynamics=dyn))
+    outs = []
+    for cfg in cfgs:
+        monkeypatch.setenv("HJ_ROWS_CFG", cfg)
+        Vd = to_dev(V, dtype)
+        solver.rk3_step(ctx, spec, m, Vd, dt)
+        outs.append(to_host(Vd, spec.n))
+    monkeypatch.delenv("HJ_ROWS_CFG")
+    for o in outs[1:]:
+        np.testing.assert_array_equal(o, outs[0])
+    # the one-node-per-thread kernel (two-sided WENO5 everywhere) agrees to rounding
+    monkeypatch.setenv("HJ_ROWS", "0")
+    Vd = to_dev(V, dtype)
+    solver.rk3_step(ctx, spec, m, Vd, dt)
+    monkeypatch.delenv("HJ_ROWS")
+    assert rel_err(to_host(Vd, spec.n), outs[0]) <= (1e-13 if dtype == "float64" else 1e-5)
+    if dtype == "float64":
+        ref = O.rk3_step(spec, oracle_method(dynamics=dyn, brt=1), V, dt)
+        assert rel_err(outs[0], ref) <= TOL64
