@@ -108,18 +108,20 @@ __global__ void __launch_bounds__(RowsLimits<T>::kMaxThreads) rows_kernel(const 
     // (past the grid edge: ghost rows), distributed over the thread rows.
     const int n_extra = 3 + (TY + 3 - rows_valid);
 
-    // streamed-dimension queue: q[k] = V at plane z-2+k, k = 0..5; carry = p- at z
+    // Streamed-dimension queue: q[k] = V at plane z-2+k (k = 0..5); carry = p- at z.
+    // The loop starts one plane early (a warm-up iteration that only evaluates
+    // the streamed interface) so that every interface goes through the same
+    // code and results do not depend on where chunks start.
     T q[6];
     T carry = T(0);
     if (D >= 3 && node) {
-        const T w0 = line_value(u + colbase, zbeg - 3, ns, sS, perS, extrap);
 #pragma unroll
-        for (int k = 0; k < 5; ++k) q[k] = line_value(u + colbase, zbeg - 2 + k, ns, sS, perS, extrap);
-        T unused;
-        weno_iface(q[0] - w0, q[1] - q[0], q[2] - q[1], q[3] - q[2], q[4] - q[3], floor_raw, inv_dxs, unused, carry);
+        for (int k = 0; k < 5; ++k) q[k] = line_value(u + colbase, zbeg - 3 + k, ns, sS, perS, extrap);
     }
+    const int zfirst = (D >= 3) ? zbeg - 1 : zbeg;
 
-    for (int z = zbeg; z < zend; ++z) {
+    for (int z = zfirst; z < zend; ++z) {
+        const bool warm = z < zbeg;  // block-uniform
         const long long zoff = (D >= 3) ? (long long)z * sS : 0;
         T center = T(0);
         if (node) {
@@ -130,73 +132,77 @@ __global__ void __launch_bounds__(RowsLimits<T>::kMaxThreads) rows_kernel(const 
                 center = ld(u + colbase);
             }
         }
-        __syncthreads();  // the previous plane is fully consumed
-        if (node) plane[(size_t)(r + 3) * nx + x] = center;
-        if (x < nx) {
-            for (int h = r; h < n_extra; h += TY) {
-                const int rr = (h < 3) ? h - 3 : rows_valid + (h - 3);
-                plane[(size_t)(rr + 3) * nx + x] =
-                    line_value(u + plane_base + zoff + x, y0 + rr, ny, g.stride[1], per1, extrap);
+        if (!warm) {
+            __syncthreads();  // the previous plane is fully consumed
+            if (node) plane[(size_t)(r + 3) * nx + x] = center;
+            if (x < nx) {
+                for (int h = r; h < n_extra; h += TY) {
+                    const int rr = (h < 3) ? h - 3 : rows_valid + (h - 3);
+                    plane[(size_t)(rr + 3) * nx + x] =
+                        line_value(u + plane_base + zoff + x, y0 + rr, ny, g.stride[1], per1, extrap);
+                }
             }
-        }
-        __syncthreads();
-        // interface between nodes x-1 and x of row r (x = nx: the row's last interface)
-        if (r < rows_valid) {
-            const T* row = plane + (size_t)(r + 3) * nx;
-            T a[6];
-            if (x >= 3 && x + 2 < nx) {
+            __syncthreads();
+            // interface between nodes x-1 and x of row r (x = nx: the row's last interface)
+            if (r < rows_valid) {
+                const T* row = plane + (size_t)(r + 3) * nx;
+                T a[6];
+                if (x >= 3 && x + 2 < nx) {
 #pragma unroll
-                for (int k = 0; k < 6; ++k) a[k] = row[x - 3 + k];
-            } else {
+                    for (int k = 0; k < 6; ++k) a[k] = row[x - 3 + k];
+                } else {
 #pragma unroll
-                for (int k = 0; k < 6; ++k) a[k] = row_value(row, x - 3 + k, nx, per0, extrap);
+                    for (int k = 0; k < 6; ++k) a[k] = row_value(row, x - 3 + k, nx, per0, extrap);
+                }
+                T ppj, pmj1;
+                weno_iface(a[1] - a[0], a[2] - a[1], a[3] - a[2], a[4] - a[3], a[5] - a[4], floor_raw, inv_dx0, ppj,
+                           pmj1);
+                if (x >= 1) pxp[(size_t)r * nx + x - 1] = ppj;
+                if (x < nx) pxm[(size_t)r * nx + x] = pmj1;
             }
-            T ppj, pmj1;
-            weno_iface(a[1] - a[0], a[2] - a[1], a[3] - a[2], a[4] - a[3], a[5] - a[4], floor_raw, inv_dx0, ppj,
-                       pmj1);
-            if (x >= 1) pxp[(size_t)r * nx + x - 1] = ppj;
-            if (x < nx) pxm[(size_t)r * nx + x] = pmj1;
+            __syncthreads();
         }
-        __syncthreads();
         if (node) {
             T pm[D], pp[D];
-            pm[0] = pxm[(size_t)r * nx + x];
-            pp[0] = pxp[(size_t)r * nx + x];
-            {
-                T v[7];
-#pragma unroll
-                for (int k = 0; k < 7; ++k) v[k] = plane[(size_t)(r + k) * nx + x];
-                weno5_pair<T>(v, dx1, floor_raw, pm[1], pp[1]);
-            }
-            if constexpr (D == 4) {
-                T v[7];
-                gather7<T>(u, colbase + zoff, i2, g.n[2], g.stride[2], (g.periodic_mask >> 2) & 1u, extrap, v);
-                weno5_pair<T>(v, T(g.dx[2]), floor_raw, pm[2], pp[2]);
-            }
+            T next = T(0);
             if constexpr (D >= 3) {
-                T next;
                 weno_iface(q[1] - q[0], q[2] - q[1], q[3] - q[2], q[4] - q[3], q[5] - q[4], floor_raw, inv_dxs,
                            pp[SD], next);
                 pm[SD] = carry;
-                carry = next;
             }
-            int idx[4] = {x, y, 0, 0};
-            if (D == 3) idx[2] = z;
-            if (D == 4) { idx[2] = i2; idx[3] = z; }
-            T yd = lf_term_dyn<T, D, DYN>(P, idx, pm, pp);
-            if (P.brt_min0) yd = fmin(yd, T(0));
-            const long long flat = colbase + zoff;
-            T res;
-            if (P.mode == kTerm) {
-                res = yd;
-            } else {
-                const T w = center + T(P.dt) * yd;
-                res = w;
-                if (P.cv != 0.0) res = T(P.cv) * ld(vn + flat) + T(P.cu) * w;
-                if (P.minv_after) res = fmin(res, ld(vn + flat));
+            if (!warm) {
+                pm[0] = pxm[(size_t)r * nx + x];
+                pp[0] = pxp[(size_t)r * nx + x];
+                {
+                    T v[7];
+#pragma unroll
+                    for (int k = 0; k < 7; ++k) v[k] = plane[(size_t)(r + k) * nx + x];
+                    weno5_pair<T>(v, dx1, floor_raw, pm[1], pp[1]);
+                }
+                if constexpr (D == 4) {
+                    T v[7];
+                    gather7<T>(u, colbase + zoff, i2, g.n[2], g.stride[2], (g.periodic_mask >> 2) & 1u, extrap, v);
+                    weno5_pair<T>(v, T(g.dx[2]), floor_raw, pm[2], pp[2]);
+                }
+                int idx[4] = {x, y, 0, 0};
+                if (D == 3) idx[2] = z;
+                if (D == 4) { idx[2] = i2; idx[3] = z; }
+                T yd = lf_term_dyn<T, D, DYN>(P, idx, pm, pp);
+                if (P.brt_min0) yd = fmin(yd, T(0));
+                const long long flat = colbase + zoff;
+                T res;
+                if (P.mode == kTerm) {
+                    res = yd;
+                } else {
+                    const T w = center + T(P.dt) * yd;
+                    res = w;
+                    if (P.cv != 0.0) res = T(P.cv) * ld(vn + flat) + T(P.cu) * w;
+                    if (P.minv_after) res = fmin(res, ld(vn + flat));
+                }
+                out[flat] = res;
             }
-            out[flat] = res;
             if constexpr (D >= 3) {
+                carry = next;
 #pragma unroll
                 for (int k = 0; k < 5; ++k) q[k] = q[k + 1];
             }
