@@ -289,8 +289,9 @@ int rows_bps(const StageParams& P, const RowsCfg& c, int dtype) {
     return dtype == HJ_F64 ? rows_blocks_per_sm_f64(P, c) : rows_blocks_per_sm_f32(P, c);
 }
 
-cudaError_t rows_launch(hj_ctx* ctx, const StageParams& P, const RowsCfg& c, int dtype) {
+cudaError_t rows_launch(hj_ctx* ctx, const StageParams& P0, const RowsCfg& c, int dtype) {
     ctx->launches += 1;
+    const StageParams P = finalize(P0);
     return dtype == HJ_F64 ? launch_rows_f64(P, c, ctx->stream) : launch_rows_f32(P, c, ctx->stream);
 }
 
@@ -413,7 +414,8 @@ cudaError_t launch_stage(hj_ctx* ctx, const StageParams& P, int scheme, int dtyp
         return rows_launch(ctx, P, c, dtype);
     }
     ctx->launches += 1;
-    return dtype == HJ_F64 ? launch_stage_f64(P, scheme, ctx->stream) : launch_stage_f32(P, scheme, ctx->stream);
+    const StageParams Q = finalize(P);
+    return dtype == HJ_F64 ? launch_stage_f64(Q, scheme, ctx->stream) : launch_stage_f32(Q, scheme, ctx->stream);
 }
 
 // Three fused stage launches of one TVD-RK3 step (Listing 6):

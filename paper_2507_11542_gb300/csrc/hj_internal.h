@@ -44,7 +44,28 @@ struct StageParams {
     const double* trig_d;  // cos, sin of the dimension-2 coordinate: [cos(0..n2-1), sin(0..n2-1)]
     const float* trig_f;
     double weno_floor;     // additive floor of the WENO5 epsilon, in raw-difference units
+    // FP32 copies of the scalars above, so that FP32 kernels do no FP64 arithmetic
+    float lo_f[kMaxDim], dx_f[kMaxDim], inv_dx_f[kMaxDim];
+    float params_f[8];
+    float dt_f, cv_f, cu_f, weno_floor_f;
+    int has_vn;            // the stage reads Vn (cv != 0 or minv_after)
 };
+
+// Fills the FP32 copies and has_vn from the FP64 fields (call before launching).
+inline StageParams finalize(StageParams p) {
+    for (int d = 0; d < kMaxDim; ++d) {
+        p.lo_f[d] = (float)p.g.lo[d];
+        p.dx_f[d] = (float)p.g.dx[d];
+        p.inv_dx_f[d] = (float)p.g.inv_dx[d];
+    }
+    for (int k = 0; k < 8; ++k) p.params_f[k] = (float)p.params[k];
+    p.dt_f = (float)p.dt;
+    p.cv_f = (float)p.cv;
+    p.cu_f = (float)p.cu;
+    p.weno_floor_f = (float)p.weno_floor;
+    p.has_vn = (p.mode == kStage) && (p.cv != 0.0 || p.minv_after);
+    return p;
+}
 
 struct UpwindParams {
     GridDev g;

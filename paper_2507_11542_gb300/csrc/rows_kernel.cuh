@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(RowsLimits<T>::kMaxThreads) rows_kernel(const 
     const T* __restrict__ u = static_cast<const T*>(P.u);
     const T* __restrict__ vn = static_cast<const T*>(P.vn);
     T* __restrict__ out = static_cast<T*>(P.out);
-    const T floor_raw = T(P.weno_floor);
+    const T floor_raw = SP<T>::floor(P);
     const bool per0 = g.periodic_mask & 1u, per1 = (g.periodic_mask >> 1) & 1u;
     const int extrap = g.extrap;
 
@@ -100,9 +100,12 @@ __global__ void __launch_bounds__(RowsLimits<T>::kMaxThreads) rows_kernel(const 
     const long long plane_base = (D == 4) ? (long long)i2 * g.stride[2] : 0;
     const long long colbase = plane_base + (long long)min(x, nx - 1) + (long long)y * g.stride[1];
 
-    const T inv_dx0 = T(g.inv_dx[0]);
-    const T inv_dxs = T(g.inv_dx[SD]);
-    const T dx1 = T(g.dx[1]);
+    const T inv_dx0 = SP<T>::inv_dx(P, 0);
+    const T inv_dx1 = SP<T>::inv_dx(P, 1);
+    const T inv_dxs = SP<T>::inv_dx(P, SD);
+    const T dt = SP<T>::dt(P), cv = SP<T>::cv(P), cu = SP<T>::cu(P);
+    const bool has_vn = P.has_vn, use_cv = P.cv != 0.0, minv = P.minv_after, brt0 = P.brt_min0;
+    const bool term_mode = P.mode == kTerm;
 
     // Halo rows this thread loads every plane: rows -3..-1 and rows_valid..TY+2
     // (past the grid edge: ghost rows), distributed over the thread rows.
@@ -174,30 +177,38 @@ __global__ void __launch_bounds__(RowsLimits<T>::kMaxThreads) rows_kernel(const 
                 pm[0] = pxm[(size_t)r * nx + x];
                 pp[0] = pxp[(size_t)r * nx + x];
                 {
+                    // dimension 1: p- from the interface below the node, p+ from the one above
                     T v[7];
 #pragma unroll
                     for (int k = 0; k < 7; ++k) v[k] = plane[(size_t)(r + k) * nx + x];
-                    weno5_pair<T>(v, dx1, floor_raw, pm[1], pp[1]);
+                    T unused0, unused1;
+                    weno_iface(v[1] - v[0], v[2] - v[1], v[3] - v[2], v[4] - v[3], v[5] - v[4], floor_raw, inv_dx1,
+                               unused0, pm[1]);
+                    weno_iface(v[2] - v[1], v[3] - v[2], v[4] - v[3], v[5] - v[4], v[6] - v[5], floor_raw, inv_dx1,
+                               pp[1], unused1);
                 }
                 if constexpr (D == 4) {
                     T v[7];
                     gather7<T>(u, colbase + zoff, i2, g.n[2], g.stride[2], (g.periodic_mask >> 2) & 1u, extrap, v);
-                    weno5_pair<T>(v, T(g.dx[2]), floor_raw, pm[2], pp[2]);
+                    weno5_pair<T>(v, SP<T>::dx(P, 2), floor_raw, pm[2], pp[2]);
                 }
                 int idx[4] = {x, y, 0, 0};
                 if (D == 3) idx[2] = z;
                 if (D == 4) { idx[2] = i2; idx[3] = z; }
                 T yd = lf_term_dyn<T, D, DYN>(P, idx, pm, pp);
-                if (P.brt_min0) yd = fmin(yd, T(0));
+                if (brt0) yd = fmin(yd, T(0));
                 const long long flat = colbase + zoff;
                 T res;
-                if (P.mode == kTerm) {
+                if (term_mode) {
                     res = yd;
                 } else {
-                    const T w = center + T(P.dt) * yd;
+                    const T w = center + dt * yd;
                     res = w;
-                    if (P.cv != 0.0) res = T(P.cv) * ld(vn + flat) + T(P.cu) * w;
-                    if (P.minv_after) res = fmin(res, ld(vn + flat));
+                    if (has_vn) {
+                        const T vv = ld(vn + flat);
+                        if (use_cv) res = cv * vv + cu * w;
+                        if (minv) res = fmin(res, vv);
+                    }
                 }
                 out[flat] = res;
             }

@@ -22,7 +22,7 @@ __global__ void __launch_bounds__(kBX * kBY) stage_kernel(const StageParams P) {
     const T* __restrict__ u = static_cast<const T*>(P.u);
     const T* __restrict__ vn = static_cast<const T*>(P.vn);
     T* __restrict__ out = static_cast<T*>(P.out);
-    const T floor_raw = T(P.weno_floor);
+    const T floor_raw = SP<T>::floor(P);
     for (int z = blockIdx.z; z < nz; z += gridDim.z) {
         int idx[4] = {i0, i1, 0, 0};
         if (D > 2) { idx[2] = z % g.n[2]; }
@@ -43,10 +43,13 @@ __global__ void __launch_bounds__(kBX * kBY) stage_kernel(const StageParams P) {
         if (P.mode == kTerm) {
             r = y;
         } else {
-            const T w = ld(u + flat) + T(P.dt) * y;
+            const T w = ld(u + flat) + SP<T>::dt(P) * y;
             r = w;
-            if (P.cv != 0.0) r = T(P.cv) * ld(vn + flat) + T(P.cu) * w;
-            if (P.minv_after) r = fmin(r, ld(vn + flat));
+            if (P.has_vn) {
+                const T vv = ld(vn + flat);
+                if (P.cv != 0.0) r = SP<T>::cv(P) * vv + SP<T>::cu(P) * w;
+                if (P.minv_after) r = fmin(r, vv);
+            }
         }
         out[flat] = r;
     }

@@ -195,6 +195,29 @@ __device__ __forceinline__ void upwind_pair(const T v[7], double dx, double inv_
     }
 }
 
+// Scalars of a stage launch in the kernel's precision.
+template <typename T> struct SP;
+template <> struct SP<double> {
+    static __device__ __forceinline__ double lo(const StageParams& P, int d) { return P.g.lo[d]; }
+    static __device__ __forceinline__ double dx(const StageParams& P, int d) { return P.g.dx[d]; }
+    static __device__ __forceinline__ double inv_dx(const StageParams& P, int d) { return P.g.inv_dx[d]; }
+    static __device__ __forceinline__ double param(const StageParams& P, int k) { return P.params[k]; }
+    static __device__ __forceinline__ double dt(const StageParams& P) { return P.dt; }
+    static __device__ __forceinline__ double cv(const StageParams& P) { return P.cv; }
+    static __device__ __forceinline__ double cu(const StageParams& P) { return P.cu; }
+    static __device__ __forceinline__ double floor(const StageParams& P) { return P.weno_floor; }
+};
+template <> struct SP<float> {
+    static __device__ __forceinline__ float lo(const StageParams& P, int d) { return P.lo_f[d]; }
+    static __device__ __forceinline__ float dx(const StageParams& P, int d) { return P.dx_f[d]; }
+    static __device__ __forceinline__ float inv_dx(const StageParams& P, int d) { return P.inv_dx_f[d]; }
+    static __device__ __forceinline__ float param(const StageParams& P, int k) { return P.params_f[k]; }
+    static __device__ __forceinline__ float dt(const StageParams& P) { return P.dt_f; }
+    static __device__ __forceinline__ float cv(const StageParams& P) { return P.cv_f; }
+    static __device__ __forceinline__ float cu(const StageParams& P) { return P.cu_f; }
+    static __device__ __forceinline__ float floor(const StageParams& P) { return P.weno_floor_f; }
+};
+
 // ---------------------------------------------------------------------------
 // Hamiltonian + Lax-Friedrichs dissipation (Sec. 4):
 //   ydot = Hg(x, (p- + p+)/2) + sum_d alpha_d(x) (p+_d - p-_d)/2
@@ -210,38 +233,38 @@ __device__ __forceinline__ T lf_term_dyn(const StageParams& P, const int* idx, c
     for (int d = 0; d < D; ++d) {
         pb[d] = T(0.5) * (pm[d] + pp[d]);
         dd[d] = T(0.5) * (pp[d] - pm[d]);
-        x[d] = T(P.g.lo[d] + (double)idx[d] * P.g.dx[d]);
+        x[d] = SP<T>::lo(P, d) + T(idx[d]) * SP<T>::dx(P, d);
     }
-    const double* q = P.params;
+    const auto q = [&P](int k) { return SP<T>::param(P, k); };
     T y = T(0);
     if constexpr (DYN == HJ_DYN_DOUBLE_INTEGRATOR && D == 2) {
-        const T umax = T(q[0]);
+        const T umax = q(0);
         y = pb[0] * x[1] - umax * fabs(pb[1]) + fabs(x[1]) * dd[0] + umax * dd[1];
     } else if constexpr (DYN == HJ_DYN_AIR3D && D == 3) {
         const T* tr = Trig<T>::get(P);
         const T c = tr[idx[2]], s = tr[P.g.n[2] + idx[2]];
-        const T va = T(q[0]), vb = T(q[1]), amax = T(q[2]), bmax = T(q[3]);
+        const T va = q(0), vb = q(1), amax = q(2), bmax = q(3);
         const T f0 = -va + vb * c, f1 = vb * s;
         y = pb[0] * f0 + pb[1] * f1 + amax * fabs(pb[0] * x[1] - pb[1] * x[0] - pb[2]) - bmax * fabs(pb[2]);
         y += (fabs(f0) + amax * fabs(x[1])) * dd[0] + (fabs(f1) + amax * fabs(x[0])) * dd[1] + (amax + bmax) * dd[2];
     } else if constexpr (DYN == HJ_DYN_DUBINS4D && D == 4) {
         const T* tr = Trig<T>::get(P);
         const T c = tr[idx[2]], s = tr[P.g.n[2] + idx[2]];
-        const T wmax = T(q[0]), accmax = T(q[1]);
+        const T wmax = q(0), accmax = q(1);
         const T f0 = x[3] * c, f1 = x[3] * s;
         y = pb[0] * f0 + pb[1] * f1 - wmax * fabs(pb[2]) - accmax * fabs(pb[3]);
         y += fabs(f0) * dd[0] + fabs(f1) * dd[1] + wmax * dd[2] + accmax * dd[3];
     } else if constexpr (DYN == HJ_DYN_NORM) {
-        const T c = T(q[0]);
+        const T c = q(0);
         T s2 = T(0), diss = T(0);
 #pragma unroll
         for (int d = 0; d < D; ++d) { s2 += pb[d] * pb[d]; diss += dd[d]; }
         y = -c * sqrt(s2) + c * diss;
     } else if constexpr (DYN == HJ_DYN_ADVECT) {
 #pragma unroll
-        for (int d = 0; d < D; ++d) { const T c = T(q[d]); y += -c * pb[d] + fabs(c) * dd[d]; }
+        for (int d = 0; d < D; ++d) { const T c = q(d); y += -c * pb[d] + fabs(c) * dd[d]; }
     } else if constexpr (DYN == HJ_DYN_ROTATE && D >= 2) {
-        const T w = T(q[0]);
+        const T w = q(0);
         const T f0 = -w * x[1], f1 = w * x[0];
         y = -(pb[0] * f0 + pb[1] * f1) + fabs(f0) * dd[0] + fabs(f1) * dd[1];
     }

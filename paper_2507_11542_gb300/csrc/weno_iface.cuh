@@ -3,62 +3,68 @@
 // node j+1 use the same five differences
 //   e1..e5 = v_{j-1}-v_{j-2}, v_j-v_{j-1}, v_{j+1}-v_j, v_{j+2}-v_{j+1}, v_{j+3}-v_{j+2}
 // (mirrored), hence the same three smoothness indicators and epsilon; only
-// the candidate stencils and the ideal weights' order differ. Computing both
-// from one interface halves the smoothness work per node along a dimension.
+// the candidate stencils and the order of the ideal weights differ:
 //
 //   windows A = (e1,e2,e3), B = (e2,e3,e4), C = (e3,e4,e5)
 //   SA = 13/12 (e1-2e2+e3)^2 + 1/4 (e1-4e2+3e3)^2
 //   SB = 13/12 (e2-2e3+e4)^2 + 1/4 (e2-e4)^2
 //   SC = 13/12 (e3-2e4+e5)^2 + 1/4 (3e3-4e4+e5)^2
-//   p-_{j+1}: candidates (2e1-7e2+11e3, -e2+5e3+2e4, 2e3+5e4-e5)/6, weights 0.1, 0.6, 0.3 on SA, SB, SC
-//   p+_j    : candidates (2e5-7e4+11e3, -e4+5e3+2e2, 2e3+5e2-e1)/6, weights 0.1, 0.6, 0.3 on SC, SB, SA
-//   eps = 1e-6 max(e_k^2) + floor (raw differences; the result is divided by dx)
+//   eps = 1e-6 max(e_k^2) + floor
+//   p-_{j+1} = sum_k w_k phi_k, phi = (2e1-7e2+11e3, -e2+5e3+2e4, 2e3+5e4-e5)/6,
+//              w ~ (0.1, 0.6, 0.3) / (S+eps)^2 over (SA, SB, SC)
+//   p+_j     = sum_k w_k psi_k, psi = (2e5-7e4+11e3, -e4+5e3+2e2, 2e3+5e2-e1)/6,
+//              w ~ (0.1, 0.6, 0.3) / (S+eps)^2 over (SC, SB, SA)
+//
+// Evaluated here in an equivalent form (the weights sum to one):
+//   p- = phi2 + (w1 T1/3 + w3 T2/6),   p+ = psi2 - (w1' T2/3 + w3' T1/6)
+// with the third differences T1 = e1-3e2+3e3-e4 = tA-tB and T2 = e2-3e3+3e4-e5
+// = tB-tC shared by both sides, and the smoothness indicators scaled by 12/13
+// (S~ = t^2 + 3/13 u^2, eps scaled alike), which leaves every weight unchanged.
+// All differences are raw (not divided by dx); the results are divided by dx.
 #pragma once
 
 #include <cuda_runtime.h>
 
 namespace hj {
 
-// Smoothness indicators and epsilon of one interface.
-template <typename T>
-__device__ __forceinline__ void weno_smooth(T e1, T e2, T e3, T e4, T e5, T floor_raw, T& SA, T& SB, T& SC, T& eps) {
-    const T c13 = T(13) / T(12);
-    const T tA = e1 - T(2) * e2 + e3;
-    const T tB = e2 - T(2) * e3 + e4;
-    const T tC = e3 - T(2) * e4 + e5;
-    const T uA = e1 - T(4) * e2 + T(3) * e3;
-    const T uB = e2 - e4;
-    const T uC = T(3) * e3 - T(4) * e4 + e5;
-    SA = c13 * tA * tA + T(0.25) * uA * uA;
-    SB = c13 * tB * tB + T(0.25) * uB * uB;
-    SC = c13 * tC * tC + T(0.25) * uC * uC;
-    const T m = fmax(fmax(fmax(e1 * e1, e2 * e2), fmax(e3 * e3, e4 * e4)), e5 * e5);
-    eps = T(1e-6) * m + floor_raw;
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
 }
 
-// FP32: fast reciprocals of (S+eps)^2 >= 1e-36 (normal) and of each side's
-// weight sum; candidates carry their ideal weight and the 1/6.
+// FP32. (S~ + eps~)^2 >= (12/13 * 1e-18)^2 stays a normal number, so the
+// approximate reciprocals neither overflow nor divide by zero.
 __device__ __forceinline__ void weno_iface(float e1, float e2, float e3, float e4, float e5, float floor_raw,
                                            float inv_dx, float& pp_j, float& pm_j1) {
-    float SA, SB, SC, eps;
-    weno_smooth<float>(e1, e2, e3, e4, e5, floor_raw, SA, SB, SC, eps);
-    const float rA = __fdividef(1.0f, (SA + eps) * (SA + eps));
-    const float rB = __fdividef(1.0f, (SB + eps) * (SB + eps));
-    const float rC = __fdividef(1.0f, (SC + eps) * (SC + eps));
-    // left of j+1
-    const float l1 = (0.1f / 6.0f) * (2.0f * e1 - 7.0f * e2 + 11.0f * e3);
-    const float l2 = (0.6f / 6.0f) * (-e2 + 5.0f * e3 + 2.0f * e4);
-    const float l3 = (0.3f / 6.0f) * (2.0f * e3 + 5.0f * e4 - e5);
-    const float numL = rA * l1 + rB * l2 + rC * l3;
-    const float denL = 0.1f * rA + 0.6f * rB + 0.3f * rC;
-    // right of j
-    const float q1 = (0.1f / 6.0f) * (2.0f * e5 - 7.0f * e4 + 11.0f * e3);
-    const float q2 = (0.6f / 6.0f) * (-e4 + 5.0f * e3 + 2.0f * e2);
-    const float q3 = (0.3f / 6.0f) * (2.0f * e3 + 5.0f * e2 - e1);
-    const float numR = rC * q1 + rB * q2 + rA * q3;
-    const float denR = 0.1f * rC + 0.6f * rB + 0.3f * rA;
-    pm_j1 = numL * __fdividef(inv_dx, denL);
-    pp_j = numR * __fdividef(inv_dx, denR);
+    const float k = 3.0f / 13.0f;
+    const float tA = fmaf(-2.0f, e2, e1) + e3;
+    const float tB = fmaf(-2.0f, e3, e2) + e4;
+    const float tC = fmaf(-2.0f, e4, e3) + e5;
+    const float uA = fmaf(2.0f, e3 - e2, tA);  // e1 - 4e2 + 3e3
+    const float uB = e2 - e4;
+    const float uC = fmaf(2.0f, e3 - e4, tC);  // 3e3 - 4e4 + e5
+    const float SA = fmaf(tA, tA, uA * (k * uA));
+    const float SB = fmaf(tB, tB, uB * (k * uB));
+    const float SC = fmaf(tC, tC, uC * (k * uC));
+    const float amax = fmaxf(fmaxf(fmaxf(fabsf(e1), fabsf(e2)), fmaxf(fabsf(e3), fabsf(e4))), fabsf(e5));
+    const float eps = fmaf((12.0f / 13.0f) * 1e-6f, amax * amax, (12.0f / 13.0f) * floor_raw);
+    const float sA = SA + eps, sB = SB + eps, sC = SC + eps;
+    const float rA = rcp_approx(sA * sA);
+    const float rB = rcp_approx(sB * sB);
+    const float rC = rcp_approx(sC * sC);
+    const float T1 = tA - tB, T2 = tB - tC;
+    const float X = rA * T1, Y = rC * T2;
+    const float b6 = 0.6f * rB;
+    const float denL = fmaf(0.1f, rA, fmaf(0.3f, rC, b6));
+    const float denR = fmaf(0.3f, rA, fmaf(0.1f, rC, b6));
+    const float numL = fmaf(1.0f / 30.0f, X, 0.05f * Y);
+    const float numR = fmaf(0.05f, X, (1.0f / 30.0f) * Y);
+    const float c5 = (5.0f / 6.0f) * e3;
+    const float phi2 = fmaf(1.0f / 3.0f, e4, fmaf(-1.0f / 6.0f, e2, c5));
+    const float psi2 = fmaf(1.0f / 3.0f, e2, fmaf(-1.0f / 6.0f, e4, c5));
+    pm_j1 = fmaf(numL, rcp_approx(denL), phi2) * inv_dx;
+    pp_j = fmaf(-numR, rcp_approx(denR), psi2) * inv_dx;
 }
 
 // Integer maximum of non-negative doubles (their bit patterns order alike):
@@ -68,51 +74,64 @@ __device__ __forceinline__ double nonneg_max(double a, double b) {
     return __longlong_as_double(ia > ib ? ia : ib);
 }
 
-// FP64: weights normalised by products of the d_k = (S_k+eps)^2,
-//   p = sum_k c_k q_k prod_{i!=k} d_i / sum_k c_k prod_{i!=k} d_i,
+__device__ __forceinline__ double abs_bits(double a) {
+    return __longlong_as_double(__double_as_longlong(a) & 0x7fffffffffffffffLL);
+}
+
+// 1/x for a positive normal double: the hardware estimate refined by two
+// Newton-Raphson steps r <- r + r (1 - x r) (each squares the relative error).
+__device__ __forceinline__ double rcp_newton(double x) {
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+    double e = fma(-x, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-x, r, 1.0);
+    return fma(r, e, r);
+}
+
+// FP64. Weights normalised by products of the d_k = (S~_k + eps~)^2:
+//   w_k = c_k prod_{i!=k} d_i / sum_m c_m prod_{i!=m} d_i,
 // and both sides share one reciprocal 1/(denL denR). When that product
 // leaves [1e-290, 1e290] (nearly flat or huge data) each side divides alone,
-// and an exactly flat window (den = 0) returns its zero candidate.
+// and an exactly flat window (den = 0) returns its central candidate.
 __device__ __forceinline__ void weno_iface(double e1, double e2, double e3, double e4, double e5, double floor_raw,
                                            double inv_dx, double& pp_j, double& pm_j1) {
-    const double c13 = 13.0 / 12.0;
-    const double tA = e1 - 2.0 * e2 + e3;
-    const double tB = e2 - 2.0 * e3 + e4;
-    const double tC = e3 - 2.0 * e4 + e5;
-    const double uA = e1 - 4.0 * e2 + 3.0 * e3;
+    const double k = 3.0 / 13.0;
+    const double tA = fma(-2.0, e2, e1) + e3;
+    const double tB = fma(-2.0, e3, e2) + e4;
+    const double tC = fma(-2.0, e4, e3) + e5;
+    const double uA = fma(2.0, e3 - e2, tA);
     const double uB = e2 - e4;
-    const double uC = 3.0 * e3 - 4.0 * e4 + e5;
-    const double SA = c13 * tA * tA + 0.25 * uA * uA;
-    const double SB = c13 * tB * tB + 0.25 * uB * uB;
-    const double SC = c13 * tC * tC + 0.25 * uC * uC;
-    const double m = nonneg_max(nonneg_max(nonneg_max(e1 * e1, e2 * e2), nonneg_max(e3 * e3, e4 * e4)), e5 * e5);
-    const double eps = 1e-6 * m + floor_raw;
-    const double dA = (SA + eps) * (SA + eps);
-    const double dB = (SB + eps) * (SB + eps);
-    const double dC = (SC + eps) * (SC + eps);
+    const double uC = fma(2.0, e3 - e4, tC);
+    const double SA = fma(tA, tA, uA * (k * uA));
+    const double SB = fma(tB, tB, uB * (k * uB));
+    const double SC = fma(tC, tC, uC * (k * uC));
+    const double amax = nonneg_max(nonneg_max(nonneg_max(abs_bits(e1), abs_bits(e2)),
+                                              nonneg_max(abs_bits(e3), abs_bits(e4))), abs_bits(e5));
+    const double eps = fma((12.0 / 13.0) * 1e-6, amax * amax, (12.0 / 13.0) * floor_raw);
+    const double sA = SA + eps, sB = SB + eps, sC = SC + eps;
+    const double dA = sA * sA, dB = sB * sB, dC = sC * sC;
     const double PA = dB * dC, PB = dA * dC, PC = dA * dB;
-    const double l1 = (0.1 / 6.0) * (2.0 * e1 - 7.0 * e2 + 11.0 * e3);
-    const double l2 = (0.6 / 6.0) * (-e2 + 5.0 * e3 + 2.0 * e4);
-    const double l3 = (0.3 / 6.0) * (2.0 * e3 + 5.0 * e4 - e5);
-    const double q1 = (0.1 / 6.0) * (2.0 * e5 - 7.0 * e4 + 11.0 * e3);
-    const double q2 = (0.6 / 6.0) * (-e4 + 5.0 * e3 + 2.0 * e2);
-    const double q3 = (0.3 / 6.0) * (2.0 * e3 + 5.0 * e2 - e1);
-    const double numL = PA * l1 + PB * l2 + PC * l3;
-    const double denL = 0.1 * PA + 0.6 * PB + 0.3 * PC;
-    const double numR = PC * q1 + PB * q2 + PA * q3;
-    const double denR = 0.1 * PC + 0.6 * PB + 0.3 * PA;
+    const double T1 = tA - tB, T2 = tB - tC;
+    const double X = PA * T1, Y = PC * T2;
+    const double b6 = 0.6 * PB;
+    const double denL = fma(0.1, PA, fma(0.3, PC, b6));
+    const double denR = fma(0.3, PA, fma(0.1, PC, b6));
+    const double numL = fma(1.0 / 30.0, X, 0.05 * Y);
+    const double numR = fma(0.05, X, (1.0 / 30.0) * Y);
+    const double c5 = (5.0 / 6.0) * e3;
+    const double phi2 = fma(1.0 / 3.0, e4, fma(-1.0 / 6.0, e2, c5));
+    const double psi2 = fma(1.0 / 3.0, e2, fma(-1.0 / 6.0, e4, c5));
     const double den2 = denL * denR;
-    // range test on the exponent field (integer pipe): 1e-290 < den2 < 1e290
     const long long bits = __double_as_longlong(den2);
-    const int expo = (int)((bits >> 52) & 0x7ff);
+    const int expo = (int)((bits >> 52) & 0x7ff);  // 1e-290 < den2 < 1e290 (integer test)
     if (expo > 60 && expo < 1986) {
-        const double r = inv_dx / den2;
-        pm_j1 = numL * denR * r;
-        pp_j = numR * denL * r;
+        const double r = rcp_newton(den2);
+        pm_j1 = fma(numL * denR, r, phi2) * inv_dx;
+        pp_j = fma(-numR * denL, r, psi2) * inv_dx;
     } else {
-        // l2 / 0.6 and q2 / 0.6 are the unweighted central candidates
-        pm_j1 = denL > 0.0 ? numL * inv_dx / denL : l2 / 0.6 * inv_dx;
-        pp_j = denR > 0.0 ? numR * inv_dx / denR : q2 / 0.6 * inv_dx;
+        pm_j1 = (denL > 0.0 ? phi2 + numL / denL : phi2) * inv_dx;
+        pp_j = (denR > 0.0 ? psi2 - numR / denR : psi2) * inv_dx;
     }
 }
 
