@@ -188,6 +188,38 @@ hj_status hj_rk3_stage(hj_ctx* ctx, const hj_grid* grid, const hj_method* method
 hj_status hj_solve(hj_ctx* ctx, const hj_problem* problem, void* out_slices, int32_t out_on_device,
                    double* out_times, hj_stats* stats);
 
+/* No-allocation variant of hj_rk3_step. -------------------------------- */
+
+/* Capacity of the fixed scratch used by hj_rk3_step_static. */
+#define HJ_STATIC_MAX_NODES (1 << 20)  /* grid nodes per call (101^3 fits) */
+#define HJ_STATIC_MAX_ANGLES 4096      /* nodes along dimension 2 for air3D / Dubins4D */
+
+/* The paper has no counterpart of this call; it exists for callers that may
+ * not allocate device memory while they run -- for example a real-time
+ * control loop (a safety filter that re-solves its reachable set every cycle)
+ * where allocation after start-up is forbidden because cudaMalloc can block
+ * and fragment memory, or a host application that owns the GPU's memory pool
+ * and admits no other allocator. It needs no hj_ctx.
+ *
+ * Same arithmetic as hj_rk3_step: one TVD-RK3 step of size dt, in place on the
+ * caller's device array v (prod(n) elements of dtype, on `device`), enqueued
+ * on `cuda_stream` (a cudaStream_t; NULL = legacy default stream). The two
+ * stage buffers and the heading-angle tables live in one fixed __device__
+ * array of 2 * HJ_STATIC_MAX_NODES * 8 bytes plus 96 KiB (about 16 MiB) that
+ * every GPU which loads this library holds until the process exits. The call
+ * performs no cudaMalloc/cudaFree and calls no allocating routine.
+ *  - The first call on a device looks up that array's device address
+ *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  - All calls share the one array, and nothing in it needs to start at zero:
+ *    each call writes every element it later reads. Calls whose work overlaps
+ *    on the GPU (e.g. on two streams at once) race on it; serialise them.
+ *  - Asynchronous: returns after enqueueing.
+ * Errors: HJ_EINVAL for a malformed argument, for prod(n) > HJ_STATIC_MAX_NODES,
+ * or for more than HJ_STATIC_MAX_ANGLES nodes along dimension 2 with air3D or
+ * Dubins4D dynamics (nothing is enqueued); HJ_ECUDA if a CUDA call fails. */
+hj_status hj_rk3_step_static(void* cuda_stream, int32_t device, const hj_grid* grid, const hj_method* method,
+                             int32_t dtype, void* v, double dt);
+
 #ifdef __cplusplus
 }
 #endif

@@ -31,7 +31,10 @@ HJ_EXTRAP_AWAY_FROM_ZERO, HJ_EXTRAP_LINEAR = 0, 1
 
 # every function include/hj.h declares (checked by the test-suite against the .so)
 EXPORTS = ["hj_ctx_create", "hj_ctx_destroy", "hj_status_str", "hj_ctx_last_error", "hj_version",
-           "hj_upwind", "hj_term", "hj_step_bound", "hj_rk3_step", "hj_rk3_stage", "hj_solve"]
+           "hj_upwind", "hj_term", "hj_step_bound", "hj_rk3_step", "hj_rk3_stage", "hj_solve",
+           "hj_rk3_step_static"]
+HJ_STATIC_MAX_NODES = 1 << 20
+HJ_STATIC_MAX_ANGLES = 4096
 
 
 class hj_grid(ctypes.Structure):
@@ -98,6 +101,8 @@ def load():
             L.hj_rk3_stage.argtypes = [_vp, _P(hj_grid), _P(hj_method), ctypes.c_int32, ctypes.c_int32, _vp, _vp, _vp,
                                        ctypes.c_double]
             L.hj_solve.argtypes = [_vp, _P(hj_problem), _vp, ctypes.c_int32, _P(ctypes.c_double), _P(hj_stats)]
+            L.hj_rk3_step_static.argtypes = [_vp, ctypes.c_int32, _P(hj_grid), _P(hj_method), ctypes.c_int32, _vp,
+                                             ctypes.c_double]
             _lib = L
     return _lib
 
@@ -216,6 +221,12 @@ def hj_rk3_step(ctx, grid: hj_grid, method: hj_method, dtype: int, v, dt: float)
 def hj_rk3_stage(ctx, grid: hj_grid, method: hj_method, dtype: int, stage: int, u, vn, out, dt: float) -> None:
     _check(ctx, load().hj_rk3_stage(_vp(ctx), ctypes.byref(grid), ctypes.byref(method), dtype, int(stage),
                                     _vp(_ptr(u)), _vp(_ptr(vn)), _vp(_ptr(out)), float(dt)))
+
+
+def hj_rk3_step_static(stream: int, device: int, grid: hj_grid, method: hj_method, dtype: int, v, dt: float) -> int:
+    """No-allocation RK3 step; returns the raw hj_status (there is no context for a message)."""
+    return load().hj_rk3_step_static(_vp(stream or 0), int(device), ctypes.byref(grid), ctypes.byref(method), dtype,
+                                     _vp(_ptr(v)), float(dt))
 
 
 def hj_solve(ctx, problem: hj_problem, out_slices_ptr: int, out_on_device: bool, out_times: np.ndarray | None):
