@@ -309,7 +309,7 @@ std::vector<RowsCfg> rows_candidates(hj_ctx* ctx, const StageParams& P, int dtyp
     std::vector<std::pair<double, RowsCfg>> scored;
     for (int ty : tys) {
         if (ty > ny || (nx + 1) * ty > rows_max_threads(dtype)) continue;
-        if (es * ((size_t)(ty + 6) * nx + 2 * (size_t)ty * nx) > 200 * 1024) continue;
+        if (rows_smem(nx, ty, es) > 200 * 1024) continue;
         std::vector<int> zs;
         if (D >= 3) {
             for (int tz : tzs)

@@ -84,6 +84,12 @@ struct RowsCfg {
     int row_tiles;  // ceil(n1 / ty)
 };
 
+// Dynamic shared memory of a rows_kernel block (element size es): two
+// alternating buffers of (ty + 6) padded rows of n0 + 6 and two ty x n0 arrays.
+inline size_t rows_smem(int nx, int ty, size_t es) {
+    return 2 * es * ((size_t)(ty + 6) * (size_t)(nx + 6) + 2 * (size_t)ty * (size_t)nx);
+}
+
 // Launchers (one translation unit per element type). Return the launch error.
 cudaError_t launch_stage_f64(const StageParams& p, int scheme, cudaStream_t s);
 cudaError_t launch_stage_f32(const StageParams& p, int scheme, cudaStream_t s);

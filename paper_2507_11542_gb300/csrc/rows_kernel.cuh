@@ -70,9 +70,10 @@ __global__ void __launch_bounds__(RowsLimits<T>::kMaxThreads) rows_kernel(const 
     const GridDev& g = P.g;
     const int nx = g.n[0], ny = g.n[1];
     const int TY = C.ty;
-    T* plane = reinterpret_cast<T*>(smem_raw);  // (TY + 6) rows x nx
-    T* pxm = plane + (size_t)(TY + 6) * nx;      // TY x nx : p- along dimension 0
-    T* pxp = pxm + (size_t)TY * nx;              // TY x nx : p+ along dimension 0
+    const int W = nx + 6;  // shared row: 3 ghost cells, nx nodes, 3 ghost cells
+    // two buffers, alternating by plane: (TY + 6) rows x W, then p- and p+ along dimension 0 (TY x nx each)
+    const size_t buf_elems = (size_t)(TY + 6) * W + 2 * (size_t)TY * nx;
+    T* const smem = reinterpret_cast<T*>(smem_raw);
 
     const T* __restrict__ u = static_cast<const T*>(P.u);
     const T* __restrict__ vn = static_cast<const T*>(P.vn);
@@ -81,7 +82,7 @@ __global__ void __launch_bounds__(RowsLimits<T>::kMaxThreads) rows_kernel(const 
     const bool per0 = g.periodic_mask & 1u, per1 = (g.periodic_mask >> 1) & 1u;
     const int extrap = g.extrap;
 
-    const int x = threadIdx.x;  // 0 .. nx (x == nx: last interface of the row only)
+    const int x = threadIdx.x;  // 0 .. nx; x == nx: the row's last interface and its ghost cells
     const int r = threadIdx.y;
     const int y0 = blockIdx.x * TY;
     const int y = y0 + r;
@@ -97,8 +98,10 @@ __global__ void __launch_bounds__(RowsLimits<T>::kMaxThreads) rows_kernel(const 
     const int zend = (D >= 3) ? min(ns, zbeg + C.tz) : 1;
     const long long sS = (D >= 3) ? g.stride[SD] : 0;
     const bool perS = (D >= 3) ? ((g.periodic_mask >> SD) & 1u) : false;
-    const long long plane_base = (D == 4) ? (long long)i2 * g.stride[2] : 0;
-    const long long colbase = plane_base + (long long)min(x, nx - 1) + (long long)y * g.stride[1];
+    // the chunk's streamed-dimension reads stay inside the grid: no ghost logic needed
+    const bool z_inside = (D < 3) || (zbeg >= 3 && zend + 3 <= ns);
+    const T* __restrict__ uplane = u + ((D == 4) ? (long long)i2 * g.stride[2] : 0);
+    const long long colbase = (long long)min(x, nx - 1) + (long long)min(y, ny - 1) * nx;  // within a plane
 
     const T inv_dx0 = SP<T>::inv_dx(P, 0);
     const T inv_dx1 = SP<T>::inv_dx(P, 1);
@@ -107,8 +110,8 @@ __global__ void __launch_bounds__(RowsLimits<T>::kMaxThreads) rows_kernel(const 
     const bool has_vn = P.has_vn, use_cv = P.cv != 0.0, minv = P.minv_after, brt0 = P.brt_min0;
     const bool term_mode = P.mode == kTerm;
 
-    // Halo rows this thread loads every plane: rows -3..-1 and rows_valid..TY+2
-    // (past the grid edge: ghost rows), distributed over the thread rows.
+    // Halo rows (three above, three below, and rows past the grid edge in a
+    // ragged last tile) are loaded by thread rows in turn: row h of n_extra.
     const int n_extra = 3 + (TY + 3 - rows_valid);
 
     // Streamed-dimension queue: q[k] = V at plane z-2+k (k = 0..5); carry = p- at z.
@@ -119,44 +122,60 @@ __global__ void __launch_bounds__(RowsLimits<T>::kMaxThreads) rows_kernel(const 
     T carry = T(0);
     if (D >= 3 && node) {
 #pragma unroll
-        for (int k = 0; k < 5; ++k) q[k] = line_value(u + colbase, zbeg - 3 + k, ns, sS, perS, extrap);
+        for (int k = 0; k < 5; ++k) q[k] = line_value(uplane + colbase, zbeg - 3 + k, ns, sS, perS, extrap);
     }
     const int zfirst = (D >= 3) ? zbeg - 1 : zbeg;
 
     for (int z = zfirst; z < zend; ++z) {
         const bool warm = z < zbeg;  // block-uniform
         const long long zoff = (D >= 3) ? (long long)z * sS : 0;
+        const T* __restrict__ uz = uplane + zoff;
+        T* const buf = smem + (size_t)((z - zfirst) & 1) * buf_elems;
+        T* const plane = buf;
+        T* const pxm = buf + (size_t)(TY + 6) * W;
+        T* const pxp = pxm + (size_t)TY * nx;
         T center = T(0);
         if (node) {
             if (D >= 3) {
-                q[5] = line_value(u + colbase, z + 3, ns, sS, perS, extrap);
+                q[5] = z_inside ? ld(uplane + colbase + (long long)(z + 3) * sS)
+                                : line_value(uplane + colbase, z + 3, ns, sS, perS, extrap);
                 center = q[2];
             } else {
-                center = ld(u + colbase);
+                center = ld(uz + colbase);
             }
         }
         if (!warm) {
-            __syncthreads();  // the previous plane is fully consumed
-            if (node) plane[(size_t)(r + 3) * nx + x] = center;
+            // stage the plane: node rows from the threads' own values, halo rows
+            // from global memory (ghost rule along dimension 1), and the x-ghost
+            // cells of each node row from its spare thread x == nx
+            if (node) plane[(size_t)(r + 3) * W + 3 + x] = center;
             if (x < nx) {
                 for (int h = r; h < n_extra; h += TY) {
                     const int rr = (h < 3) ? h - 3 : rows_valid + (h - 3);
-                    plane[(size_t)(rr + 3) * nx + x] =
-                        line_value(u + plane_base + zoff + x, y0 + rr, ny, g.stride[1], per1, extrap);
+                    plane[(size_t)(rr + 3) * W + 3 + x] = line_value(uz + x, y0 + rr, ny, (long long)nx, per1, extrap);
+                }
+            } else if (r < rows_valid) {
+                const T* rowg = uz + (long long)y * nx;
+                T* rows = plane + (size_t)(r + 3) * W;
+                if (per0) {
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        rows[k] = ld(rowg + ((nx - 3 + k) % nx + nx) % nx);
+                        rows[nx + 3 + k] = ld(rowg + k % nx);
+                    }
+                } else {
+                    const T e0 = ld(rowg), e1 = ld(rowg + 1), f0 = ld(rowg + nx - 1), f1 = ld(rowg + nx - 2);
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        rows[k] = ghost_value(e0, e1, 3 - k, extrap);
+                        rows[nx + 3 + k] = ghost_value(f0, f1, k + 1, extrap);
+                    }
                 }
             }
             __syncthreads();
             // interface between nodes x-1 and x of row r (x = nx: the row's last interface)
             if (r < rows_valid) {
-                const T* row = plane + (size_t)(r + 3) * nx;
-                T a[6];
-                if (x >= 3 && x + 2 < nx) {
-#pragma unroll
-                    for (int k = 0; k < 6; ++k) a[k] = row[x - 3 + k];
-                } else {
-#pragma unroll
-                    for (int k = 0; k < 6; ++k) a[k] = row_value(row, x - 3 + k, nx, per0, extrap);
-                }
+                const T* a = plane + (size_t)(r + 3) * W + x;  // a[k] = value at node x - 3 + k
                 T ppj, pmj1;
                 weno_iface(a[1] - a[0], a[2] - a[1], a[3] - a[2], a[4] - a[3], a[5] - a[4], floor_raw, inv_dx0, ppj,
                            pmj1);
@@ -178,9 +197,10 @@ __global__ void __launch_bounds__(RowsLimits<T>::kMaxThreads) rows_kernel(const 
                 pp[0] = pxp[(size_t)r * nx + x];
                 {
                     // dimension 1: p- from the interface below the node, p+ from the one above
+                    const T* c = plane + (size_t)r * W + 3 + x;
                     T v[7];
 #pragma unroll
-                    for (int k = 0; k < 7; ++k) v[k] = plane[(size_t)(r + k) * nx + x];
+                    for (int k = 0; k < 7; ++k) v[k] = c[(size_t)k * W];
                     T unused0, unused1;
                     weno_iface(v[1] - v[0], v[2] - v[1], v[3] - v[2], v[4] - v[3], v[5] - v[4], floor_raw, inv_dx1,
                                unused0, pm[1]);
@@ -189,7 +209,8 @@ __global__ void __launch_bounds__(RowsLimits<T>::kMaxThreads) rows_kernel(const 
                 }
                 if constexpr (D == 4) {
                     T v[7];
-                    gather7<T>(u, colbase + zoff, i2, g.n[2], g.stride[2], (g.periodic_mask >> 2) & 1u, extrap, v);
+                    gather7<T>(u, (long long)i2 * g.stride[2] + zoff + colbase, i2, g.n[2], g.stride[2],
+                               (g.periodic_mask >> 2) & 1u, extrap, v);
                     weno5_pair<T>(v, SP<T>::dx(P, 2), floor_raw, pm[2], pp[2]);
                 }
                 int idx[4] = {x, y, 0, 0};
@@ -197,7 +218,7 @@ __global__ void __launch_bounds__(RowsLimits<T>::kMaxThreads) rows_kernel(const 
                 if (D == 4) { idx[2] = i2; idx[3] = z; }
                 T yd = lf_term_dyn<T, D, DYN>(P, idx, pm, pp);
                 if (brt0) yd = fmin(yd, T(0));
-                const long long flat = colbase + zoff;
+                const long long flat = (uz - u) + colbase;
                 T res;
                 if (term_mode) {
                     res = yd;
@@ -224,7 +245,7 @@ __global__ void __launch_bounds__(RowsLimits<T>::kMaxThreads) rows_kernel(const 
 // Shared memory of a rows_kernel block.
 template <typename T>
 inline size_t rows_smem_bytes(int nx, int ty) {
-    return sizeof(T) * ((size_t)(ty + 6) * nx + 2 * (size_t)ty * nx);
+    return rows_smem(nx, ty, sizeof(T));
 }
 
 template <typename T, int D, int DYN>

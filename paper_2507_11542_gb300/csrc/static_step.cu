@@ -100,7 +100,7 @@ bool pick_rows(const StageParams& P, int dtype, int sm_count, RowsCfg* c) {
     int ty = 1;
     while (ty < ny && (nx + 1) * (ty + 1) <= max_threads && (nx + 1) * ty < 256) ++ty;
     const size_t es = dtype == HJ_F64 ? 8 : 4;
-    if (es * ((size_t)(ty + 6) * nx + 2 * (size_t)ty * nx) > 200 * 1024) return false;
+    if (rows_smem(nx, ty, es) > 200 * 1024) return false;
     c->ty = ty;
     c->row_tiles = (ny + ty - 1) / ty;
     const int ns = D >= 3 ? G.n[D - 1] : 1;
