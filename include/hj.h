@@ -188,6 +188,24 @@ hj_status hj_rk3_stage(hj_ctx* ctx, const hj_grid* grid, const hj_method* method
 hj_status hj_solve(hj_ctx* ctx, const hj_problem* problem, void* out_slices, int32_t out_on_device,
                    double* out_times, hj_stats* stats);
 
+/* Many independent solves at once (the batched form of hj_solve). Problem i
+ * writes its slices to out_slices[i] (device memory if out_on_device[i], else
+ * host memory), its slice times to out_times[i] (may be NULL, or out_times
+ * itself NULL) and its statistics to stats[i] (stats may be NULL).
+ * WENO5 instances of the row kernel's (dimension, dynamics) pairs with
+ * n0 < 1024 (FP32) or n0 < 512 (FP64) advance together: one launch per RK
+ * stage and (element type, dimension, dynamics) group covers every tile of
+ * every active instance, a small kernel advances each instance's own dt and
+ * slice cursor, and blocks of steps replay as CUDA graphs. Other problems are
+ * solved one by one with hj_solve. Every problem is validated before any work;
+ * results equal those of hj_solve on each problem alone (same arithmetic per
+ * node). elapsed_ms and kernel_launches in stats are those of the whole call.
+ * The first batch with a new (element type, dimension, dynamics) group times a
+ * few launch shapes. Synchronises the stream.
+ * Errors: HJ_EINVAL (names the problem index), HJ_ENOMEM, HJ_ENONFINITE, HJ_ECUDA. */
+hj_status hj_solve_batch(hj_ctx* ctx, int32_t n, const hj_problem* problems, void* const* out_slices,
+                         const int32_t* out_on_device, double* const* out_times, hj_stats* stats);
+
 /* No-allocation variant of hj_rk3_step. -------------------------------- */
 
 /* Capacity of the fixed scratch used by hj_rk3_step_static. */

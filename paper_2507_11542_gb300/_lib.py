@@ -32,7 +32,7 @@ HJ_EXTRAP_AWAY_FROM_ZERO, HJ_EXTRAP_LINEAR = 0, 1
 # every function include/hj.h declares (checked by the test-suite against the .so)
 EXPORTS = ["hj_ctx_create", "hj_ctx_destroy", "hj_status_str", "hj_ctx_last_error", "hj_version",
            "hj_upwind", "hj_term", "hj_step_bound", "hj_rk3_step", "hj_rk3_stage", "hj_solve",
-           "hj_rk3_step_static"]
+           "hj_rk3_step_static", "hj_solve_batch"]
 HJ_STATIC_MAX_NODES = 1 << 20
 HJ_STATIC_MAX_ANGLES = 4096
 
@@ -101,6 +101,8 @@ def load():
             L.hj_rk3_stage.argtypes = [_vp, _P(hj_grid), _P(hj_method), ctypes.c_int32, ctypes.c_int32, _vp, _vp, _vp,
                                        ctypes.c_double]
             L.hj_solve.argtypes = [_vp, _P(hj_problem), _vp, ctypes.c_int32, _P(ctypes.c_double), _P(hj_stats)]
+            L.hj_solve_batch.argtypes = [_vp, ctypes.c_int32, _P(hj_problem), _P(_vp), _P(ctypes.c_int32),
+                                         _P(_P(ctypes.c_double)), _P(hj_stats)]
             L.hj_rk3_step_static.argtypes = [_vp, ctypes.c_int32, _P(hj_grid), _P(hj_method), ctypes.c_int32, _vp,
                                              ctypes.c_double]
             _lib = L
@@ -235,6 +237,20 @@ def hj_solve(ctx, problem: hj_problem, out_slices_ptr: int, out_on_device: bool,
     _check(ctx, load().hj_solve(_vp(ctx), ctypes.byref(problem), _vp(out_slices_ptr), int(bool(out_on_device)), tp,
                                 ctypes.byref(stats)))
     return stats
+
+
+def hj_solve_batch(ctx, problems, out_ptrs, out_on_device, out_times):
+    """problems: list of hj_problem; out_ptrs: list of int addresses; out_on_device: list of bools;
+    out_times: list of float64 numpy arrays (or None). Returns a list of hj_stats."""
+    n = len(problems)
+    P = (hj_problem * n)(*problems)
+    O = (_vp * n)(*[_vp(p) for p in out_ptrs])
+    F = (ctypes.c_int32 * n)(*[int(bool(f)) for f in out_on_device])
+    T = (_P(ctypes.c_double) * n)(*[(t.ctypes.data_as(_P(ctypes.c_double)) if t is not None else None)
+                                   for t in out_times])
+    S = (hj_stats * n)()
+    _check(ctx, load().hj_solve_batch(_vp(ctx), n, P, O, F, T, S))
+    return [S[i] for i in range(n)]
 
 
 def make_problem(spec, method: hj_method, dtype: int, v0_ptr: int, v0_on_device: bool, slice_times: np.ndarray):

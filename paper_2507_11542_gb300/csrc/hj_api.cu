@@ -15,31 +15,10 @@
 
 #include "../../include/hj.h"
 #include "hj_internal.h"
+#include "ctx.h"
 
-struct hj_ctx {
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    void* work[2] = {nullptr, nullptr};   // RK stage buffers (V1, V2)
-    size_t work_bytes = 0;
-    void* state = nullptr;                // the solve's own copy of V
-    size_t state_bytes = 0;
-    unsigned long long* aux = nullptr;    // [0] step-bound accumulator, [1] non-finite flag
-    double* trig_d = nullptr;             // cos/sin tables of the dimension-2 coordinate
-    float* trig_f = nullptr;
-    size_t trig_cap = 0;
-    double trig_key[3] = {0.0, 0.0, 0.0};  // (n, lo, dx) of the uploaded tables
-    bool trig_valid = false;
-    std::string last_error;
-    long long launches = 0;
-    int sm_count = 0;
-    std::map<std::vector<long long>, hj::RowsCfg> rows_cache;  // tuned launch shapes per grid shape
-    void* tune_buf = nullptr;                                 // output scratch of tuning launches
-    size_t tune_bytes = 0;
-};
 
-namespace {
-
-using namespace hj;
+namespace hj {
 
 hj_status fail(hj_ctx* ctx, hj_status st, const char* fmt, ...) {
     if (ctx) {
@@ -57,11 +36,6 @@ hj_status cuda_fail(hj_ctx* ctx, cudaError_t e, const char* what) {
     return fail(ctx, e == cudaErrorMemoryAllocation ? HJ_ENOMEM : HJ_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-#define HJ_CUDA(ctx, call)                                       \
-    do {                                                         \
-        cudaError_t e_ = (call);                                 \
-        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
-    } while (0)
 
 size_t elem_size(int dtype) { return dtype == HJ_F64 ? 8 : (dtype == HJ_F32 ? 4 : 0); }
 
@@ -205,6 +179,52 @@ hj_status ensure_work(hj_ctx* ctx, size_t bytes) {
 
 // cos/sin of the dimension-2 coordinate (the heading angle of air3D and
 // Dubins4D), from the host math library, in both precisions.
+void angle_table(const hj_grid* g, std::vector<double>* out) {
+    const int n = (int)g->n[2];
+    const bool periodic = (g->periodic_mask >> 2) & 1u;
+    const double dx = (g->hi[2] - g->lo[2]) / (periodic ? (double)n : (double)(n - 1));
+    out->assign(2 * (size_t)n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        const double x = g->lo[2] + (double)i * dx;
+        (*out)[i] = std::cos(x);
+        (*out)[n + i] = std::sin(x);
+    }
+}
+
+hj_status check_slices(hj_ctx* ctx, int n_slices, const double* slice_times) {
+    if (n_slices < 1 || !slice_times) return fail(ctx, HJ_EINVAL, "need at least one slice time");
+    for (int s = 0; s < n_slices; ++s) {
+        const double ts = slice_times[s];
+        if (!(ts >= 0.0) || !std::isfinite(ts)) return fail(ctx, HJ_EINVAL, "slice time %d invalid", s);
+        if (s > 0 && ts < slice_times[s - 1]) return fail(ctx, HJ_EINVAL, "slice times must not decrease");
+    }
+    return HJ_OK;
+}
+
+// Listing 6: dt = min(t_f - t, maxStep, cfl * stepBound), stepBound = 1/stepBoundInv,
+// while t_f - t >= eps t_f; alpha depends on x only, so stepBound is the same at
+// every step and the whole schedule is known before the first step.
+void plan_schedule(const hj_method* m, double sbi, int n_slices, const double* slice_times, Schedule* S) {
+    S->dts.clear();
+    S->slice_steps.assign(n_slices, 0);
+    S->slice_t.assign(n_slices, 0.0);
+    const double step_bound_v = 1.0 / sbi;
+    const double eps = 100.0 * DBL_EPSILON;
+    double t = 0.0;
+    for (int s = 0; s < n_slices; ++s) {
+        const double ts = slice_times[s];
+        while (ts > t && ts - t >= eps * ts) {
+            double dt = ts - t;
+            if (m->max_step < dt) dt = m->max_step;
+            if (m->cfl * step_bound_v < dt) dt = m->cfl * step_bound_v;
+            S->dts.push_back(dt);
+            t += dt;
+        }
+        S->slice_steps[s] = (long long)S->dts.size();
+        S->slice_t[s] = t;
+    }
+}
+
 hj_status upload_trig(hj_ctx* ctx, const hj_grid* g, int dynamics) {
     if (dynamics != HJ_DYN_AIR3D && dynamics != HJ_DYN_DUBINS4D) return HJ_OK;
     const int n = (int)g->n[2];
@@ -212,15 +232,9 @@ hj_status upload_trig(hj_ctx* ctx, const hj_grid* g, int dynamics) {
     const double dx = (g->hi[2] - g->lo[2]) / (periodic ? (double)n : (double)(n - 1));
     if (ctx->trig_valid && ctx->trig_key[0] == (double)n && ctx->trig_key[1] == g->lo[2] && ctx->trig_key[2] == dx)
         return HJ_OK;  // the tables on the device already hold these angles
-    std::vector<double> hd(2 * (size_t)n);
-    std::vector<float> hf(2 * (size_t)n);
-    for (int i = 0; i < n; ++i) {
-        const double x = g->lo[2] + (double)i * dx;
-        hd[i] = std::cos(x);
-        hd[n + i] = std::sin(x);
-        hf[i] = (float)hd[i];
-        hf[n + i] = (float)hd[n + i];
-    }
+    std::vector<double> hd;
+    angle_table(g, &hd);
+    std::vector<float> hf(hd.begin(), hd.end());
     const size_t need = 2 * (size_t)n;
     if (ctx->trig_cap < need) {
         HJ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
@@ -468,19 +482,10 @@ hj_status nonfinite(hj_ctx* ctx, const void* v, long long n, int dtype, bool* ba
     return HJ_OK;
 }
 
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        if (prev != dev) cudaSetDevice(dev);
-    }
-    ~DeviceGuard() {
-        int cur = -1;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-    }
-};
 
-}  // namespace
+}  // namespace hj
+
+using namespace hj;
 
 extern "C" {
 
@@ -536,6 +541,9 @@ void hj_ctx_destroy(hj_ctx* ctx) {
     cudaFree(ctx->trig_d);
     cudaFree(ctx->trig_f);
     cudaFree(ctx->tune_buf);
+    cudaFree(ctx->batch_arena);
+    cudaFree(ctx->batch_aux);
+    if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
     delete ctx;
 }
 
@@ -654,12 +662,7 @@ hj_status hj_solve(hj_ctx* ctx, const hj_problem* pr, void* out_slices, int32_t 
     const size_t es = elem_size(pr->dtype);
     if (!es) return fail(ctx, HJ_EINVAL, "unknown dtype %d", pr->dtype);
     if (!pr->v0 || !out_slices) return fail(ctx, HJ_EINVAL, "NULL v0 or output");
-    if (pr->n_slices < 1 || !pr->slice_times) return fail(ctx, HJ_EINVAL, "need at least one slice time");
-    for (int s = 0; s < pr->n_slices; ++s) {
-        const double ts = pr->slice_times[s];
-        if (!(ts >= 0.0) || !std::isfinite(ts)) return fail(ctx, HJ_EINVAL, "slice time %d invalid", s);
-        if (s > 0 && ts < pr->slice_times[s - 1]) return fail(ctx, HJ_EINVAL, "slice times must not decrease");
-    }
+    if ((st = check_slices(ctx, pr->n_slices, pr->slice_times))) return st;
     DeviceGuard guard(ctx->device);
     const GridDev G = make_grid(&pr->grid, pr->method.extrap);
     const size_t bytes = (size_t)G.total * es;
@@ -675,27 +678,19 @@ hj_status hj_solve(hj_ctx* ctx, const hj_problem* pr, void* out_slices, int32_t 
     double sbi = 0.0;
     if ((st = step_bound(ctx, &pr->grid, &pr->method, &sbi))) return st;  // also uploads the angle tables
     StageParams P = stage_params(ctx, G, &pr->method, pr->dtype);
-    // Listing 6: dt = min(t_f - t, maxStep, cfl * stepBound), stepBound = 1/stepBoundInv;
-    // alpha depends on x only, so stepBound is the same at every step.
-    const double step_bound_v = 1.0 / sbi;
-    const double eps = 100.0 * DBL_EPSILON;
-    double t = 0.0;
-    long long steps = 0;
+    Schedule S;
+    plan_schedule(&pr->method, sbi, pr->n_slices, pr->slice_times, &S);
     const cudaMemcpyKind out_kind = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    size_t k = 0;
     for (int s = 0; s < pr->n_slices; ++s) {
-        const double ts = pr->slice_times[s];
-        while (ts > t && ts - t >= eps * ts) {
-            double dt = ts - t;
-            if (pr->method.max_step < dt) dt = pr->method.max_step;
-            if (pr->method.cfl * step_bound_v < dt) dt = pr->method.cfl * step_bound_v;
-            if ((st = rk3_launch(ctx, P, pr->method.scheme, pr->dtype, pr->method.brt, V, dt))) return st;
-            t += dt;
-            ++steps;
-        }
+        for (; k < (size_t)S.slice_steps[s]; ++k)
+            if ((st = rk3_launch(ctx, P, pr->method.scheme, pr->dtype, pr->method.brt, V, S.dts[k]))) return st;
         HJ_CUDA(ctx, cudaMemcpyAsync(static_cast<char*>(out_slices) + (size_t)s * bytes, V, bytes, out_kind,
                                      ctx->stream));
-        if (out_times) out_times[s] = t;
+        if (out_times) out_times[s] = S.slice_t[s];
     }
+    const long long steps = (long long)S.dts.size();
+    const double t = S.slice_t[pr->n_slices - 1];
     if ((st = nonfinite(ctx, V, G.total, pr->dtype, &bad))) return st;  // synchronises the stream
     if (bad) return fail(ctx, HJ_ENONFINITE, "the solution became non-finite");
     if (stats) {

@@ -105,6 +105,45 @@ cudaError_t launch_rows_f32(const StageParams& p, const RowsCfg& c, cudaStream_t
 int rows_blocks_per_sm_f64(const StageParams& p, const RowsCfg& c);
 int rows_blocks_per_sm_f32(const StageParams& p, const RowsCfg& c);
 
+// ---------------------------------------------------------------------------
+// Batched solves: many instances advanced together by one launch per stage
+// over a list of tiles (batch.cuh).
+// ---------------------------------------------------------------------------
+struct BatchTile {
+    int inst;      // instance index
+    int row_tile;  // rows row_tile*ty .. of the instance's planes
+    int i2;        // dimension-2 index (4-D instances)
+    int chunk;     // chunk along the streamed dimension
+};
+
+struct BatchInst {
+    StageParams P;            // grid, dynamics, parameters (FP64 + FP32), angle tables, WENO floor
+    int ty, tz;               // tile shape of this instance
+    int steps_total;          // RK3 steps of the whole solve
+    int k;                    // steps completed (advanced on the device)
+    double dt;                // dt of the current step
+    float dt_f;
+    int brt;                  // HJ_BRT_*
+    void* V;                  // value function (in place)
+    void* V1;                 // stage buffers
+    void* V2;
+    void* slice_out;          // stage 3 of the current step also writes here, or null
+    const double* dts;        // dt of every step
+    const long long* ends;    // distinct positive step counts at which slices are taken, ascending
+    const int* end_slice;     // slice index written at each of those
+    int n_ends;
+    int cursor;               // next entry of ends not yet scheduled
+    void* out;                // slice outputs: n_slices x nodes elements
+    long long nodes;
+    int elem;                 // element size in bytes
+};
+
+cudaError_t launch_batch_stage_f32(const BatchTile* tiles, int ntiles, const BatchInst* insts, int stage, int ndim,
+                                   int dynamics, int threads, size_t smem, cudaStream_t s);
+cudaError_t launch_batch_stage_f64(const BatchTile* tiles, int ntiles, const BatchInst* insts, int stage, int ndim,
+                                   int dynamics, int threads, size_t smem, cudaStream_t s);
+cudaError_t launch_batch_advance(BatchInst* insts, int n, cudaStream_t s);
+
 // max over nodes of sum_d alpha_d(x)/dx_d, as the FP64 bit pattern, atomically
 // max-ed into *acc (which the caller zeroes first).
 cudaError_t launch_step_bound(const GridDev& g, int dynamics, const double* params, const double* trig_d,

@@ -64,38 +64,68 @@ __device__ __forceinline__ T row_value(const T* row, int i, int n, bool periodic
     return ghost_value(row[n - 1], row[n - 2], i - (n - 1), extrap);
 }
 
+// Values of one stage launch that differ between the three RK stages, in the
+// kernel's precision (kept in registers).
+template <typename T>
+struct StageRun {
+    const T* u;        // stencil input
+    const T* vn;       // V^n (stages 2 and 3)
+    T* out;            // result
+    T* also_out;       // if not null, the result is written here as well (a time slice)
+    T dt, cv, cu;
+    bool has_vn, use_cv, minv, brt0, term;
+};
+
+template <typename T>
+__device__ __forceinline__ StageRun<T> stage_run(const StageParams& P) {
+    StageRun<T> R;
+    R.u = static_cast<const T*>(P.u);
+    R.vn = static_cast<const T*>(P.vn);
+    R.out = static_cast<T*>(P.out);
+    R.also_out = nullptr;
+    R.dt = SP<T>::dt(P);
+    R.cv = SP<T>::cv(P);
+    R.cu = SP<T>::cu(P);
+    R.has_vn = P.has_vn;
+    R.use_cv = P.cv != 0.0;
+    R.minv = P.minv_after;
+    R.brt0 = P.brt_min0;
+    R.term = P.mode == kTerm;
+    return R;
+}
+
+// One tile: rows y0 = row_tile*TY .. +TY-1 of the plane(s) at dimension-2 index
+// i2 (4-D) and the planes of chunk `chunk` along the streamed dimension
+// (planes chunk*tz .. +tz-1). (x, r) is this thread's position: x in 0..n0,
+// r in 0..; threads with r >= TY only take part in the barriers.
 template <typename T, int D, int DYN>
-__global__ void __launch_bounds__(RowsLimits<T>::kMaxThreads) rows_kernel(const StageParams P, const RowsCfg C) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T>& R, const int TY, const int tz,
+                                          const int row_tile, const int i2_in, const int chunk_in, const int x,
+                                          const int r, T* const smem) {
     const GridDev& g = P.g;
     const int nx = g.n[0], ny = g.n[1];
-    const int TY = C.ty;
     const int W = nx + 6;  // shared row: 3 ghost cells, nx nodes, 3 ghost cells
     // two buffers, alternating by plane: (TY + 6) rows x W, then p- and p+ along dimension 0 (TY x nx each)
     const size_t buf_elems = (size_t)(TY + 6) * W + 2 * (size_t)TY * nx;
-    T* const smem = reinterpret_cast<T*>(smem_raw);
 
-    const T* __restrict__ u = static_cast<const T*>(P.u);
-    const T* __restrict__ vn = static_cast<const T*>(P.vn);
-    T* __restrict__ out = static_cast<T*>(P.out);
+    const T* __restrict__ u = R.u;
+    const T* __restrict__ vn = R.vn;
+    T* __restrict__ out = R.out;
     const T floor_raw = SP<T>::floor(P);
     const bool per0 = g.periodic_mask & 1u, per1 = (g.periodic_mask >> 1) & 1u;
     const int extrap = g.extrap;
 
-    const int x = threadIdx.x;  // 0 .. nx; x == nx: the row's last interface and its ghost cells
-    const int r = threadIdx.y;
-    const int y0 = blockIdx.x * TY;
+    const int y0 = row_tile * TY;
     const int y = y0 + r;
     const int rows_valid = min(TY, ny - y0);
     const bool node = (x < nx) && (r < rows_valid);
 
-    int i2 = 0, chunk = 0;
-    if (D == 3) chunk = blockIdx.y;
-    if (D == 4) { i2 = blockIdx.y; chunk = blockIdx.z; }
+    const int i2 = (D == 4) ? i2_in : 0;
+    const int chunk = (D >= 3) ? chunk_in : 0;
     constexpr int SD = (D >= 3) ? D - 1 : 0;  // streamed dimension
     const int ns = (D >= 3) ? g.n[SD] : 1;
-    const int zbeg = (D >= 3) ? chunk * C.tz : 0;
-    const int zend = (D >= 3) ? min(ns, zbeg + C.tz) : 1;
+    const int zbeg = (D >= 3) ? chunk * tz : 0;
+    const int zend = (D >= 3) ? min(ns, zbeg + tz) : 1;
     const long long sS = (D >= 3) ? g.stride[SD] : 0;
     const bool perS = (D >= 3) ? ((g.periodic_mask >> SD) & 1u) : false;
     // the chunk's streamed-dimension reads stay inside the grid: no ghost logic needed
@@ -106,9 +136,10 @@ __global__ void __launch_bounds__(RowsLimits<T>::kMaxThreads) rows_kernel(const 
     const T inv_dx0 = SP<T>::inv_dx(P, 0);
     const T inv_dx1 = SP<T>::inv_dx(P, 1);
     const T inv_dxs = SP<T>::inv_dx(P, SD);
-    const T dt = SP<T>::dt(P), cv = SP<T>::cv(P), cu = SP<T>::cu(P);
-    const bool has_vn = P.has_vn, use_cv = P.cv != 0.0, minv = P.minv_after, brt0 = P.brt_min0;
-    const bool term_mode = P.mode == kTerm;
+    const T dt = R.dt, cv = R.cv, cu = R.cu;
+    const bool has_vn = R.has_vn, use_cv = R.use_cv, minv = R.minv, brt0 = R.brt0;
+    const bool term_mode = R.term;
+    T* __restrict__ also_out = R.also_out;
 
     // Halo rows (three above, three below, and rows past the grid edge in a
     // ragged last tile) are loaded by thread rows in turn: row h of n_extra.
@@ -149,7 +180,7 @@ __global__ void __launch_bounds__(RowsLimits<T>::kMaxThreads) rows_kernel(const 
             // from global memory (ghost rule along dimension 1), and the x-ghost
             // cells of each node row from its spare thread x == nx
             if (node) plane[(size_t)(r + 3) * W + 3 + x] = center;
-            if (x < nx) {
+            if (x < nx && r < TY) {
                 for (int h = r; h < n_extra; h += TY) {
                     const int rr = (h < 3) ? h - 3 : rows_valid + (h - 3);
                     plane[(size_t)(rr + 3) * W + 3 + x] = line_value(uz + x, y0 + rr, ny, (long long)nx, per1, extrap);
@@ -232,6 +263,7 @@ __global__ void __launch_bounds__(RowsLimits<T>::kMaxThreads) rows_kernel(const 
                     }
                 }
                 out[flat] = res;
+                if (also_out) also_out[flat] = res;
             }
             if constexpr (D >= 3) {
                 carry = next;
@@ -240,6 +272,16 @@ __global__ void __launch_bounds__(RowsLimits<T>::kMaxThreads) rows_kernel(const 
             }
         }
     }
+}
+
+template <typename T, int D, int DYN>
+__global__ void __launch_bounds__(RowsLimits<T>::kMaxThreads) rows_kernel(const StageParams P, const RowsCfg C) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const StageRun<T> R = stage_run<T>(P);
+    const int i2 = (D == 4) ? (int)blockIdx.y : 0;
+    const int chunk = (D == 3) ? (int)blockIdx.y : ((D == 4) ? (int)blockIdx.z : 0);
+    rows_tile<T, D, DYN>(P, R, C.ty, C.tz, blockIdx.x, i2, chunk, threadIdx.x, threadIdx.y,
+                         reinterpret_cast<T*>(smem_raw));
 }
 
 // Shared memory of a rows_kernel block.

@@ -108,3 +108,30 @@ def solve(ctx: Context, spec, m: L.hj_method, V0, slice_times, out=None):
     stats = L.hj_solve(ctx.handle, prob, int(out.data_ptr()), out.is_cuda, times)
     del keep
     return out, times, stats.as_dict()
+
+
+def solve_batch(ctx: Context, specs, methods, V0s, slice_times, outs=None):
+    """Many independent solves in one call (hj_solve_batch).
+
+    specs, methods, V0s (flat tensors, device or host), slice_times: one entry
+    per problem. outs: optional list of [n_slices, prod(n)] tensors.
+    Returns (outs, times_list, stats_list)."""
+    import torch
+    n = len(specs)
+    if not (len(methods) == len(V0s) == len(slice_times) == n):
+        raise ValueError("one method, V0 and slice-time list per grid")
+    probs, keep, times = [], [], []
+    if outs is None:
+        outs = [torch.empty((len(ts), V0.numel()), dtype=V0.dtype, device=V0.device)
+                for V0, ts in zip(V0s, slice_times)]
+    for spec, m, V0, ts, out in zip(specs, methods, V0s, slice_times, outs):
+        N = int(np.prod(spec.n))
+        if V0.numel() != N or not V0.is_contiguous() or out.numel() != len(ts) * N or out.dtype != V0.dtype:
+            raise ValueError("V0/out do not match the grid")
+        p, k = L.make_problem(spec, m, L.dtype_code(V0.dtype), int(V0.data_ptr()), V0.is_cuda, ts)
+        probs.append(p)
+        keep.append(k)
+        times.append(np.zeros(len(ts)))
+    stats = L.hj_solve_batch(ctx.handle, probs, [int(o.data_ptr()) for o in outs], [o.is_cuda for o in outs], times)
+    del keep
+    return outs, times, [s.as_dict() for s in stats]

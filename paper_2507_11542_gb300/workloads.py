@@ -105,3 +105,23 @@ def random_field(grid: GridSpec, seed: int, scale: float = 1.0) -> np.ndarray:
             arg = arg + 2 * math.pi * k[d] * (X[d] - grid.lo[d]) / span
         V = V + rng.uniform(0.2, 1.0) * np.sin(arg)
     return np.asfortranarray(scale * V)
+
+
+def batch_mix(seed: int = 42, n_di: int = 32, n_air: int = 32):
+    """The batched workload: n_di double-integrator solves with n ~ U{51..201}
+    and target radius ~ U[0.2, 0.8] (horizon 1), and n_air air3D solves with
+    n ~ U{41..121} and radius ~ U[3, 7] (horizon 2.8), seeded.
+    Returns a list of (kind, GridSpec, V0, horizon)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n_di):
+        n = int(rng.integers(51, 202))
+        r = float(rng.uniform(0.2, 0.8))
+        g, V0 = double_integrator(n, r)
+        out.append(("di", g, V0, 1.0))
+    for _ in range(n_air):
+        n = int(rng.integers(41, 122))
+        r = float(rng.uniform(3.0, 7.0))
+        g, V0 = air3d(n, r)
+        out.append(("air3d", g, V0, 2.8))
+    return out

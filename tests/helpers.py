@@ -43,9 +43,11 @@ def rel_err(a, ref):
     return float(np.max(np.abs(np.asarray(a) - np.asarray(ref)))) / scale
 
 
-def zero_set_displacement(V, Vref, spec):
+def zero_set_displacement(V, Vref, spec, margin=0):
     """Zero-level-set displacement of V against Vref, in grid cells: over nodes
-    within two cells of Vref's zero set, |V - Vref| / (|grad_h Vref| dx)."""
+    within two cells of Vref's zero set, |V - Vref| / (|grad_h Vref| dx).
+    margin > 0 leaves out nodes closer than that many cells to a non-periodic
+    edge, where the away-from-zero ghost rule flips with the sign of V."""
     dxs = [(spec.hi[d] - spec.lo[d]) / (spec.n[d] if d in spec.periodic else spec.n[d] - 1)
            for d in range(len(spec.n))]
     grads = np.gradient(Vref, *dxs)
@@ -54,6 +56,17 @@ def zero_set_displacement(V, Vref, spec):
     gnorm = np.sqrt(sum(g * g for g in grads))
     h = min(dxs)
     near = np.abs(Vref) < 2.0 * h * np.maximum(gnorm, 1e-12)
+    if margin > 0:
+        inner = np.ones(Vref.shape, dtype=bool)
+        for d in range(len(spec.n)):
+            if d in spec.periodic:
+                continue
+            sl = [slice(None)] * len(spec.n)
+            sl[d] = slice(0, margin)
+            inner[tuple(sl)] = False
+            sl[d] = slice(spec.n[d] - margin, None)
+            inner[tuple(sl)] = False
+        near &= inner
     if not near.any():
         return 0.0
     return float(np.max(np.abs(V - Vref)[near] / (np.maximum(gnorm[near], 1e-12) * h)))
