@@ -206,6 +206,58 @@ hj_status hj_solve(hj_ctx* ctx, const hj_problem* problem, void* out_slices, int
 hj_status hj_solve_batch(hj_ctx* ctx, int32_t n, const hj_problem* problems, void* const* out_slices,
                          const int32_t* out_on_device, double* const* out_times, hj_stats* stats);
 
+/* Serving: a continuous-batching request loop (Sec. 6 reachability solves as
+ * requests). A server owns a private stream, a private context and an HBM
+ * arena of hbm_budget bytes (allocated at creation), and one engine thread.
+ * Requests queue in arrival order; each engine tick admits queued requests
+ * while a slot (at most max_slots) is free and the request's footprint (its
+ * three grid arrays, angle tables, slice bookkeeping and, for host outputs, a
+ * device copy of its slices) fits the arena, then advances every admitted
+ * request by a block of RK3 steps in batched launches (as hj_solve_batch),
+ * and retires requests whose steps are done. Grids stay on the device from
+ * admission to retirement; requests arriving meanwhile join at the next tick.
+ * Each result equals hj_solve on the same problem alone (same arithmetic per
+ * node). All functions are thread-safe except destroy, which no other call
+ * may overlap. */
+typedef struct hj_server hj_server;
+
+typedef struct hj_server_info {
+    int64_t queued;          /* requests waiting for admission */
+    int64_t running;         /* requests on the device */
+    int64_t completed;       /* requests finished (any status) */
+    int64_t bytes_in_use;    /* arena bytes held by admitted requests */
+    int64_t budget;          /* arena size */
+    int64_t kernel_launches; /* kernels launched by the engine so far */
+} hj_server_info;
+
+/* Creates a server on ctx's device (ctx itself is not used afterwards).
+ * Errors: HJ_EINVAL (max_slots < 1, budget < 4096 bytes), HJ_ENOMEM, HJ_ECUDA. */
+hj_status hj_server_create(hj_ctx* ctx, size_t hbm_budget, int32_t max_slots, hj_server** out);
+/* Queues a request; never waits for the GPU. The problem (including its slice
+ * times) is copied; v0 and out_slices (n_slices x prod(n) elements, device
+ * memory if out_on_device) and out_times (host, n_slices doubles, may be
+ * NULL) must stay valid until hj_server_wait returns for the ticket.
+ * Errors: HJ_EINVAL (malformed, or not served by the batched row kernel:
+ * WENO5, dimension/dynamics pairs of hj_solve_batch), HJ_ENOMEM (footprint
+ * larger than the whole budget), HJ_ECANCELLED (server stopping). */
+hj_status hj_server_submit(hj_server* srv, const hj_problem* problem, void* out_slices, int32_t out_on_device,
+                           double* out_times, uint64_t* ticket);
+/* Waits up to timeout_ms (< 0: no limit) for a request. On completion returns
+ * its status (HJ_OK, HJ_ENONFINITE, HJ_ECANCELLED, ...) and forgets the
+ * ticket; stats->elapsed_ms is the latency from submission to retirement.
+ * Errors: HJ_ETIMEOUT (still running; the ticket stays valid), HJ_EINVAL
+ * (unknown ticket). */
+hj_status hj_server_wait(hj_server* srv, uint64_t ticket, int32_t timeout_ms, hj_stats* stats);
+/* Cancels a queued request at once, or a running one at the next tick
+ * boundary (its outputs are then unspecified); wait then returns
+ * HJ_ECANCELLED. Errors: HJ_EINVAL (unknown or finished ticket). */
+hj_status hj_server_cancel(hj_server* srv, uint64_t ticket);
+/* Counters of the server; returns the server's fatal status (HJ_OK unless a
+ * CUDA failure stopped the engine). */
+hj_status hj_server_counters(hj_server* srv, hj_server_info* info);
+/* Stops the engine (requests not finished are cancelled), frees the arena. */
+void hj_server_destroy(hj_server* srv);
+
 /* No-allocation variant of hj_rk3_step. -------------------------------- */
 
 /* Capacity of the fixed scratch used by hj_rk3_step_static. */

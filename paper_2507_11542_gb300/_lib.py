@@ -32,7 +32,8 @@ HJ_EXTRAP_AWAY_FROM_ZERO, HJ_EXTRAP_LINEAR = 0, 1
 # every function include/hj.h declares (checked by the test-suite against the .so)
 EXPORTS = ["hj_ctx_create", "hj_ctx_destroy", "hj_status_str", "hj_ctx_last_error", "hj_version",
            "hj_upwind", "hj_term", "hj_step_bound", "hj_rk3_step", "hj_rk3_stage", "hj_solve",
-           "hj_rk3_step_static", "hj_solve_batch"]
+           "hj_rk3_step_static", "hj_solve_batch", "hj_server_create", "hj_server_submit", "hj_server_wait",
+           "hj_server_cancel", "hj_server_counters", "hj_server_destroy"]
 HJ_STATIC_MAX_NODES = 1 << 20
 HJ_STATIC_MAX_ANGLES = 4096
 
@@ -57,6 +58,14 @@ class hj_problem(ctypes.Structure):
 class hj_stats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int64), ("cell_updates", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
                 ("step_bound_inv", ctypes.c_double), ("t_final", ctypes.c_double), ("elapsed_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class hj_server_info(ctypes.Structure):
+    _fields_ = [("queued", ctypes.c_int64), ("running", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("bytes_in_use", ctypes.c_int64), ("budget", ctypes.c_int64), ("kernel_launches", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -103,6 +112,14 @@ def load():
             L.hj_solve.argtypes = [_vp, _P(hj_problem), _vp, ctypes.c_int32, _P(ctypes.c_double), _P(hj_stats)]
             L.hj_solve_batch.argtypes = [_vp, ctypes.c_int32, _P(hj_problem), _P(_vp), _P(ctypes.c_int32),
                                          _P(_P(ctypes.c_double)), _P(hj_stats)]
+            L.hj_server_create.argtypes = [_vp, ctypes.c_size_t, ctypes.c_int32, _P(_vp)]
+            L.hj_server_submit.argtypes = [_vp, _P(hj_problem), _vp, ctypes.c_int32, _P(ctypes.c_double),
+                                           _P(ctypes.c_uint64)]
+            L.hj_server_wait.argtypes = [_vp, ctypes.c_uint64, ctypes.c_int32, _P(hj_stats)]
+            L.hj_server_cancel.argtypes = [_vp, ctypes.c_uint64]
+            L.hj_server_counters.argtypes = [_vp, _P(hj_server_info)]
+            L.hj_server_destroy.argtypes = [_vp]
+            L.hj_server_destroy.restype = None
             L.hj_rk3_step_static.argtypes = [_vp, ctypes.c_int32, _P(hj_grid), _P(hj_method), ctypes.c_int32, _vp,
                                              ctypes.c_double]
             _lib = L
@@ -251,6 +268,46 @@ def hj_solve_batch(ctx, problems, out_ptrs, out_on_device, out_times):
     S = (hj_stats * n)()
     _check(ctx, load().hj_solve_batch(_vp(ctx), n, P, O, F, T, S))
     return [S[i] for i in range(n)]
+
+
+def hj_server_create(ctx, hbm_budget: int, max_slots: int) -> int:
+    out = _vp()
+    _check(ctx, load().hj_server_create(_vp(ctx), int(hbm_budget), int(max_slots), ctypes.byref(out)))
+    return out.value
+
+
+def hj_server_submit(srv, problem: hj_problem, out_ptr: int, out_on_device: bool, out_times) -> int:
+    """Returns the ticket; raises HJError with the status on refusal."""
+    t = ctypes.c_uint64(0)
+    tp = None if out_times is None else out_times.ctypes.data_as(_P(ctypes.c_double))
+    st = load().hj_server_submit(_vp(srv), ctypes.byref(problem), _vp(out_ptr), int(bool(out_on_device)), tp,
+                                 ctypes.byref(t))
+    if st != HJ_OK:
+        raise HJError(st, "hj_server_submit")
+    return t.value
+
+
+def hj_server_wait(srv, ticket: int, timeout_ms: int = -1):
+    """Returns (status, stats)."""
+    s = hj_stats()
+    st = load().hj_server_wait(_vp(srv), ctypes.c_uint64(ticket), int(timeout_ms), ctypes.byref(s))
+    return st, s
+
+
+def hj_server_cancel(srv, ticket: int) -> int:
+    return load().hj_server_cancel(_vp(srv), ctypes.c_uint64(ticket))
+
+
+def hj_server_counters(srv) -> dict:
+    info = hj_server_info()
+    st = load().hj_server_counters(_vp(srv), ctypes.byref(info))
+    d = info.as_dict()
+    d["status"] = st
+    return d
+
+
+def hj_server_destroy(srv) -> None:
+    load().hj_server_destroy(_vp(srv))
 
 
 def make_problem(spec, method: hj_method, dtype: int, v0_ptr: int, v0_on_device: bool, slice_times: np.ndarray):

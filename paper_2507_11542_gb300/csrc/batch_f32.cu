@@ -8,8 +8,9 @@ cudaError_t launch_batch_stage_f32(const BatchTile* tiles, int ntiles, const Bat
     HJ_BATCH_DISPATCH(float)
 }
 
-// After stage 3 of a step: count the step, load the next step's dt and the
-// slice (if any) that the next step completes.
+// After stage 3 of a step: count the step, and set up the next one. Every
+// step uses dt_full except the one that completes a slice, which is clipped
+// to land on the slice time (Listing 6) and also writes the slice output.
 __global__ void batch_advance_kernel(BatchInst* insts, int n) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -18,12 +19,14 @@ __global__ void batch_advance_kernel(BatchInst* insts, int n) {
     const int k = ++I.k;
     I.slice_out = nullptr;
     if (k < I.steps_total) {
-        I.dt = I.dts[k];
-        I.dt_f = (float)I.dt;
+        double dt = I.dt_full;
         if (I.cursor < I.n_ends && I.ends[I.cursor] == (long long)k + 1) {
+            dt = I.end_dt[I.cursor];
             I.slice_out = static_cast<char*>(I.out) + (size_t)I.end_slice[I.cursor] * (size_t)I.nodes * I.elem;
             I.cursor += 1;
         }
+        I.dt = dt;
+        I.dt_f = (float)dt;
     }
 }
 

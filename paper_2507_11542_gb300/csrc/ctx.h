@@ -10,6 +10,10 @@
 #include "../../include/hj.h"
 #include "hj_internal.h"
 
+namespace hj {
+class Engine;
+}
+
 struct hj_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -29,12 +33,10 @@ struct hj_ctx {
     std::map<std::vector<long long>, hj::RowsCfg> rows_cache;  // tuned launch shapes per grid shape
     void* tune_buf = nullptr;                                 // output scratch of tuning launches
     size_t tune_bytes = 0;
-    void* batch_arena = nullptr;                              // batched solves: arrays, tables, staging
-    size_t batch_bytes = 0;
-    void* batch_aux = nullptr;                                // batched solves: descriptors, schedules, tiles
-    size_t batch_aux_bytes = 0;
     std::map<std::vector<long long>, std::pair<int, int>> batch_shape;  // (threads, planes per tile) per group kind
-    cudaStream_t capture_stream = nullptr;                    // private stream for CUDA-graph capture
+    hj::Engine* batch_engine = nullptr;                        // reused by hj_solve_batch
+    size_t batch_engine_bytes = 0;
+    int batch_engine_slots = 0;
 };
 
 namespace hj {

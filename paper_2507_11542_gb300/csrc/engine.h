@@ -1,0 +1,128 @@
+// engine.h -- device-resident multi-instance stepping shared by the batched
+// solve and the serving loop.
+//
+// An Engine owns one device arena (first-fit), a table of instance slots with
+// their device descriptors (BatchInst), and per-group tile lists. Instances
+// are admitted into free slots (arrays uploaded, CFL bound and non-finite
+// check launched), activated together (one synchronisation: schedules and
+// descriptors), advanced K RK3 steps at a time for all active instances (a
+// captured CUDA graph replayed while the tile set is unchanged), and retired
+// when their steps are done. Not thread-safe: one thread drives an Engine.
+#pragma once
+
+#include <cstdint>
+#include <utility>
+#include <vector>
+
+#include "ctx.h"
+
+namespace hj {
+
+class Arena {
+ public:
+    void reset(unsigned char* base, size_t cap);
+    bool alloc(size_t bytes, size_t* off);  // 256-byte aligned, first fit
+    void release(size_t off, size_t bytes);
+    size_t capacity() const { return cap_; }
+    size_t used() const { return used_; }
+    unsigned char* base() const { return base_; }
+
+ private:
+    unsigned char* base_ = nullptr;
+    size_t cap_ = 0, used_ = 0;
+    std::vector<std::pair<size_t, size_t>> free_;  // (offset, size), sorted by offset
+};
+
+struct Slot {
+    bool used = false, active = false;
+    hj_problem prob;                 // copy; slice_times points into `times`
+    std::vector<double> times;
+    void* out = nullptr;
+    bool out_on_device = true;
+    double* out_times = nullptr;
+    GridDev G;
+    int dtype = 0;
+    size_t es = 0;
+    long long N = 0;
+    bool angles = false;
+    int group = -1;
+    int ty = 1, tz = 1;
+    Schedule S;
+    double sbi = 0.0;
+    long long steps_total = 0, k_host = 0;
+    size_t off = 0, bytes = 0;       // the slot's arena block
+    size_t o_v = 0, o_v1 = 0, o_v2 = 0, o_td = 0, o_tf = 0, o_stage = 0, o_ends = 0, o_end_slice = 0, o_end_dt = 0;
+    std::vector<double> table;       // host angle tables, alive until activation
+    std::vector<float> table_f;
+    hj_stats stats;
+    hj_status status = HJ_OK;
+    uint64_t tag = 0;                // caller's identifier (problem index or ticket)
+};
+
+class Engine {
+ public:
+    ~Engine();
+    // Allocates the arena (arena_bytes), descriptor table and reduction words.
+    hj_status init(hj_ctx* ctx, cudaStream_t stream, int max_slots, size_t arena_bytes);
+    void shutdown();
+
+    // Whether the batched row kernel serves this problem.
+    static bool eligible(const hj_problem* p);
+    // Arena bytes one problem needs.
+    static size_t footprint(const hj_problem* p, bool out_on_device);
+
+    int free_slot() const;
+    // Copies the problem into a free slot and enqueues its upload, CFL bound
+    // and non-finite check. HJ_EBUSY: no slot or arena space right now.
+    hj_status admit(const hj_problem* p, void* out, bool out_on_device, double* out_times, uint64_t tag,
+                    int* slot_out);
+    // Activates every admitted slot: one synchronisation, then schedules,
+    // launch shapes and descriptors. Slots whose v0 is not finite come back in
+    // `failed` with status HJ_ENONFINITE and are released.
+    hj_status activate(std::vector<int>* failed);
+    // K RK3 steps of every active slot.
+    hj_status run(int K);
+    bool any_active() const;
+    // Active slots whose steps are all enqueued.
+    void done_slots(std::vector<int>* out) const;
+    // Finishes slots (duplicate slices, host copies, final checks), one
+    // synchronisation; fills stats/out_times and releases them.
+    hj_status retire(const std::vector<int>& slots);
+    // Marks a slot finished now (cancellation) and releases it.
+    hj_status drop(int slot);
+
+    std::vector<Slot> slots;
+    long long launches = 0;
+
+ private:
+    struct Group {
+        int dtype = 0, ndim = 0, dyn = 0;
+        int threads = 0, tz_target = 8;
+        size_t smem = 0;
+        std::vector<BatchTile> tiles;
+        BatchTile* d_tiles = nullptr;
+        size_t tile_cap = 0;
+    };
+    hj_status shape_group(Group& g, const std::vector<int>& members, const std::vector<int>& fresh);
+    hj_status rebuild_tiles();
+    cudaError_t enqueue_step(cudaStream_t s, bool count);
+    long long dead_tiles() const;
+
+    hj_ctx* ctx_ = nullptr;
+    cudaStream_t stream_ = nullptr;
+    cudaStream_t cap_stream_ = nullptr;
+    int max_slots_ = 0;
+    void* arena_mem_ = nullptr;
+    Arena arena_;
+    BatchInst* d_insts_ = nullptr;
+    std::vector<BatchInst> h_insts_;
+    unsigned long long* d_words_ = nullptr;  // per slot: CFL accumulator, non-finite flag
+    std::vector<Group> groups_;
+    bool tiles_dirty_ = true;
+    long long tiles_total_ = 0;
+    cudaGraphExec_t exec_ = nullptr;
+    int exec_K_ = 0;
+    std::vector<int> pending_;
+};
+
+}  // namespace hj

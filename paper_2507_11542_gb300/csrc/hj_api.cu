@@ -16,6 +16,7 @@
 #include "../../include/hj.h"
 #include "hj_internal.h"
 #include "ctx.h"
+#include "engine.h"
 
 
 namespace hj {
@@ -541,9 +542,7 @@ void hj_ctx_destroy(hj_ctx* ctx) {
     cudaFree(ctx->trig_d);
     cudaFree(ctx->trig_f);
     cudaFree(ctx->tune_buf);
-    cudaFree(ctx->batch_arena);
-    cudaFree(ctx->batch_aux);
-    if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
+    delete ctx->batch_engine;
     delete ctx;
 }
 

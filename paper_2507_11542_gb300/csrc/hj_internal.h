@@ -128,9 +128,10 @@ struct BatchInst {
     void* V1;                 // stage buffers
     void* V2;
     void* slice_out;          // stage 3 of the current step also writes here, or null
-    const double* dts;        // dt of every step
+    double dt_full;           // dt of every step that does not end a slice: min(max_step, cfl/stepBoundInv)
     const long long* ends;    // distinct positive step counts at which slices are taken, ascending
     const int* end_slice;     // slice index written at each of those
+    const double* end_dt;     // dt of the step that completes each of those (clipped to the slice time)
     int n_ends;
     int cursor;               // next entry of ends not yet scheduled
     void* out;                // slice outputs: n_slices x nodes elements

@@ -135,3 +135,52 @@ def solve_batch(ctx: Context, specs, methods, V0s, slice_times, outs=None):
     stats = L.hj_solve_batch(ctx.handle, probs, [int(o.data_ptr()) for o in outs], [o.is_cuda for o in outs], times)
     del keep
     return outs, times, [s.as_dict() for s in stats]
+
+
+class Server:
+    """A continuous-batching server (hj_server_*). Keeps every submitted
+    request's buffers alive until its result has been collected."""
+
+    def __init__(self, ctx: Context, hbm_budget: int, max_slots: int = 64):
+        self.ctx = ctx
+        self.handle = L.hj_server_create(ctx.handle, hbm_budget, max_slots)
+        self._live = {}
+
+    def submit(self, spec, m: L.hj_method, V0, slice_times, out=None):
+        import torch
+        ts = np.ascontiguousarray(slice_times, dtype=np.float64)
+        if out is None:
+            out = torch.empty((ts.size, V0.numel()), dtype=V0.dtype, device=V0.device)
+        prob, keep = L.make_problem(spec, m, L.dtype_code(V0.dtype), int(V0.data_ptr()), V0.is_cuda, ts)
+        times = np.zeros(ts.size)
+        ticket = L.hj_server_submit(self.handle, prob, int(out.data_ptr()), out.is_cuda, times)
+        self._live[ticket] = (V0, out, times, keep)
+        return ticket
+
+    def wait(self, ticket: int, timeout_ms: int = -1):
+        """Returns (status, out, times, stats) or raises on an unknown ticket; status
+        HJ_ETIMEOUT leaves the request running."""
+        st, stats = L.hj_server_wait(self.handle, ticket, timeout_ms)
+        if st == L.HJ_ETIMEOUT:
+            return st, None, None, None
+        if st == L.HJ_EINVAL and ticket not in self._live:
+            raise KeyError(ticket)
+        V0, out, times, keep = self._live.pop(ticket)
+        return st, out, times, stats.as_dict()
+
+    def cancel(self, ticket: int) -> int:
+        return L.hj_server_cancel(self.handle, ticket)
+
+    def counters(self) -> dict:
+        return L.hj_server_counters(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            L.hj_server_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
