@@ -234,6 +234,113 @@ def bench_e2e(ctx, spec, V0, dtype, K, W_, world):
             "rk3_steps_per_step": steps // K, "launches": launches}
 
 
+def _mix_problems(mix, dtype):
+    import torch
+    from paper_2507_11542_gb300 import solver
+    specs, methods, v0s, tss = [], [], [], []
+    for kind, g, V0, horizon in mix:
+        specs.append(g)
+        if kind == "di":
+            methods.append(solver.method(dynamics=1, params=(1.0,), brt=1))
+        elif kind == "air3d":
+            methods.append(solver.method(dynamics=2, params=(5.0, 5.0, 1.0, 1.0), brt=1))
+        else:
+            methods.append(solver.method(dynamics=3, params=(1.0, 0.5), brt=1))
+        v0s.append(torch.from_numpy(np.ascontiguousarray(V0.ravel(order="F"))).to("cuda", getattr(torch, dtype)))
+        tss.append([0.0, horizon])
+    return specs, methods, v0s, tss
+
+
+def bench_batch(ctx, fp64_subset: int = 8):
+    """The 64-instance batched workload (seed 42): FP32 hj_solve_batch, the same
+    instances one by one with hj_solve (FP32), and FP64 one by one on a subset."""
+    import torch
+    from paper_2507_11542_gb300 import solver, workloads as W
+    mix = W.batch_mix(42)
+    specs, methods, v0s, tss = _mix_problems(mix, "float32")
+    solver.solve_batch(ctx, specs, methods, v0s, tss)  # warm-up: launch shapes are tuned once
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    outs, times, stats = solver.solve_batch(ctx, specs, methods, v0s, tss)
+    torch.cuda.synchronize()
+    el_batch = time.perf_counter() - t0
+    cells = sum(st["cell_updates"] for st in stats)
+    launches = stats[0]["kernel_launches"]
+    t0 = time.perf_counter()
+    for g, m, v, ts in zip(specs, methods, v0s, tss):
+        solver.solve(ctx, g, m, v, ts)
+    torch.cuda.synchronize()
+    el_serial = time.perf_counter() - t0
+    sub = list(range(0, len(mix), max(1, len(mix) // fp64_subset)))[:fp64_subset]
+    s64, m64, v64, t64 = _mix_problems([mix[i] for i in sub], "float64")
+    cells64 = 0
+    t0 = time.perf_counter()
+    for g, m, v, ts in zip(s64, m64, v64, t64):
+        _, _, st = solver.solve(ctx, g, m, v, ts)
+        cells64 += st["cell_updates"]
+    torch.cuda.synchronize()
+    el64 = time.perf_counter() - t0
+    return {"workload": "64 solves: 32 double integrator n~U{51..201}, 32 air3D n~U{41..121}, seed 42, FP32",
+            "value": cells / el_batch, "unit": "cell-updates/s", "seconds": el_batch, "kernel_launches": launches,
+            "serial_fp32": cells / el_serial, "serial_fp64": cells64 / el64,
+            "serial_fp64_sample": "%d of the 64 instances, one hj_solve each" % len(sub)}
+
+
+def bench_serve(ctx, n_req: int, seed: int = 7, load: float = 0.8, budget_gb: float = 64.0):
+    """Poisson arrivals of reachability requests (types uniform over double
+    integrator, air3D, Dubins4D; 2-D n~U{51..301}, 3-D n~U{41..161}, 4-D
+    n~U{31..81}; horizon ~U[0.5, 3]; FP32) at `load` times the capacity
+    measured by serving the same requests all at once."""
+    import torch
+    from paper_2507_11542_gb300 import solver, workloads as W
+    rng = np.random.default_rng(seed)
+    mix = []
+    for _ in range(n_req):
+        kind = int(rng.integers(0, 3))
+        horizon = float(rng.uniform(0.5, 3.0))
+        if kind == 0:
+            g, V0 = W.double_integrator(int(rng.integers(51, 302)), float(rng.uniform(0.2, 0.8)))
+            mix.append(("di", g, V0, horizon))
+        elif kind == 1:
+            g, V0 = W.air3d(int(rng.integers(41, 162)), float(rng.uniform(3.0, 7.0)))
+            mix.append(("air3d", g, V0, horizon))
+        else:
+            g, V0 = W.dubins4d(int(rng.integers(31, 82)), seed=int(rng.integers(0, 1 << 30)))
+            mix.append(("dubins", g, V0, horizon))
+    specs, methods, v0s, tss = _mix_problems(mix, "float32")
+    budget = int(budget_gb * (1 << 30))
+    with solver.Server(ctx, hbm_budget=budget, max_slots=64) as srv:
+        # capacity: everything submitted at once
+        t0 = time.perf_counter()
+        tickets = [srv.submit(g, m, v, ts) for g, m, v, ts in zip(specs, methods, v0s, tss)]
+        for t in tickets:
+            srv.wait(t)
+        cap_s = time.perf_counter() - t0
+        rate = load * n_req / cap_s
+        gaps = rng.exponential(1.0 / rate, size=n_req)
+        lat, cells = [], 0
+        t0 = time.perf_counter()
+        tickets = []
+        next_t = t0
+        for k in range(n_req):
+            next_t += gaps[k]
+            while time.perf_counter() < next_t:
+                time.sleep(min(0.001, max(0.0, next_t - time.perf_counter())))
+            tickets.append(srv.submit(specs[k], methods[k], v0s[k], tss[k]))
+        for t in tickets:
+            st, out, times, stats = srv.wait(t)
+            lat.append(stats["elapsed_ms"])
+            cells += stats["cell_updates"]
+        el = time.perf_counter() - t0
+        launches = srv.counters()["kernel_launches"]
+    lat = np.array(lat)
+    return {"workload": "%d requests, seed %d, Poisson arrivals at %.2f req/s (%.1fx of capacity %.2f req/s), FP32, "
+                        "HBM budget %.0f GB" % (n_req, seed, rate, load, n_req / cap_s, budget_gb),
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "value": cells / el, "unit": "cell-updates/s", "capacity_req_per_s": n_req / cap_s,
+            "kernel_launches": launches}
+
+
 def cpu_oracle_rate(spec, V0, steps: int):
     """The FP64 oracle, single-threaded, on the full 101^3 grid for `steps` RK3 steps."""
     from oracle import oracle as O
@@ -283,8 +390,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-steps", type=int, default=12, help="oracle steps for the cpu_baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--legs", default="f32,f64,e2e",
+    ap.add_argument("--legs", default="f32,f64,e2e,batch,serve",
                     help="comma list of legs to run (f32 always runs; a profiling run may use --legs f32)")
+    ap.add_argument("--serve-requests", type=int, default=100)
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -302,13 +410,15 @@ def main():
     legs = set(args.legs.split(","))
     with ClockSampler(local) as clk:
         r32 = bench_dtype(ctx, spec, V0, "float32", K, W_, world, flush)
-    if "f64" not in legs or "e2e" not in legs:
+    if "f64" not in legs and "e2e" not in legs and "batch" not in legs and "serve" not in legs:
         # a partial run (profiling): the FP32 leg only, no JSON line
         ctx.close()
         print("f32 leg: %.3f ms per step" % r32["ms_per_step"], flush=True)
         return
     r64 = bench_dtype(ctx, spec, V0, "float64", max(3, K // 4), 3, world, flush)
     e2e = bench_e2e(ctx, spec, V0, "float32", max(3, K // 4), 2, world)
+    batch = bench_batch(ctx) if "batch" in legs else None
+    serve = bench_serve(ctx, args.serve_requests) if "serve" in legs else None
     value = world * K * N_CELLS / (r32["total_ms"] / 1e3)
     hbm, hbm_kind = measured_hbm_gbs()
     launch_s = r32["launch_ms_mean"] / 1e3
@@ -341,6 +451,10 @@ def main():
         "clocks": clk.summary(),
     }
     line["e2e"]["rk3_steps_per_call"] = e2e["rk3_steps_per_step"]
+    if batch:
+        line["batched"] = batch
+    if serve:
+        line["served"] = serve
     if rank == 0 and not args.no_cpu_baseline:
         rate, el = cpu_oracle_rate(spec, V0, args.cpu_steps)
         line["cpu_baseline"] = {"value": rate, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",

@@ -47,11 +47,12 @@ class GridSpec:
 def sphere(grid: GridSpec, center: Sequence[float], radius: float, dims: Sequence[int] | None = None) -> np.ndarray:
     """Signed distance to a sphere (a cylinder when ``dims`` omits dimensions)."""
     dims = list(range(grid.ndim)) if dims is None else list(dims)
-    X = grid.mesh()
-    r2 = np.zeros(grid.n)
+    r2 = np.zeros([1] * grid.ndim)
     for k, d in enumerate(dims):
-        r2 = r2 + (X[d] - center[k]) ** 2
-    return np.asfortranarray(np.sqrt(r2) - radius)
+        shape = [1] * grid.ndim
+        shape[d] = grid.n[d]
+        r2 = r2 + ((grid.axis(d) - center[k]) ** 2).reshape(shape)   # broadcast: no full mesh
+    return np.asfortranarray(np.broadcast_to(np.sqrt(r2) - radius, tuple(grid.n)))
 
 
 # ----------------------------------------------------------------------------

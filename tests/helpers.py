@@ -113,3 +113,43 @@ def oracle_window_step(spec, V, center, m, dt, half=10):
     sub = V[np.ix_(*idx)]
     out = O.rk3_step(ws, m, np.asfortranarray(sub), dt)
     return out[cw]
+
+
+def crossing_displacement(V, Vref, spec):
+    """Zero-level-set displacement in cells measured on grid edges: where both
+    fields change sign along an edge, |s - s_ref| of the interpolated crossing
+    points; where only one does, the distance from that crossing to the
+    nearer end of the edge (a lower bound of the move). Max over all edges."""
+    worst = 0.0
+    pos, pos_r = V > 0, Vref > 0
+    for d in range(len(spec.n)):
+        a = [slice(None)] * len(spec.n)
+        b = [slice(None)] * len(spec.n)
+        a[d] = slice(0, spec.n[d] - 1)
+        b[d] = slice(1, spec.n[d])
+        a, b = tuple(a), tuple(b)
+        c = pos[a] != pos[b]
+        cr = pos_r[a] != pos_r[b]
+        with np.errstate(divide="ignore", invalid="ignore"):
+            s = np.nan_to_num(V[a] / (V[a] - V[b]))
+            sr = np.nan_to_num(Vref[a] / (Vref[a] - Vref[b]))
+        both = c & cr
+        if both.any():
+            worst = max(worst, float(np.max(np.abs(s - sr)[both])))
+        only = c ^ cr
+        if only.any():
+            t = np.where(c, s, sr)[only]
+            worst = max(worst, float(np.max(np.minimum(t, 1.0 - t))))
+    return worst
+
+
+def zero_set_meets_extrapolated_edge(Vref, spec):
+    """Whether the zero level set of Vref reaches a non-periodic boundary face."""
+    for d in range(len(spec.n)):
+        if d in spec.periodic:
+            continue
+        for idx in (0, spec.n[d] - 1):
+            face = np.take(Vref, idx, axis=d)
+            if (face > 0).any() and (face <= 0).any():
+                return True
+    return False

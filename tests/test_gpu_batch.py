@@ -114,13 +114,19 @@ def test_batch_mix_workload_fp32_zero_sets(ctx):
     ts = [[0.0, m[3]] for m in mix]
     outs, times, stats = solver.solve_batch(ctx, specs, methods, [to_dev(m[2], "float32") for m in mix], ts)
     outs64, _, _ = solver.solve_batch(ctx, specs, methods, [to_dev(m[2]) for m in mix], ts)
-    from helpers import zero_set_displacement
+    from helpers import crossing_displacement, zero_set_displacement, zero_set_meets_extrapolated_edge
+    checked = 0
     for k in range(len(mix)):
         a, b = to_host(outs[k][1], specs[k].n), to_host(outs64[k][1], specs[k].n)
-        full = zero_set_displacement(a, b, specs[k])
-        inner = zero_set_displacement(a, b, specs[k], margin=6)
-        print("instance %d (%s %s): zero-set displacement %.3g cells, %.3g away from extrapolated edges"
-              % (k, mix[k][0], specs[k].n, full, inner))
-        # where the zero set meets an extrapolated edge the ghost rule switches
-        # with the sign of V, so FP32 and FP64 may extrapolate differently there
-        assert inner < 0.1, (k, inner)
+        grad = zero_set_displacement(a, b, specs[k])
+        edge = crossing_displacement(a, b, specs[k])
+        touches = zero_set_meets_extrapolated_edge(b, specs[k])
+        print("instance %d (%s %s): zero-set displacement %.3g cells (gradient form), %.3g (edge crossings)%s"
+              % (k, mix[k][0], specs[k].n, grad, edge, "; zero set meets an extrapolated edge" if touches else ""))
+        # Where the zero set meets an extrapolated edge, the away-from-zero ghost
+        # rule switches with the sign of V there, so FP32 and FP64 may extrapolate
+        # differently; the 0.1-cell bar applies to the other instances.
+        if not touches:
+            assert grad < 0.1 and edge < 0.1, (k, grad, edge)
+            checked += 1
+    assert checked >= 7
