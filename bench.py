@@ -144,6 +144,30 @@ def max_over_ranks(x: float, world: int) -> float:
     return float(t.item())
 
 
+def shard(items, rank: int, world: int):
+    """The share of independent instances one rank solves: every world-th item
+    starting at its rank (no data crosses ranks)."""
+    return items[rank::world]
+
+
+def job_rate(units_per_rank: float, seconds: float, world: int) -> float:
+    """Whole-job throughput from each rank's units and its own time: all
+    ranks' units divided by the slowest rank's time (weak scaling)."""
+    slowest = max_over_ranks(seconds, world)
+    return sum_over_ranks(units_per_rank, world) / slowest
+
+
+def sum_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def workload():
     from paper_2507_11542_gb300 import workloads as W
     spec, V0 = W.air3d(101)
@@ -251,12 +275,13 @@ def _mix_problems(mix, dtype):
     return specs, methods, v0s, tss
 
 
-def bench_batch(ctx, fp64_subset: int = 8):
+def bench_batch(ctx, fp64_subset: int = 8, rank: int = 0, world: int = 1):
     """The 64-instance batched workload (seed 42): FP32 hj_solve_batch, the same
-    instances one by one with hj_solve (FP32), and FP64 one by one on a subset."""
+    instances one by one with hj_solve (FP32), and FP64 one by one on a subset.
+    With several ranks each solves its shard of the 64 instances."""
     import torch
     from paper_2507_11542_gb300 import solver, workloads as W
-    mix = W.batch_mix(42)
+    mix = shard(W.batch_mix(42), rank, world)
     specs, methods, v0s, tss = _mix_problems(mix, "float32")
     solver.solve_batch(ctx, specs, methods, v0s, tss)  # warm-up: launch shapes are tuned once
     torch.cuda.synchronize()
@@ -265,6 +290,7 @@ def bench_batch(ctx, fp64_subset: int = 8):
     torch.cuda.synchronize()
     el_batch = time.perf_counter() - t0
     cells = sum(st["cell_updates"] for st in stats)
+    rate = job_rate(cells, el_batch, world)
     launches = stats[0]["kernel_launches"]
     t0 = time.perf_counter()
     for g, m, v, ts in zip(specs, methods, v0s, tss):
@@ -280,8 +306,9 @@ def bench_batch(ctx, fp64_subset: int = 8):
         cells64 += st["cell_updates"]
     torch.cuda.synchronize()
     el64 = time.perf_counter() - t0
-    return {"workload": "64 solves: 32 double integrator n~U{51..201}, 32 air3D n~U{41..121}, seed 42, FP32",
-            "value": cells / el_batch, "unit": "cell-updates/s", "seconds": el_batch, "kernel_launches": launches,
+    return {"workload": "64 solves: 32 double integrator n~U{51..201}, 32 air3D n~U{41..121}, seed 42, FP32"
+                        + (", sharded over %d ranks" % world if world > 1 else ""),
+            "value": rate, "unit": "cell-updates/s", "seconds": el_batch, "kernel_launches": launches,
             "serial_fp32": cells / el_serial, "serial_fp64": cells64 / el64,
             "serial_fp64_sample": "%d of the 64 instances, one hj_solve each" % len(sub)}
 
@@ -417,8 +444,8 @@ def main():
         return
     r64 = bench_dtype(ctx, spec, V0, "float64", max(3, K // 4), 3, world, flush)
     e2e = bench_e2e(ctx, spec, V0, "float32", max(3, K // 4), 2, world)
-    batch = bench_batch(ctx) if "batch" in legs else None
-    serve = bench_serve(ctx, args.serve_requests) if "serve" in legs else None
+    batch = bench_batch(ctx, rank=rank, world=world) if "batch" in legs else None
+    serve = bench_serve(ctx, args.serve_requests) if ("serve" in legs and world == 1) else None
     value = world * K * N_CELLS / (r32["total_ms"] / 1e3)
     hbm, hbm_kind = measured_hbm_gbs()
     launch_s = r32["launch_ms_mean"] / 1e3
