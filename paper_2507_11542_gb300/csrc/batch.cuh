@@ -58,7 +58,8 @@ __global__ void __launch_bounds__(RowsLimits<T>::kMaxThreads)
         R.use_cv = true;
         R.minv = I.brt == HJ_BRT_MINV;
     }
-    rows_tile<T, D, DYN>(I.P, R, I.ty, I.tz, t.row_tile, t.i2, t.chunk, x, r, reinterpret_cast<T*>(smem_raw));
+    const int nr = (int)blockDim.x / (nx + 1);
+    rows_tile<T, D, DYN>(I.P, R, I.ty, nr, I.tz, t.row_tile, t.i2, t.chunk, x, r, reinterpret_cast<T*>(smem_raw));
 }
 
 template <typename T, int D, int DYN>

@@ -327,8 +327,8 @@ hj_status Engine::activate(std::vector<int>* failed) {
 namespace {
 void tile_shape(const Slot& S, int threads, int tz_target, int* ty, int* tz) {
     const int nx = S.G.n[0], ny = S.G.n[1];
-    int t = std::max(1, threads / (nx + 1));
-    t = std::min(t, ny);
+    const int nr = std::max(1, threads / (nx + 1));  // thread rows of the block
+    int t = std::min(nr >= 2 ? nr - 1 : 1, ny);       // node rows: one thread row left for the last interfaces
     while (t > 1 && rows_smem(nx, t, S.es) > 200 * 1024) --t;
     *ty = t;
     const int D = S.G.ndim;

@@ -290,9 +290,10 @@ bool rows_eligible(const GridDev& G, int scheme, int dynamics, int dtype) {
     return true;
 }
 
-RowsCfg make_rows_cfg(const GridDev& G, int ty, int tz) {
+RowsCfg make_rows_cfg(const GridDev& G, int ty, int tz, int dtype) {
     RowsCfg c;
     c.ty = ty;
+    c.nr = rows_thread_rows(G.n[0], ty, rows_max_threads(dtype));
     c.row_tiles = (G.n[1] + ty - 1) / ty;
     const int ns = G.ndim >= 3 ? G.n[G.ndim - 1] : 1;
     c.tz = G.ndim >= 3 ? tz : 1;
@@ -334,14 +335,14 @@ std::vector<RowsCfg> rows_candidates(hj_ctx* ctx, const StageParams& P, int dtyp
             zs.push_back(1);
         }
         for (int tz : zs) {
-            RowsCfg c = make_rows_cfg(G, ty, tz);
+            RowsCfg c = make_rows_cfg(G, ty, tz, dtype);
             if (c.nchunks > 65535 || c.row_tiles > (1 << 30)) continue;
             const int bps = rows_bps(P, c, dtype);
             if (bps <= 0) continue;
             const double blocks = (double)c.row_tiles * c.nchunks * (D == 4 ? G.n[2] : 1);
             const double slots = (double)ctx->sm_count * bps;
             const double waves = std::ceil(blocks / slots);
-            const double warps = std::ceil((double)(nx + 1) * ty / 32.0);
+            const double warps = std::ceil((double)(nx + 1) * c.nr / 32.0);
             const double rows_valid = std::min(ty, ny);
             const double plane = warps * (1.0 + 0.1 * (6.0 + ty - rows_valid) / ty);
             const double planes = D >= 3 ? (double)std::min(tz, ns) + 1.0 : 1.0;
@@ -351,7 +352,7 @@ std::vector<RowsCfg> rows_candidates(hj_ctx* ctx, const StageParams& P, int dtyp
     std::sort(scored.begin(), scored.end(),
               [](const std::pair<double, RowsCfg>& a, const std::pair<double, RowsCfg>& b) { return a.first < b.first; });
     std::vector<RowsCfg> out;
-    for (size_t k = 0; k < scored.size() && k < 8; ++k) out.push_back(scored[k].second);
+    for (size_t k = 0; k < scored.size() && k < 10; ++k) out.push_back(scored[k].second);
     return out;
 }
 
@@ -366,7 +367,7 @@ hj_status rows_config(hj_ctx* ctx, const StageParams& P, int dtype, RowsCfg* out
         int ty = 0, tz = 0;
         if (std::sscanf(pin, "%d,%d", &ty, &tz) == 2 && ty >= 1 && tz >= 1 && ty <= G.n[1] &&
             (G.n[0] + 1) * ty <= rows_max_threads(dtype)) {
-            *out = make_rows_cfg(G, ty, tz);
+            *out = make_rows_cfg(G, ty, tz, dtype);
             if (out->nchunks <= 65535 && rows_bps(P, *out, dtype) > 0) return HJ_OK;
         }
         return fail(ctx, HJ_EINVAL, "HJ_ROWS_CFG=%s does not fit this grid", pin);

@@ -78,16 +78,30 @@ struct UpwindParams {
 
 // Launch configuration of the row-tiled WENO5 stage kernel (rows_kernel.cuh).
 struct RowsCfg {
-    int ty;         // rows per tile (blockDim.y); blockDim.x = n0 + 1
+    int ty;         // node rows per tile; blockDim.x = n0 + 1
+    int nr;         // thread rows (blockDim.y): ty + 1 where it fits, else ty
     int tz;         // planes per chunk along the streamed (last) dimension
     int nchunks;    // chunks along the streamed dimension
     int row_tiles;  // ceil(n1 / ty)
 };
 
-// Dynamic shared memory of a rows_kernel block (element size es): two
-// alternating buffers of (ty + 6) padded rows of n0 + 6 and two ty x n0 arrays.
+// Thread rows of a row-kernel block with ty node rows: one more than ty
+// (the extra row evaluates the tile's last dimension-1 interfaces) where the
+// block size allows it, else ty (then thread row 0 evaluates those as well).
+inline int rows_thread_rows(int nx, int ty, int max_threads) {
+    return (nx + 1) * (ty + 1) <= max_threads ? ty + 1 : ty;
+}
+
+// Elements of one of the two alternating shared buffers of a rows_kernel
+// block: (ty + 6) padded rows of n0 + 6, then p+ along dimension 0 (ty rows
+// of n0 + 1) and along dimension 1 (ty + 1 rows of n0).
+__host__ __device__ inline size_t rows_buf_elems(int nx, int ty) {
+    return (size_t)(ty + 6) * (size_t)(nx + 6) + (size_t)ty * (size_t)(nx + 1) + (size_t)(ty + 1) * (size_t)nx;
+}
+
+// Dynamic shared memory of a rows_kernel block (element size es).
 inline size_t rows_smem(int nx, int ty, size_t es) {
-    return 2 * es * ((size_t)(ty + 6) * (size_t)(nx + 6) + 2 * (size_t)ty * (size_t)nx);
+    return 2 * es * rows_buf_elems(nx, ty);
 }
 
 // Launchers (one translation unit per element type). Return the launch error.

@@ -2,13 +2,15 @@
 // grids, tiled for GB300:
 //
 //  * A thread block owns TY full rows (all n0 nodes along dimension 0) of one
-//    plane of dimensions (0, 1); threadIdx = (x, row). The plane with three
-//    halo rows above and below lives in shared memory.
-//  * Along dimension 0, WENO5 is evaluated per interface (one interface gives
-//    p+ of a node and p- of the next; thread x computes the interface between
-//    nodes x-1 and x, the extra thread x = n0 the row's last one), so each
-//    node pays for about one interface instead of two.
-//  * Dimension 1 is differentiated two-sided from the shared-memory column.
+//    plane of dimensions (0, 1); threadIdx = (x, row), with n0 + 1 threads
+//    per row and usually TY + 1 thread rows. The plane with three halo rows
+//    above and below lives in shared memory.
+//  * WENO5 is evaluated per interface (one interface gives p+ of a node and
+//    p- of the next). Along dimension 0 thread x computes the interface
+//    between nodes x-1 and x (the extra thread x = n0 the row's last one);
+//    along dimension 1 thread row k the one between tile rows k-1 and k (the
+//    extra thread row the tile's last one). So each node pays for about one
+//    interface per dimension instead of two.
 //  * For 3-D and 4-D grids the block streams along the last dimension through
 //    a chunk of planes: each thread keeps six values of its column in
 //    registers and carries the interface result p- to the next plane.
@@ -96,17 +98,27 @@ __device__ __forceinline__ StageRun<T> stage_run(const StageParams& P) {
 
 // One tile: rows y0 = row_tile*TY .. +TY-1 of the plane(s) at dimension-2 index
 // i2 (4-D) and the planes of chunk `chunk` along the streamed dimension
-// (planes chunk*tz .. +tz-1). (x, r) is this thread's position: x in 0..n0,
-// r in 0..; threads with r >= TY only take part in the barriers.
+// (planes chunk*tz .. +tz-1). The block has NR thread rows; (x, r) is this
+// thread's position, x in 0..n0, r in 0..NR-1 (threads with r >= NR only
+// take part in the barriers). Per plane, the interfaces along dimensions 0
+// and 1 are each evaluated once and shared through shared memory:
+//   x-interfaces: n0+1 per node row (rows k = r, r+NR, ...),
+//   y-interfaces: TY+1 per column (gaps k = r, r+NR, ...; gap k lies between
+//                 tile rows k-1 and k),
+// so with NR = TY+1 every thread evaluates at most one of each. The p- half
+// of the interface a thread evaluates for its own row or gap belongs to its
+// own node and stays in a register; the p+ half belongs to the neighbour
+// (x-1 or row k-1) and goes through shared memory.
 template <typename T, int D, int DYN>
-__device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T>& R, const int TY, const int tz,
-                                          const int row_tile, const int i2_in, const int chunk_in, const int x,
-                                          const int r, T* const smem) {
+__device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T>& R, const int TY, const int NR,
+                                          const int tz, const int row_tile, const int i2_in, const int chunk_in,
+                                          const int x, const int r, T* const smem) {
     const GridDev& g = P.g;
     const int nx = g.n[0], ny = g.n[1];
     const int W = nx + 6;  // shared row: 3 ghost cells, nx nodes, 3 ghost cells
-    // two buffers, alternating by plane: (TY + 6) rows x W, then p- and p+ along dimension 0 (TY x nx each)
-    const size_t buf_elems = (size_t)(TY + 6) * W + 2 * (size_t)TY * nx;
+    // two buffers, alternating by plane: (TY + 6) rows x W, then p+ along
+    // dimension 0 (TY rows of nx + 1) and along dimension 1 (TY + 1 rows of nx)
+    const size_t buf_elems = rows_buf_elems(nx, TY);
 
     const T* __restrict__ u = R.u;
     const T* __restrict__ vn = R.vn;
@@ -118,6 +130,7 @@ __device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T
     const int y0 = row_tile * TY;
     const int y = y0 + r;
     const int rows_valid = min(TY, ny - y0);
+    const bool in_rows = r < NR;
     const bool node = (x < nx) && (r < rows_valid);
 
     const int i2 = (D == 4) ? i2_in : 0;
@@ -163,9 +176,10 @@ __device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T
         const T* __restrict__ uz = uplane + zoff;
         T* const buf = smem + (size_t)((z - zfirst) & 1) * buf_elems;
         T* const plane = buf;
-        T* const pxm = buf + (size_t)(TY + 6) * W;
-        T* const pxp = pxm + (size_t)TY * nx;
+        T* const pxp = buf + (size_t)(TY + 6) * W;
+        T* const pyp = pxp + (size_t)TY * (nx + 1);
         T center = T(0);
+        T pm_x = T(0), pm_y = T(0);
         if (node) {
             if (D >= 3) {
                 q[5] = z_inside ? ld(uplane + colbase + (long long)(z + 3) * sS)
@@ -180,38 +194,58 @@ __device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T
             // from global memory (ghost rule along dimension 1), and the x-ghost
             // cells of each node row from its spare thread x == nx
             if (node) plane[(size_t)(r + 3) * W + 3 + x] = center;
-            if (x < nx && r < TY) {
-                for (int h = r; h < n_extra; h += TY) {
-                    const int rr = (h < 3) ? h - 3 : rows_valid + (h - 3);
-                    plane[(size_t)(rr + 3) * W + 3 + x] = line_value(uz + x, y0 + rr, ny, (long long)nx, per1, extrap);
-                }
-            } else if (r < rows_valid) {
-                const T* rowg = uz + (long long)y * nx;
-                T* rows = plane + (size_t)(r + 3) * W;
-                if (per0) {
-#pragma unroll
-                    for (int k = 0; k < 3; ++k) {
-                        rows[k] = ld(rowg + ((nx - 3 + k) % nx + nx) % nx);
-                        rows[nx + 3 + k] = ld(rowg + k % nx);
+            if (in_rows) {
+                if (x < nx) {
+                    for (int h = r; h < n_extra; h += NR) {
+                        const int rr = (h < 3) ? h - 3 : rows_valid + (h - 3);
+                        plane[(size_t)(rr + 3) * W + 3 + x] =
+                            line_value(uz + x, y0 + rr, ny, (long long)nx, per1, extrap);
                     }
-                } else {
-                    const T e0 = ld(rowg), e1 = ld(rowg + 1), f0 = ld(rowg + nx - 1), f1 = ld(rowg + nx - 2);
+                } else if (r < rows_valid) {
+                    const T* rowg = uz + (long long)y * nx;
+                    T* rows = plane + (size_t)(r + 3) * W;
+                    if (per0) {
 #pragma unroll
-                    for (int k = 0; k < 3; ++k) {
-                        rows[k] = ghost_value(e0, e1, 3 - k, extrap);
-                        rows[nx + 3 + k] = ghost_value(f0, f1, k + 1, extrap);
+                        for (int k = 0; k < 3; ++k) {
+                            rows[k] = ld(rowg + ((nx - 3 + k) % nx + nx) % nx);
+                            rows[nx + 3 + k] = ld(rowg + k % nx);
+                        }
+                    } else {
+                        const T e0 = ld(rowg), e1 = ld(rowg + 1), f0 = ld(rowg + nx - 1), f1 = ld(rowg + nx - 2);
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) {
+                            rows[k] = ghost_value(e0, e1, 3 - k, extrap);
+                            rows[nx + 3 + k] = ghost_value(f0, f1, k + 1, extrap);
+                        }
                     }
                 }
             }
             __syncthreads();
-            // interface between nodes x-1 and x of row r (x = nx: the row's last interface)
-            if (r < rows_valid) {
-                const T* a = plane + (size_t)(r + 3) * W + x;  // a[k] = value at node x - 3 + k
-                T ppj, pmj1;
+            // x-interface between nodes x-1 and x of row r (x = nx: the row's last one);
+            // pxp slot r*(nx+1) + x receives p+ of node x-1 (slot 0 of a row is unused)
+            if (in_rows && r < rows_valid) {
+                const T* a = plane + (size_t)(r + 3) * W + x;  // a[m] = value at node x - 3 + m
+                T ppj;
                 weno_iface(a[1] - a[0], a[2] - a[1], a[3] - a[2], a[4] - a[3], a[5] - a[4], floor_raw, inv_dx0, ppj,
-                           pmj1);
-                if (x >= 1) pxp[(size_t)r * nx + x - 1] = ppj;
-                if (x < nx) pxm[(size_t)r * nx + x] = pmj1;
+                           pm_x);
+                pxp[(size_t)r * (nx + 1) + x] = ppj;
+            }
+            // y-interface of gap k (between tile rows k-1 and k) of column x, k = r;
+            // pyp slot k*nx + x receives p+ of tile row k-1 (row 0 of pyp is unused)
+            if (x < nx && in_rows && r <= rows_valid) {
+                const T* c = plane + (size_t)r * W + 3 + x;  // c[m W] = tile row r - 3 + m
+                T ppj;
+                weno_iface(c[W] - c[0], c[2 * W] - c[W], c[3 * W] - c[2 * W], c[4 * W] - c[3 * W],
+                           c[5 * W] - c[4 * W], floor_raw, inv_dx1, ppj, pm_y);
+                pyp[(size_t)r * nx + x] = ppj;
+            }
+            // without an extra thread row (NR == TY), row 0 also takes the tile's last gap
+            if (NR <= rows_valid && r == 0 && x < nx) {
+                const T* c = plane + (size_t)NR * W + 3 + x;
+                T ppj, unused;
+                weno_iface(c[W] - c[0], c[2 * W] - c[W], c[3 * W] - c[2 * W], c[4 * W] - c[3 * W],
+                           c[5 * W] - c[4 * W], floor_raw, inv_dx1, ppj, unused);
+                pyp[(size_t)NR * nx + x] = ppj;
             }
             __syncthreads();
         }
@@ -224,20 +258,10 @@ __device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T
                 pm[SD] = carry;
             }
             if (!warm) {
-                pm[0] = pxm[(size_t)r * nx + x];
-                pp[0] = pxp[(size_t)r * nx + x];
-                {
-                    // dimension 1: p- from the interface below the node, p+ from the one above
-                    const T* c = plane + (size_t)r * W + 3 + x;
-                    T v[7];
-#pragma unroll
-                    for (int k = 0; k < 7; ++k) v[k] = c[(size_t)k * W];
-                    T unused0, unused1;
-                    weno_iface(v[1] - v[0], v[2] - v[1], v[3] - v[2], v[4] - v[3], v[5] - v[4], floor_raw, inv_dx1,
-                               unused0, pm[1]);
-                    weno_iface(v[2] - v[1], v[3] - v[2], v[4] - v[3], v[5] - v[4], v[6] - v[5], floor_raw, inv_dx1,
-                               pp[1], unused1);
-                }
+                pm[0] = pm_x;
+                pp[0] = pxp[(size_t)r * (nx + 1) + x + 1];
+                pm[1] = pm_y;
+                pp[1] = pyp[(size_t)(r + 1) * nx + x];
                 if constexpr (D == 4) {
                     T v[7];
                     gather7<T>(u, (long long)i2 * g.stride[2] + zoff + colbase, i2, g.n[2], g.stride[2],
@@ -280,7 +304,7 @@ __global__ void __launch_bounds__(RowsLimits<T>::kMaxThreads) rows_kernel(const 
     const StageRun<T> R = stage_run<T>(P);
     const int i2 = (D == 4) ? (int)blockIdx.y : 0;
     const int chunk = (D == 3) ? (int)blockIdx.y : ((D == 4) ? (int)blockIdx.z : 0);
-    rows_tile<T, D, DYN>(P, R, C.ty, C.tz, blockIdx.x, i2, chunk, threadIdx.x, threadIdx.y,
+    rows_tile<T, D, DYN>(P, R, C.ty, C.nr, C.tz, blockIdx.x, i2, chunk, threadIdx.x, threadIdx.y,
                          reinterpret_cast<T*>(smem_raw));
 }
 
@@ -292,7 +316,7 @@ inline size_t rows_smem_bytes(int nx, int ty) {
 
 template <typename T, int D, int DYN>
 inline void rows_shape(const StageParams& p, const RowsCfg& c, dim3& grid, dim3& block, size_t& smem) {
-    block = dim3((unsigned)(p.g.n[0] + 1), (unsigned)c.ty, 1);
+    block = dim3((unsigned)(p.g.n[0] + 1), (unsigned)c.nr, 1);
     grid = dim3((unsigned)c.row_tiles, 1, 1);
     if (D == 3) grid.y = (unsigned)c.nchunks;
     if (D == 4) { grid.y = (unsigned)p.g.n[2]; grid.z = (unsigned)c.nchunks; }

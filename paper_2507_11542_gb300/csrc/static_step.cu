@@ -98,10 +98,11 @@ bool pick_rows(const StageParams& P, int dtype, int sm_count, RowsCfg* c) {
     const int nx = G.n[0], ny = G.n[1];
     if (nx + 1 > max_threads) return false;
     int ty = 1;
-    while (ty < ny && (nx + 1) * (ty + 1) <= max_threads && (nx + 1) * ty < 256) ++ty;
+    while (ty < ny && (nx + 1) * (ty + 2) <= max_threads && (nx + 1) * ty < 256) ++ty;
     const size_t es = dtype == HJ_F64 ? 8 : 4;
     if (rows_smem(nx, ty, es) > 200 * 1024) return false;
     c->ty = ty;
+    c->nr = rows_thread_rows(nx, ty, max_threads);
     c->row_tiles = (ny + ty - 1) / ty;
     const int ns = D >= 3 ? G.n[D - 1] : 1;
     const long long per_plane = (long long)c->row_tiles * (D == 4 ? G.n[2] : 1);
