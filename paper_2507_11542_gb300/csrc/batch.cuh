@@ -14,7 +14,8 @@ __device__ __forceinline__ T batch_dt(const BatchInst& I);
 template <> __device__ __forceinline__ double batch_dt<double>(const BatchInst& I) { return I.dt; }
 template <> __device__ __forceinline__ float batch_dt<float>(const BatchInst& I) { return I.dt_f; }
 
-template <typename T, int D, int DYN>
+// KIND: kKindFirst for stage 1, kKindCombine for stages 2 and 3.
+template <typename T, int D, int DYN, int KIND>
 __global__ void __launch_bounds__(RowsLimits<T>::kMaxThreads)
     batch_kernel(const BatchTile* __restrict__ tiles, const BatchInst* __restrict__ insts, const int stage) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -27,26 +28,20 @@ __global__ void __launch_bounds__(RowsLimits<T>::kMaxThreads)
     StageRun<T> R;
     R.dt = batch_dt<T>(I);
     R.brt0 = I.brt == HJ_BRT_MIN0;
-    R.term = false;
     R.also_out = nullptr;
+    R.minv = false;
     if (stage == 1) {
         R.u = static_cast<const T*>(I.V);
         R.vn = nullptr;
         R.out = static_cast<T*>(I.V1);
         R.cv = T(0);
         R.cu = T(1);
-        R.has_vn = false;
-        R.use_cv = false;
-        R.minv = false;
     } else if (stage == 2) {
         R.u = static_cast<const T*>(I.V1);
         R.vn = static_cast<const T*>(I.V);
         R.out = static_cast<T*>(I.V2);
         R.cv = T(0.75);
         R.cu = T(0.25);
-        R.has_vn = true;
-        R.use_cv = true;
-        R.minv = false;
     } else {
         R.u = static_cast<const T*>(I.V2);
         R.vn = static_cast<const T*>(I.V);
@@ -54,26 +49,32 @@ __global__ void __launch_bounds__(RowsLimits<T>::kMaxThreads)
         R.also_out = static_cast<T*>(I.slice_out);
         R.cv = T(1.0 / 3.0);
         R.cu = T(2.0 / 3.0);
-        R.has_vn = true;
-        R.use_cv = true;
         R.minv = I.brt == HJ_BRT_MINV;
     }
     const int nr = (int)blockDim.x / (nx + 1);
-    rows_tile<T, D, DYN>(I.P, R, I.ty, nr, I.tz, t.row_tile, t.i2, t.chunk, x, r, reinterpret_cast<T*>(smem_raw));
+    rows_tile<T, D, DYN, KIND>(I.P, R, I.ty, nr, I.tz, t.row_tile, t.i2, t.chunk, x, r,
+                               reinterpret_cast<T*>(smem_raw));
+}
+
+template <typename T, int D, int DYN, int KIND>
+cudaError_t launch_batch_kind(const BatchTile* tiles, int ntiles, const BatchInst* insts, int stage, int threads,
+                              size_t smem, cudaStream_t s) {
+    static bool done = false;  // benign race: setting the attribute twice is harmless
+    if (!done) {
+        cudaError_t e = cudaFuncSetAttribute(batch_kernel<T, D, DYN, KIND>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e != cudaSuccess) return e;
+        done = true;
+    }
+    batch_kernel<T, D, DYN, KIND><<<ntiles, threads, smem, s>>>(tiles, insts, stage);
+    return cudaGetLastError();
 }
 
 template <typename T, int D, int DYN>
 cudaError_t launch_batch_dyn(const BatchTile* tiles, int ntiles, const BatchInst* insts, int stage, int threads,
                              size_t smem, cudaStream_t s) {
-    static bool done = false;  // benign race: setting the attribute twice is harmless
-    if (!done) {
-        cudaError_t e = cudaFuncSetAttribute(batch_kernel<T, D, DYN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             200 * 1024);
-        if (e != cudaSuccess) return e;
-        done = true;
-    }
-    batch_kernel<T, D, DYN><<<ntiles, threads, smem, s>>>(tiles, insts, stage);
-    return cudaGetLastError();
+    return stage == 1 ? launch_batch_kind<T, D, DYN, kKindFirst>(tiles, ntiles, insts, stage, threads, smem, s)
+                      : launch_batch_kind<T, D, DYN, kKindCombine>(tiles, ntiles, insts, stage, threads, smem, s);
 }
 
 #define HJ_BATCH_DISPATCH(T)                                                                                   \

@@ -277,7 +277,6 @@ StageParams stage_params(hj_ctx* ctx, const GridDev& G, const hj_method* m, int 
 // Row-tiled WENO5 kernel: eligibility, launch-shape tuning, dispatch
 // ---------------------------------------------------------------------------
 
-int rows_max_threads(int dtype) { return dtype == HJ_F64 ? 512 : 1024; }
 
 bool rows_eligible(const GridDev& G, int scheme, int dynamics, int dtype) {
     if (scheme != HJ_WENO5 || !rows_supported(G.ndim, dynamics)) return false;
@@ -285,15 +284,16 @@ bool rows_eligible(const GridDev& G, int scheme, int dynamics, int dtype) {
         if (env[0] == '0') return false;
     for (int d = 0; d < G.ndim; ++d)
         if (G.n[d] < 4) return false;
-    if (G.n[0] + 1 > rows_max_threads(dtype)) return false;
+    if (G.n[0] + 1 > rows_max_threads(dtype == HJ_F64)) return false;
     if (G.ndim == 4 && G.n[2] > 65535) return false;
+    if (G.total >= (1LL << 31)) return false;  // the row kernel indexes with 32-bit integers
     return true;
 }
 
 RowsCfg make_rows_cfg(const GridDev& G, int ty, int tz, int dtype) {
     RowsCfg c;
     c.ty = ty;
-    c.nr = rows_thread_rows(G.n[0], ty, rows_max_threads(dtype));
+    c.nr = rows_thread_rows(G.n[0], ty, rows_max_threads(dtype == HJ_F64));
     c.row_tiles = (G.n[1] + ty - 1) / ty;
     const int ns = G.ndim >= 3 ? G.n[G.ndim - 1] : 1;
     c.tz = G.ndim >= 3 ? tz : 1;
@@ -324,7 +324,7 @@ std::vector<RowsCfg> rows_candidates(hj_ctx* ctx, const StageParams& P, int dtyp
     static const int tzs[] = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64, 128, 256};
     std::vector<std::pair<double, RowsCfg>> scored;
     for (int ty : tys) {
-        if (ty > ny || (nx + 1) * ty > rows_max_threads(dtype)) continue;
+        if (ty > ny || (nx + 1) * ty > rows_max_threads(dtype == HJ_F64)) continue;
         if (rows_smem(nx, ty, es) > 200 * 1024) continue;
         std::vector<int> zs;
         if (D >= 3) {
@@ -357,8 +357,8 @@ std::vector<RowsCfg> rows_candidates(hj_ctx* ctx, const StageParams& P, int dtyp
 }
 
 // The launch shape for this grid: measured once per (shape, dtype, dynamics)
-// over the model's best candidates (stage kernel in term mode writing to a
-// scratch buffer), then cached in the context. HJ_TUNE=0 keeps the model's
+// over the model's best candidates (a first-stage launch writing to a
+// scratch buffer, best of three), then cached in the context. HJ_TUNE=0 keeps the model's
 // first choice without timing.
 hj_status rows_config(hj_ctx* ctx, const StageParams& P, int dtype, RowsCfg* out) {
     const GridDev& G = P.g;
@@ -366,7 +366,7 @@ hj_status rows_config(hj_ctx* ctx, const StageParams& P, int dtype, RowsCfg* out
     if (const char* pin = std::getenv("HJ_ROWS_CFG")) {
         int ty = 0, tz = 0;
         if (std::sscanf(pin, "%d,%d", &ty, &tz) == 2 && ty >= 1 && tz >= 1 && ty <= G.n[1] &&
-            (G.n[0] + 1) * ty <= rows_max_threads(dtype)) {
+            (G.n[0] + 1) * ty <= rows_max_threads(dtype == HJ_F64)) {
             *out = make_rows_cfg(G, ty, tz, dtype);
             if (out->nchunks <= 65535 && rows_bps(P, *out, dtype) > 0) return HJ_OK;
         }
@@ -386,8 +386,13 @@ hj_status rows_config(hj_ctx* ctx, const StageParams& P, int dtype, RowsCfg* out
         const size_t bytes = (size_t)G.total * (dtype == HJ_F64 ? 8 : 4);
         hj_status st = ensure(ctx, &ctx->tune_buf, &ctx->tune_bytes, bytes);
         if (st) return st;
+        // timed as a first RK stage (reads u, writes the scratch buffer)
         StageParams T = P;
-        T.mode = kTerm;
+        T.mode = kStage;
+        T.vn = nullptr;
+        T.cv = 0.0;
+        T.cu = 1.0;
+        T.minv_after = 0;
         T.out = ctx->tune_buf;
         cudaEvent_t e0, e1;
         HJ_CUDA(ctx, cudaEventCreate(&e0));
@@ -396,7 +401,7 @@ hj_status rows_config(hj_ctx* ctx, const StageParams& P, int dtype, RowsCfg* out
         for (const RowsCfg& c : cands) {
             cudaError_t e = rows_launch(ctx, T, c, dtype);  // warm-up
             float ms_min = 1e30f;
-            for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+            for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
                 cudaEventRecord(e0, ctx->stream);
                 e = rows_launch(ctx, T, c, dtype);
                 cudaEventRecord(e1, ctx->stream);

@@ -9,6 +9,13 @@ namespace hj {
 
 constexpr int kMaxDim = 4;
 
+// Largest block of the row-tiled kernels: FP32 blocks may hold 1024 threads
+// (<= 64 registers each), FP64 blocks 512 (<= 128 registers), since the FP64
+// interface arithmetic needs more registers.
+constexpr int kRowsMaxThreadsF32 = 1024;
+constexpr int kRowsMaxThreadsF64 = 512;
+inline int rows_max_threads(int dtype_is_f64) { return dtype_is_f64 ? kRowsMaxThreadsF64 : kRowsMaxThreadsF32; }
+
 // Grid as the kernels see it. Spacing and its inverse are computed once on
 // the host from the hj_grid (periodic: (hi-lo)/n, else (hi-lo)/(n-1)).
 struct GridDev {
@@ -44,8 +51,9 @@ struct StageParams {
     const double* trig_d;  // cos, sin of the dimension-2 coordinate: [cos(0..n2-1), sin(0..n2-1)]
     const float* trig_f;
     double weno_floor;     // additive floor of the WENO5 epsilon, in raw-difference units
+    double half_inv_dx[kMaxDim];  // 1 / (2 dx): raw differences to (p- + p+)/2 and (p+ - p-)/2
     // FP32 copies of the scalars above, so that FP32 kernels do no FP64 arithmetic
-    float lo_f[kMaxDim], dx_f[kMaxDim], inv_dx_f[kMaxDim];
+    float lo_f[kMaxDim], dx_f[kMaxDim], inv_dx_f[kMaxDim], half_inv_dx_f[kMaxDim];
     float params_f[8];
     float dt_f, cv_f, cu_f, weno_floor_f;
     int has_vn;            // the stage reads Vn (cv != 0 or minv_after)
@@ -57,6 +65,8 @@ inline StageParams finalize(StageParams p) {
         p.lo_f[d] = (float)p.g.lo[d];
         p.dx_f[d] = (float)p.g.dx[d];
         p.inv_dx_f[d] = (float)p.g.inv_dx[d];
+        p.half_inv_dx[d] = 0.5 * p.g.inv_dx[d];
+        p.half_inv_dx_f[d] = (float)p.half_inv_dx[d];
     }
     for (int k = 0; k < 8; ++k) p.params_f[k] = (float)p.params[k];
     p.dt_f = (float)p.dt;
@@ -65,6 +75,14 @@ inline StageParams finalize(StageParams p) {
     p.weno_floor_f = (float)p.weno_floor;
     p.has_vn = (p.mode == kStage) && (p.cv != 0.0 || p.minv_after);
     return p;
+}
+
+// What the row kernels store per node, by launch (a template parameter, so
+// that no per-node branch remains): the stage term alone, the first RK
+// stage (no V^n), or a combination with V^n (stages 2 and 3).
+enum StageKind { kKindTerm = 0, kKindFirst = 1, kKindCombine = 2 };
+inline int stage_kind(const StageParams& p) {  // p finalized
+    return p.mode == kTerm ? kKindTerm : (p.has_vn ? kKindCombine : kKindFirst);
 }
 
 struct UpwindParams {
@@ -94,9 +112,11 @@ inline int rows_thread_rows(int nx, int ty, int max_threads) {
 
 // Elements of one of the two alternating shared buffers of a rows_kernel
 // block: (ty + 6) padded rows of n0 + 6, then p+ along dimension 0 (ty rows
-// of n0 + 1) and along dimension 1 (ty + 1 rows of n0).
+// of n0 + 1), along dimension 1 (ty + 1 rows of n0), and the two outermost
+// values at each end of every node row (4 per row, for the ghost cells).
 __host__ __device__ inline size_t rows_buf_elems(int nx, int ty) {
-    return (size_t)(ty + 6) * (size_t)(nx + 6) + (size_t)ty * (size_t)(nx + 1) + (size_t)(ty + 1) * (size_t)nx;
+    return (size_t)(ty + 6) * (size_t)(nx + 6) + (size_t)ty * (size_t)(nx + 1) + (size_t)(ty + 1) * (size_t)nx +
+           4 * (size_t)ty;
 }
 
 // Dynamic shared memory of a rows_kernel block (element size es).

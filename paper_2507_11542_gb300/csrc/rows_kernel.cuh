@@ -13,7 +13,9 @@
 //    interface per dimension instead of two.
 //  * For 3-D and 4-D grids the block streams along the last dimension through
 //    a chunk of planes: each thread keeps six values of its column in
-//    registers and carries the interface result p- to the next plane.
+//    registers and carries the interface result p- to the next plane. Planes
+//    are staged in shared memory two ahead of their use (asynchronous
+//    copies), with one barrier per plane.
 //  * In 4-D, dimension 2 is differentiated two-sided from 7-point loads.
 //  * Ghost values (periodic wrap or slope continued away from zero, Sec. 2.1)
 //    are produced where values are read; no padded array exists.
@@ -26,11 +28,9 @@
 
 namespace hj {
 
-// FP32 blocks may hold 1024 threads (<= 64 registers each); FP64 blocks at
-// most 512 (<= 128 registers), since the FP64 interface math needs more.
 template <typename T> struct RowsLimits;
-template <> struct RowsLimits<float> { static constexpr int kMaxThreads = 1024; };
-template <> struct RowsLimits<double> { static constexpr int kMaxThreads = 512; };
+template <> struct RowsLimits<float> { static constexpr int kMaxThreads = kRowsMaxThreadsF32; };
+template <> struct RowsLimits<double> { static constexpr int kMaxThreads = kRowsMaxThreadsF64; };
 
 template <typename T>
 __device__ __forceinline__ T ghost_value(T edge, T inner, int m, int extrap) {
@@ -53,19 +53,6 @@ __device__ __forceinline__ T line_value(const T* __restrict__ base, int i, int n
     return ghost_value(ld(base + (long long)(n - 1) * s), ld(base + (long long)(n - 2) * s), i - (n - 1), extrap);
 }
 
-// Value at index i of a shared-memory row of n nodes (ghosts from its ends).
-template <typename T>
-__device__ __forceinline__ T row_value(const T* row, int i, int n, bool periodic, int extrap) {
-    if (i >= 0 && i < n) return row[i];
-    if (periodic) {
-        int j = i % n;
-        if (j < 0) j += n;
-        return row[j];
-    }
-    if (i < 0) return ghost_value(row[0], row[1], -i, extrap);
-    return ghost_value(row[n - 1], row[n - 2], i - (n - 1), extrap);
-}
-
 // Values of one stage launch that differ between the three RK stages, in the
 // kernel's precision (kept in registers).
 template <typename T>
@@ -75,7 +62,7 @@ struct StageRun {
     T* out;            // result
     T* also_out;       // if not null, the result is written here as well (a time slice)
     T dt, cv, cu;
-    bool has_vn, use_cv, minv, brt0, term;
+    bool minv, brt0;
 };
 
 template <typename T>
@@ -88,37 +75,68 @@ __device__ __forceinline__ StageRun<T> stage_run(const StageParams& P) {
     R.dt = SP<T>::dt(P);
     R.cv = SP<T>::cv(P);
     R.cu = SP<T>::cu(P);
-    R.has_vn = P.has_vn;
-    R.use_cv = P.cv != 0.0;
     R.minv = P.minv_after;
     R.brt0 = P.brt_min0;
-    R.term = P.mode == kTerm;
     return R;
 }
+
+// Asynchronous copy of one element from global to shared memory (cp.async:
+// no register is involved). The issuing thread waits for its own copies with
+// cp_async_wait_all; a barrier after that publishes them to the block.
+template <typename T> __device__ __forceinline__ void cp_async_elem(T* dst, const T* src);
+template <> __device__ __forceinline__ void cp_async_elem<float>(float* dst, const float* src) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+    const size_t gsrc = __cvta_generic_to_global(src);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+template <> __device__ __forceinline__ void cp_async_elem<double>(double* dst, const double* src) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+    const size_t gsrc = __cvta_generic_to_global(src);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // One tile: rows y0 = row_tile*TY .. +TY-1 of the plane(s) at dimension-2 index
 // i2 (4-D) and the planes of chunk `chunk` along the streamed dimension
 // (planes chunk*tz .. +tz-1). The block has NR thread rows; (x, r) is this
 // thread's position, x in 0..n0, r in 0..NR-1 (threads with r >= NR only
-// take part in the barriers). Per plane, the interfaces along dimensions 0
-// and 1 are each evaluated once and shared through shared memory:
-//   x-interfaces: n0+1 per node row (rows k = r, r+NR, ...),
-//   y-interfaces: TY+1 per column (gaps k = r, r+NR, ...; gap k lies between
-//                 tile rows k-1 and k),
+// take part in the barriers).
+//
+// Interfaces along dimensions 0 and 1 are each evaluated once per plane and
+// shared through shared memory:
+//   x-interfaces: n0+1 per node row (row r by thread row r),
+//   y-interfaces: TY+1 per column (gap k, between tile rows k-1 and k, by
+//                 thread row k; without an extra thread row, thread row 0
+//                 also takes the last gap),
 // so with NR = TY+1 every thread evaluates at most one of each. The p- half
 // of the interface a thread evaluates for its own row or gap belongs to its
 // own node and stays in a register; the p+ half belongs to the neighbour
-// (x-1 or row k-1) and goes through shared memory.
-template <typename T, int D, int DYN>
+// (x-1 or row k-1) and goes through shared memory. Derivatives stay raw
+// (undivided differences) until the node combines them, scaled by 1/(2 dx),
+// into the means and half differences the Hamiltonian takes.
+//
+// Planes are software-pipelined through two shared buffers (plane p in
+// buffer p mod 2) with one barrier per plane:
+//   phase A(z): interfaces of plane z; ghost cells of plane z+1 from its row
+//               ends; wait for this thread's copies into plane z+1
+//   barrier
+//   phase B(z): node updates of plane z; staging of plane z+2 (node values
+//               from the column queues, halo rows and row ends copied
+//               asynchronously), two planes ahead of its use.
+// Flat indices are 32-bit (the grid has fewer than 2^31 nodes).
+template <typename T, int D, int DYN, int KIND>
 __device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T>& R, const int TY, const int NR,
                                           const int tz, const int row_tile, const int i2_in, const int chunk_in,
                                           const int x, const int r, T* const smem) {
     const GridDev& g = P.g;
     const int nx = g.n[0], ny = g.n[1];
     const int W = nx + 6;  // shared row: 3 ghost cells, nx nodes, 3 ghost cells
-    // two buffers, alternating by plane: (TY + 6) rows x W, then p+ along
-    // dimension 0 (TY rows of nx + 1) and along dimension 1 (TY + 1 rows of nx)
-    const size_t buf_elems = rows_buf_elems(nx, TY);
+    // per buffer: (TY + 6) rows x W, p+ along dimension 0 (TY rows of nx + 1),
+    // p+ along dimension 1 (TY + 1 rows of nx), row ends (4 per node row)
+    const int buf_elems = (int)rows_buf_elems(nx, TY);
+    const int o_pxp = (TY + 6) * W;
+    const int o_pyp = o_pxp + TY * (nx + 1);
+    const int o_ends = o_pyp + (TY + 1) * nx;
 
     const T* __restrict__ u = R.u;
     const T* __restrict__ vn = R.vn;
@@ -132,6 +150,11 @@ __device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T
     const int rows_valid = min(TY, ny - y0);
     const bool in_rows = r < NR;
     const bool node = (x < nx) && (r < rows_valid);
+    const bool do_xrow = in_rows && r < rows_valid;
+    const bool do_ygap = in_rows && x < nx && r <= rows_valid;
+    const bool do_ylast = NR <= rows_valid && r == 0 && x < nx;
+    const bool spare = in_rows && x == nx && r < rows_valid;  // the spare thread of node row r
+    const bool halo_thread = in_rows && x < nx;
 
     const int i2 = (D == 4) ? i2_in : 0;
     const int chunk = (D >= 3) ? chunk_in : 0;
@@ -139,156 +162,212 @@ __device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T
     const int ns = (D >= 3) ? g.n[SD] : 1;
     const int zbeg = (D >= 3) ? chunk * tz : 0;
     const int zend = (D >= 3) ? min(ns, zbeg + tz) : 1;
-    const long long sS = (D >= 3) ? g.stride[SD] : 0;
+    const int sS = (D >= 3) ? (int)g.stride[SD] : 0;
     const bool perS = (D >= 3) ? ((g.periodic_mask >> SD) & 1u) : false;
     // the chunk's streamed-dimension reads stay inside the grid: no ghost logic needed
     const bool z_inside = (D < 3) || (zbeg >= 3 && zend + 3 <= ns);
-    const T* __restrict__ uplane = u + ((D == 4) ? (long long)i2 * g.stride[2] : 0);
-    const long long colbase = (long long)min(x, nx - 1) + (long long)min(y, ny - 1) * nx;  // within a plane
+    const int plane0 = (D == 4) ? i2 * (int)g.stride[2] : 0;      // flat index of (0, 0, i2, 0)
+    const int col = plane0 + min(x, nx - 1) + min(y, ny - 1) * nx;  // flat index of (x, y) at streamed index 0
+    const T* __restrict__ ucol = u + col;
 
-    const T inv_dx0 = SP<T>::inv_dx(P, 0);
-    const T inv_dx1 = SP<T>::inv_dx(P, 1);
-    const T inv_dxs = SP<T>::inv_dx(P, SD);
+    // shared-memory offsets within a buffer
+    const int s_center = (r + 3) * W + 3 + x;
+    const int s_xrow = (r + 3) * W + x;        // value at node x - 3 of row r
+    const int s_ycol = r * W + 3 + x;          // value at tile row r - 3 of column x
+    const int s_ylast = NR * W + 3 + x;
+    const int s_pxp = o_pxp + r * (nx + 1) + x;  // p+ of node x - 1 of row r (written); + 1: of node x (read)
+    const int s_pyp = o_pyp + r * nx + x;        // p+ of tile row r - 1 (written); + nx: of row r (read)
+
+    const T h0 = SP<T>::half_inv_dx(P, 0), h1 = SP<T>::half_inv_dx(P, 1), hS = SP<T>::half_inv_dx(P, SD);
     const T dt = R.dt, cv = R.cv, cu = R.cu;
-    const bool has_vn = R.has_vn, use_cv = R.use_cv, minv = R.minv, brt0 = R.brt0;
-    const bool term_mode = R.term;
+    const bool minv = R.minv, brt0 = R.brt0;
     T* __restrict__ also_out = R.also_out;
+    // node coordinates that do not change along the streamed dimension
+    T xc[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) xc[d] = T(0);
+    if constexpr (uses_coord<D, DYN>(0)) xc[0] = SP<T>::lo(P, 0) + T(x) * SP<T>::dx(P, 0);
+    if constexpr (uses_coord<D, DYN>(1)) xc[1] = SP<T>::lo(P, 1) + T(y) * SP<T>::dx(P, 1);
+    if constexpr (D == 4 && uses_coord<D, DYN>(2)) xc[2] = SP<T>::lo(P, 2) + T(i2) * SP<T>::dx(P, 2);
+    const T* __restrict__ trig = Trig<T>::get(P);
+    T cos2 = T(0), sin2 = T(0);  // angle of dimension 2 (fixed for the block in 4-D)
+    if constexpr (D == 4 && uses_angle<D, DYN>()) {
+        cos2 = trig[i2];
+        sin2 = trig[g.n[2] + i2];
+    }
 
     // Halo rows (three above, three below, and rows past the grid edge in a
-    // ragged last tile) are loaded by thread rows in turn: row h of n_extra.
+    // ragged last tile), loaded by thread rows in turn: row h of n_extra.
     const int n_extra = 3 + (TY + 3 - rows_valid);
 
-    // Streamed-dimension queue: q[k] = V at plane z-2+k (k = 0..5); carry = p- at z.
-    // The loop starts one plane early (a warm-up iteration that only evaluates
-    // the streamed interface) so that every interface goes through the same
-    // code and results do not depend on where chunks start.
+    // Plane p into buffer b, except the node values: halo rows (in-grid or
+    // periodic rows copied asynchronously, rows past an extrapolated edge by
+    // the ghost rule) and, from the spare thread, the row's x-ghost sources
+    // (periodic: the wrapped nodes into the ghost cells; extrapolated: the
+    // two outermost nodes at each end into the row-end slots).
+    auto stage_rest = [&](int p, T* b) {
+        const int fp = p * sS;
+        if (halo_thread) {
+            const T* base = u + plane0 + fp + x;
+            for (int h = r; h < n_extra; h += NR) {
+                const int rr = (h < 3) ? h - 3 : rows_valid + (h - 3);
+                int yy = y0 + rr;
+                T* dst = b + (rr + 3) * W + 3 + x;
+                if (per1 && (yy < 0 || yy >= ny)) yy = (yy % ny + ny) % ny;
+                if (yy >= 0 && yy < ny) cp_async_elem(dst, base + yy * nx);
+                else *dst = line_value(base, yy, ny, (long long)nx, false, extrap);
+            }
+        } else if (spare) {
+            const T* rowg = u + plane0 + fp + y * nx;
+            if (per0) {
+                T* rows = b + (r + 3) * W;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    cp_async_elem(rows + k, rowg + nx - 3 + k);
+                    cp_async_elem(rows + nx + 3 + k, rowg + k);
+                }
+            } else {
+                T* e = b + o_ends + 4 * r;
+                cp_async_elem(e + 0, rowg);
+                cp_async_elem(e + 1, rowg + 1);
+                cp_async_elem(e + 2, rowg + nx - 1);
+                cp_async_elem(e + 3, rowg + nx - 2);
+            }
+        }
+    };
+    // Spare thread, after its copies into b have landed: the extrapolated x-ghost cells of its row.
+    auto finish_ghosts = [&](T* b) {
+        if (spare && !per0) {
+            const T* e = b + o_ends + 4 * r;
+            T* rows = b + (r + 3) * W;
+            const T e0 = e[0], e1 = e[1], f0 = e[2], f1 = e[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                rows[k] = ghost_value(e0, e1, 3 - k, extrap);
+                rows[nx + 3 + k] = ghost_value(f0, f1, k + 1, extrap);
+            }
+        }
+    };
+
+    // Streamed-dimension queue: q[k] = V at plane z-2+k (k = 0..5); carry = raw p- at z.
+    // A warm-up step evaluates the interface below the first plane, so that
+    // every interface goes through the same code and results do not depend
+    // on where chunks start.
     T q[6];
     T carry = T(0);
     if (D >= 3 && node) {
 #pragma unroll
-        for (int k = 0; k < 5; ++k) q[k] = line_value(uplane + colbase, zbeg - 3 + k, ns, sS, perS, extrap);
+        for (int k = 0; k < 6; ++k) q[k] = line_value(ucol, zbeg - 3 + k, ns, (long long)sS, perS, extrap);
+        T unused;
+        weno_iface(q[1] - q[0], q[2] - q[1], q[3] - q[2], q[4] - q[3], q[5] - q[4], floor_raw, unused, carry);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) q[k] = q[k + 1];
     }
-    const int zfirst = (D >= 3) ? zbeg - 1 : zbeg;
 
-    for (int z = zfirst; z < zend; ++z) {
-        const bool warm = z < zbeg;  // block-uniform
-        const long long zoff = (D >= 3) ? (long long)z * sS : 0;
-        const T* __restrict__ uz = uplane + zoff;
-        T* const buf = smem + (size_t)((z - zfirst) & 1) * buf_elems;
-        T* const plane = buf;
-        T* const pxp = buf + (size_t)(TY + 6) * W;
-        T* const pyp = pxp + (size_t)TY * (nx + 1);
-        T center = T(0);
-        T pm_x = T(0), pm_y = T(0);
-        if (node) {
-            if (D >= 3) {
-                q[5] = z_inside ? ld(uplane + colbase + (long long)(z + 3) * sS)
-                                : line_value(uplane + colbase, z + 3, ns, sS, perS, extrap);
-                center = q[2];
-            } else {
-                center = ld(uz + colbase);
-            }
+    // prologue: planes zbeg and zbeg+1 (ghost cells of zbeg+1 follow in phase A(zbeg))
+    {
+        T* const b0 = smem;
+        if (node) b0[s_center] = (D >= 3) ? q[2] : ld(ucol);
+        stage_rest(zbeg, b0);
+        if (zbeg + 1 < zend) {
+            T* const b1 = smem + buf_elems;
+            if (node) b1[s_center] = q[3];
+            stage_rest(zbeg + 1, b1);
         }
-        if (!warm) {
-            // stage the plane: node rows from the threads' own values, halo rows
-            // from global memory (ghost rule along dimension 1), and the x-ghost
-            // cells of each node row from its spare thread x == nx
-            if (node) plane[(size_t)(r + 3) * W + 3 + x] = center;
-            if (in_rows) {
-                if (x < nx) {
-                    for (int h = r; h < n_extra; h += NR) {
-                        const int rr = (h < 3) ? h - 3 : rows_valid + (h - 3);
-                        plane[(size_t)(rr + 3) * W + 3 + x] =
-                            line_value(uz + x, y0 + rr, ny, (long long)nx, per1, extrap);
-                    }
-                } else if (r < rows_valid) {
-                    const T* rowg = uz + (long long)y * nx;
-                    T* rows = plane + (size_t)(r + 3) * W;
-                    if (per0) {
-#pragma unroll
-                        for (int k = 0; k < 3; ++k) {
-                            rows[k] = ld(rowg + ((nx - 3 + k) % nx + nx) % nx);
-                            rows[nx + 3 + k] = ld(rowg + k % nx);
-                        }
-                    } else {
-                        const T e0 = ld(rowg), e1 = ld(rowg + 1), f0 = ld(rowg + nx - 1), f1 = ld(rowg + nx - 2);
-#pragma unroll
-                        for (int k = 0; k < 3; ++k) {
-                            rows[k] = ghost_value(e0, e1, 3 - k, extrap);
-                            rows[nx + 3 + k] = ghost_value(f0, f1, k + 1, extrap);
-                        }
-                    }
-                }
-            }
-            __syncthreads();
-            // x-interface between nodes x-1 and x of row r (x = nx: the row's last one);
-            // pxp slot r*(nx+1) + x receives p+ of node x-1 (slot 0 of a row is unused)
-            if (in_rows && r < rows_valid) {
-                const T* a = plane + (size_t)(r + 3) * W + x;  // a[m] = value at node x - 3 + m
-                T ppj;
-                weno_iface(a[1] - a[0], a[2] - a[1], a[3] - a[2], a[4] - a[3], a[5] - a[4], floor_raw, inv_dx0, ppj,
-                           pm_x);
-                pxp[(size_t)r * (nx + 1) + x] = ppj;
-            }
-            // y-interface of gap k (between tile rows k-1 and k) of column x, k = r;
-            // pyp slot k*nx + x receives p+ of tile row k-1 (row 0 of pyp is unused)
-            if (x < nx && in_rows && r <= rows_valid) {
-                const T* c = plane + (size_t)r * W + 3 + x;  // c[m W] = tile row r - 3 + m
-                T ppj;
-                weno_iface(c[W] - c[0], c[2 * W] - c[W], c[3 * W] - c[2 * W], c[4 * W] - c[3 * W],
-                           c[5 * W] - c[4 * W], floor_raw, inv_dx1, ppj, pm_y);
-                pyp[(size_t)r * nx + x] = ppj;
-            }
-            // without an extra thread row (NR == TY), row 0 also takes the tile's last gap
-            if (NR <= rows_valid && r == 0 && x < nx) {
-                const T* c = plane + (size_t)NR * W + 3 + x;
-                T ppj, unused;
-                weno_iface(c[W] - c[0], c[2 * W] - c[W], c[3 * W] - c[2 * W], c[4 * W] - c[3 * W],
-                           c[5 * W] - c[4 * W], floor_raw, inv_dx1, ppj, unused);
-                pyp[(size_t)NR * nx + x] = ppj;
-            }
-            __syncthreads();
+        cp_async_wait_all();
+        finish_ghosts(b0);
+        __syncthreads();
+    }
+
+    for (int z = zbeg; z < zend; ++z) {
+        const int fz = z * sS;
+        T* const bz = smem + ((z - zbeg) & 1) * buf_elems;        // plane z (and z+2)
+        T* const bn = smem + ((z - zbeg + 1) & 1) * buf_elems;    // plane z+1
+        T cosz = cos2, sinz = sin2;
+        if constexpr (D == 3 && uses_angle<D, DYN>()) {
+            cosz = trig[z];
+            sinz = trig[g.n[2] + z];
+        }
+        if (D >= 3 && node)
+            q[5] = z_inside ? ld(ucol + fz + 3 * sS) : line_value(ucol, z + 3, ns, (long long)sS, perS, extrap);
+
+        // phase A: interfaces of plane z along dimensions 0 and 1
+        T pmx = T(0), pmy = T(0);
+        // x-interface between nodes x-1 and x of row r (x = nx: the row's last one)
+        if (do_xrow) {
+            const T* a = bz + s_xrow;
+            T ppj;
+            weno_iface(a[1] - a[0], a[2] - a[1], a[3] - a[2], a[4] - a[3], a[5] - a[4], floor_raw, ppj, pmx);
+            bz[s_pxp] = ppj;
+        }
+        // y-interface of gap r (between tile rows r-1 and r) of column x
+        if (do_ygap) {
+            const T* c = bz + s_ycol;
+            T ppj;
+            weno_iface(c[W] - c[0], c[2 * W] - c[W], c[3 * W] - c[2 * W], c[4 * W] - c[3 * W], c[5 * W] - c[4 * W],
+                       floor_raw, ppj, pmy);
+            bz[s_pyp] = ppj;
+        }
+        if (do_ylast) {
+            const T* c = bz + s_ylast;
+            T ppj, unused;
+            weno_iface(c[W] - c[0], c[2 * W] - c[W], c[3 * W] - c[2 * W], c[4 * W] - c[3 * W], c[5 * W] - c[4 * W],
+                       floor_raw, ppj, unused);
+            bz[o_pyp + NR * nx + x] = ppj;
+        }
+        cp_async_wait_all();  // this thread's copies into plane z+1
+        if (z + 1 < zend) finish_ghosts(bn);
+        __syncthreads();
+
+        // phase B: staging of plane z+2, then the node update of plane z
+        if (z + 2 < zend) {
+            if (node) bz[s_center] = q[4];
+            stage_rest(z + 2, bz);
         }
         if (node) {
-            T pm[D], pp[D];
+            const T center = (D >= 3) ? q[2] : ld(ucol);
+            T pb[D], dd[D];
+            const T ppx = bz[s_pxp + 1];
+            const T ppy = bz[s_pyp + nx];
+            pb[0] = (pmx + ppx) * h0;
+            dd[0] = (ppx - pmx) * h0;
+            pb[1] = (pmy + ppy) * h1;
+            dd[1] = (ppy - pmy) * h1;
             T next = T(0);
             if constexpr (D >= 3) {
-                weno_iface(q[1] - q[0], q[2] - q[1], q[3] - q[2], q[4] - q[3], q[5] - q[4], floor_raw, inv_dxs,
-                           pp[SD], next);
-                pm[SD] = carry;
+                T pps;
+                weno_iface(q[1] - q[0], q[2] - q[1], q[3] - q[2], q[4] - q[3], q[5] - q[4], floor_raw, pps, next);
+                pb[SD] = (carry + pps) * hS;
+                dd[SD] = (pps - carry) * hS;
             }
-            if (!warm) {
-                pm[0] = pm_x;
-                pp[0] = pxp[(size_t)r * (nx + 1) + x + 1];
-                pm[1] = pm_y;
-                pp[1] = pyp[(size_t)(r + 1) * nx + x];
-                if constexpr (D == 4) {
-                    T v[7];
-                    gather7<T>(u, (long long)i2 * g.stride[2] + zoff + colbase, i2, g.n[2], g.stride[2],
-                               (g.periodic_mask >> 2) & 1u, extrap, v);
-                    weno5_pair<T>(v, SP<T>::dx(P, 2), floor_raw, pm[2], pp[2]);
-                }
-                int idx[4] = {x, y, 0, 0};
-                if (D == 3) idx[2] = z;
-                if (D == 4) { idx[2] = i2; idx[3] = z; }
-                T yd = lf_term_dyn<T, D, DYN>(P, idx, pm, pp);
-                if (brt0) yd = fmin(yd, T(0));
-                const long long flat = (uz - u) + colbase;
-                T res;
-                if (term_mode) {
-                    res = yd;
-                } else {
-                    const T w = center + dt * yd;
-                    res = w;
-                    if (has_vn) {
-                        const T vv = ld(vn + flat);
-                        if (use_cv) res = cv * vv + cu * w;
-                        if (minv) res = fmin(res, vv);
-                    }
-                }
-                out[flat] = res;
-                if (also_out) also_out[flat] = res;
+            if constexpr (D == 4) {
+                // dimension 2: both interfaces of the node from a 7-point line
+                T v[7];
+                gather7<T>(u, (long long)(col + fz), i2, g.n[2], g.stride[2], (g.periodic_mask >> 2) & 1u, extrap, v);
+                T pm2, pp2, unused0, unused1;
+                weno_iface(v[1] - v[0], v[2] - v[1], v[3] - v[2], v[4] - v[3], v[5] - v[4], floor_raw, unused0, pm2);
+                weno_iface(v[2] - v[1], v[3] - v[2], v[4] - v[3], v[5] - v[4], v[6] - v[5], floor_raw, pp2, unused1);
+                const T h2 = SP<T>::half_inv_dx(P, 2);
+                pb[2] = (pm2 + pp2) * h2;
+                dd[2] = (pp2 - pm2) * h2;
+                if constexpr (uses_coord<D, DYN>(3)) xc[3] = SP<T>::lo(P, 3) + T(z) * SP<T>::dx(P, 3);
             }
+            if constexpr (D == 3 && uses_coord<D, DYN>(2)) xc[2] = SP<T>::lo(P, 2) + T(z) * SP<T>::dx(P, 2);
+            T yd = lf_combine<T, D, DYN>(P, xc, cosz, sinz, pb, dd);
+            if (brt0) yd = fmin(yd, T(0));
+            const int flat = col + fz;
+            T res;
+            if constexpr (KIND == kKindTerm) {
+                res = yd;
+            } else if constexpr (KIND == kKindFirst) {
+                res = center + dt * yd;
+            } else {
+                const T vv = ld(vn + flat);
+                res = cv * vv + cu * (center + dt * yd);
+                if (minv) res = fmin(res, vv);
+            }
+            out[flat] = res;
+            if (also_out) also_out[flat] = res;
             if constexpr (D >= 3) {
                 carry = next;
 #pragma unroll
@@ -298,14 +377,14 @@ __device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T
     }
 }
 
-template <typename T, int D, int DYN>
+template <typename T, int D, int DYN, int KIND>
 __global__ void __launch_bounds__(RowsLimits<T>::kMaxThreads) rows_kernel(const StageParams P, const RowsCfg C) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const StageRun<T> R = stage_run<T>(P);
     const int i2 = (D == 4) ? (int)blockIdx.y : 0;
     const int chunk = (D == 3) ? (int)blockIdx.y : ((D == 4) ? (int)blockIdx.z : 0);
-    rows_tile<T, D, DYN>(P, R, C.ty, C.nr, C.tz, blockIdx.x, i2, chunk, threadIdx.x, threadIdx.y,
-                         reinterpret_cast<T*>(smem_raw));
+    rows_tile<T, D, DYN, KIND>(P, R, C.ty, C.nr, C.tz, blockIdx.x, i2, chunk, threadIdx.x, threadIdx.y,
+                               reinterpret_cast<T*>(smem_raw));
 }
 
 // Shared memory of a rows_kernel block.
@@ -323,11 +402,11 @@ inline void rows_shape(const StageParams& p, const RowsCfg& c, dim3& grid, dim3&
     smem = rows_smem_bytes<T>(p.g.n[0], c.ty);
 }
 
-template <typename T, int D, int DYN>
+template <typename T, int D, int DYN, int KIND>
 inline cudaError_t rows_prepare() {
     static bool done = false;  // benign race: setting the attribute twice is harmless
     if (!done) {
-        cudaError_t e = cudaFuncSetAttribute(rows_kernel<T, D, DYN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(rows_kernel<T, D, DYN, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              200 * 1024);
         if (e != cudaSuccess) return e;
         done = true;
@@ -335,28 +414,44 @@ inline cudaError_t rows_prepare() {
     return cudaSuccess;
 }
 
-template <typename T, int D, int DYN>
-cudaError_t launch_rows_dyn(const StageParams& p, const RowsCfg& c, cudaStream_t s) {
+template <typename T, int D, int DYN, int KIND>
+cudaError_t launch_rows_kind(const StageParams& p, const RowsCfg& c, cudaStream_t s) {
     dim3 grid, block;
     size_t smem;
     rows_shape<T, D, DYN>(p, c, grid, block, smem);
-    cudaError_t e = rows_prepare<T, D, DYN>();
+    cudaError_t e = rows_prepare<T, D, DYN, KIND>();
     if (e != cudaSuccess) return e;
-    rows_kernel<T, D, DYN><<<grid, block, smem, s>>>(p, c);
+    rows_kernel<T, D, DYN, KIND><<<grid, block, smem, s>>>(p, c);
     return cudaGetLastError();
 }
 
 template <typename T, int D, int DYN>
-int rows_bps_dyn(const StageParams& p, const RowsCfg& c) {
+cudaError_t launch_rows_dyn(const StageParams& p, const RowsCfg& c, cudaStream_t s) {
+    switch (stage_kind(p)) {
+    case kKindTerm: return launch_rows_kind<T, D, DYN, kKindTerm>(p, c, s);
+    case kKindFirst: return launch_rows_kind<T, D, DYN, kKindFirst>(p, c, s);
+    default: return launch_rows_kind<T, D, DYN, kKindCombine>(p, c, s);
+    }
+}
+
+template <typename T, int D, int DYN, int KIND>
+int rows_bps_kind(const StageParams& p, const RowsCfg& c) {
     dim3 grid, block;
     size_t smem;
     rows_shape<T, D, DYN>(p, c, grid, block, smem);
-    if (rows_prepare<T, D, DYN>() != cudaSuccess) return 0;
+    if (rows_prepare<T, D, DYN, KIND>() != cudaSuccess) return 0;
     int bps = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, rows_kernel<T, D, DYN>, (int)(block.x * block.y), smem) !=
-        cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, rows_kernel<T, D, DYN, KIND>, (int)(block.x * block.y),
+                                                      smem) != cudaSuccess)
         return 0;
     return bps;
+}
+
+// Resident blocks per SM of the stage kernels (the combining stages, the
+// largest of the three kinds).
+template <typename T, int D, int DYN>
+int rows_bps_dyn(const StageParams& p, const RowsCfg& c) {
+    return rows_bps_kind<T, D, DYN, kKindCombine>(p, c);
 }
 
 // Dispatch over the (dimension, dynamics) pairs the row kernel is built for.

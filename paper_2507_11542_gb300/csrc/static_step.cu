@@ -94,7 +94,7 @@ bool pick_rows(const StageParams& P, int dtype, int sm_count, RowsCfg* c) {
     if (!rows_supported(D, P.dynamics)) return false;
     for (int d = 0; d < D; ++d)
         if (G.n[d] < 4) return false;
-    const int max_threads = dtype == HJ_F64 ? 512 : 1024;
+    const int max_threads = rows_max_threads(dtype == HJ_F64);
     const int nx = G.n[0], ny = G.n[1];
     if (nx + 1 > max_threads) return false;
     int ty = 1;

@@ -201,6 +201,7 @@ template <> struct SP<double> {
     static __device__ __forceinline__ double lo(const StageParams& P, int d) { return P.g.lo[d]; }
     static __device__ __forceinline__ double dx(const StageParams& P, int d) { return P.g.dx[d]; }
     static __device__ __forceinline__ double inv_dx(const StageParams& P, int d) { return P.g.inv_dx[d]; }
+    static __device__ __forceinline__ double half_inv_dx(const StageParams& P, int d) { return P.half_inv_dx[d]; }
     static __device__ __forceinline__ double param(const StageParams& P, int k) { return P.params[k]; }
     static __device__ __forceinline__ double dt(const StageParams& P) { return P.dt; }
     static __device__ __forceinline__ double cv(const StageParams& P) { return P.cv; }
@@ -211,6 +212,7 @@ template <> struct SP<float> {
     static __device__ __forceinline__ float lo(const StageParams& P, int d) { return P.lo_f[d]; }
     static __device__ __forceinline__ float dx(const StageParams& P, int d) { return P.dx_f[d]; }
     static __device__ __forceinline__ float inv_dx(const StageParams& P, int d) { return P.inv_dx_f[d]; }
+    static __device__ __forceinline__ float half_inv_dx(const StageParams& P, int d) { return P.half_inv_dx_f[d]; }
     static __device__ __forceinline__ float param(const StageParams& P, int k) { return P.params_f[k]; }
     static __device__ __forceinline__ float dt(const StageParams& P) { return P.dt_f; }
     static __device__ __forceinline__ float cv(const StageParams& P) { return P.cv_f; }
@@ -226,32 +228,31 @@ template <typename T> struct Trig;
 template <> struct Trig<double> { static __device__ __forceinline__ const double* get(const StageParams& P) { return P.trig_d; } };
 template <> struct Trig<float>  { static __device__ __forceinline__ const float*  get(const StageParams& P) { return P.trig_f; } };
 
+// Whether a dynamics takes cos/sin of the dimension-2 coordinate (from the
+// angle table of the launch).
+template <int D, int DYN>
+__host__ __device__ constexpr bool uses_angle() {
+    return (DYN == HJ_DYN_AIR3D && D == 3) || (DYN == HJ_DYN_DUBINS4D && D == 4);
+}
+
+// ydot from node coordinates xc, cos/sin (c, s) of the dimension-2
+// coordinate (dynamics with uses_angle), the mean derivatives
+// pb = (p- + p+)/2 and the half differences dd = (p+ - p-)/2.
 template <typename T, int D, int DYN>
-__device__ __forceinline__ T lf_term_dyn(const StageParams& P, const int* idx, const T* pm, const T* pp) {
-    T pb[D], dd[D], x[D];
-#pragma unroll
-    for (int d = 0; d < D; ++d) {
-        pb[d] = T(0.5) * (pm[d] + pp[d]);
-        dd[d] = T(0.5) * (pp[d] - pm[d]);
-        x[d] = SP<T>::lo(P, d) + T(idx[d]) * SP<T>::dx(P, d);
-    }
+__device__ __forceinline__ T lf_combine(const StageParams& P, const T* xc, T c, T s, const T* pb, const T* dd) {
     const auto q = [&P](int k) { return SP<T>::param(P, k); };
     T y = T(0);
     if constexpr (DYN == HJ_DYN_DOUBLE_INTEGRATOR && D == 2) {
         const T umax = q(0);
-        y = pb[0] * x[1] - umax * fabs(pb[1]) + fabs(x[1]) * dd[0] + umax * dd[1];
+        y = pb[0] * xc[1] - umax * fabs(pb[1]) + fabs(xc[1]) * dd[0] + umax * dd[1];
     } else if constexpr (DYN == HJ_DYN_AIR3D && D == 3) {
-        const T* tr = Trig<T>::get(P);
-        const T c = tr[idx[2]], s = tr[P.g.n[2] + idx[2]];
         const T va = q(0), vb = q(1), amax = q(2), bmax = q(3);
         const T f0 = -va + vb * c, f1 = vb * s;
-        y = pb[0] * f0 + pb[1] * f1 + amax * fabs(pb[0] * x[1] - pb[1] * x[0] - pb[2]) - bmax * fabs(pb[2]);
-        y += (fabs(f0) + amax * fabs(x[1])) * dd[0] + (fabs(f1) + amax * fabs(x[0])) * dd[1] + (amax + bmax) * dd[2];
+        y = pb[0] * f0 + pb[1] * f1 + amax * fabs(pb[0] * xc[1] - pb[1] * xc[0] - pb[2]) - bmax * fabs(pb[2]);
+        y += (fabs(f0) + amax * fabs(xc[1])) * dd[0] + (fabs(f1) + amax * fabs(xc[0])) * dd[1] + (amax + bmax) * dd[2];
     } else if constexpr (DYN == HJ_DYN_DUBINS4D && D == 4) {
-        const T* tr = Trig<T>::get(P);
-        const T c = tr[idx[2]], s = tr[P.g.n[2] + idx[2]];
         const T wmax = q(0), accmax = q(1);
-        const T f0 = x[3] * c, f1 = x[3] * s;
+        const T f0 = xc[3] * c, f1 = xc[3] * s;
         y = pb[0] * f0 + pb[1] * f1 - wmax * fabs(pb[2]) - accmax * fabs(pb[3]);
         y += fabs(f0) * dd[0] + fabs(f1) * dd[1] + wmax * dd[2] + accmax * dd[3];
     } else if constexpr (DYN == HJ_DYN_NORM) {
@@ -265,10 +266,36 @@ __device__ __forceinline__ T lf_term_dyn(const StageParams& P, const int* idx, c
         for (int d = 0; d < D; ++d) { const T c = q(d); y += -c * pb[d] + fabs(c) * dd[d]; }
     } else if constexpr (DYN == HJ_DYN_ROTATE && D >= 2) {
         const T w = q(0);
-        const T f0 = -w * x[1], f1 = w * x[0];
+        const T f0 = -w * xc[1], f1 = w * xc[0];
         y = -(pb[0] * f0 + pb[1] * f1) + fabs(f0) * dd[0] + fabs(f1) * dd[1];
     }
     return y;
+}
+
+// Whether a dynamics reads the coordinate of dimension d (the others are not computed).
+template <int D, int DYN>
+__host__ __device__ constexpr bool uses_coord(int d) {
+    return (DYN == HJ_DYN_DOUBLE_INTEGRATOR && d == 1) || (DYN == HJ_DYN_AIR3D && d <= 1) ||
+           (DYN == HJ_DYN_DUBINS4D && d == 3) || (DYN == HJ_DYN_ROTATE && d <= 1);
+}
+
+// ydot at grid index idx from the one-sided derivatives (already divided by dx).
+template <typename T, int D, int DYN>
+__device__ __forceinline__ T lf_term_dyn(const StageParams& P, const int* idx, const T* pm, const T* pp) {
+    T pb[D], dd[D], x[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        pb[d] = T(0.5) * (pm[d] + pp[d]);
+        dd[d] = T(0.5) * (pp[d] - pm[d]);
+        x[d] = SP<T>::lo(P, d) + T(idx[d]) * SP<T>::dx(P, d);
+    }
+    T c = T(0), s = T(0);
+    if constexpr (uses_angle<D, DYN>()) {
+        const T* tr = Trig<T>::get(P);
+        c = tr[idx[2]];
+        s = tr[P.g.n[2] + idx[2]];
+    }
+    return lf_combine<T, D, DYN>(P, x, c, s, pb, dd);
 }
 
 template <typename T, int D>

@@ -20,7 +20,8 @@
 // with the third differences T1 = e1-3e2+3e3-e4 = tA-tB and T2 = e2-3e3+3e4-e5
 // = tB-tC shared by both sides, and the smoothness indicators scaled by 12/13
 // (S~ = t^2 + 3/13 u^2, eps scaled alike), which leaves every weight unchanged.
-// All differences are raw (not divided by dx); the results are divided by dx.
+// All differences and both results are raw (not divided by dx): the caller
+// scales them once per node and dimension.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -36,7 +37,7 @@ __device__ __forceinline__ float rcp_approx(float x) {
 // FP32. (S~ + eps~)^2 >= (12/13 * 1e-18)^2 stays a normal number, so the
 // approximate reciprocals neither overflow nor divide by zero.
 __device__ __forceinline__ void weno_iface(float e1, float e2, float e3, float e4, float e5, float floor_raw,
-                                           float inv_dx, float& pp_j, float& pm_j1) {
+                                           float& pp_j, float& pm_j1) {
     const float k = 3.0f / 13.0f;
     const float tA = fmaf(-2.0f, e2, e1) + e3;
     const float tB = fmaf(-2.0f, e3, e2) + e4;
@@ -63,8 +64,8 @@ __device__ __forceinline__ void weno_iface(float e1, float e2, float e3, float e
     const float c5 = (5.0f / 6.0f) * e3;
     const float phi2 = fmaf(1.0f / 3.0f, e4, fmaf(-1.0f / 6.0f, e2, c5));
     const float psi2 = fmaf(1.0f / 3.0f, e2, fmaf(-1.0f / 6.0f, e4, c5));
-    pm_j1 = fmaf(numL, rcp_approx(denL), phi2) * inv_dx;
-    pp_j = fmaf(-numR, rcp_approx(denR), psi2) * inv_dx;
+    pm_j1 = fmaf(numL, rcp_approx(denL), phi2);
+    pp_j = fmaf(-numR, rcp_approx(denR), psi2);
 }
 
 // Integer maximum of non-negative doubles (their bit patterns order alike):
@@ -95,7 +96,7 @@ __device__ __forceinline__ double rcp_newton(double x) {
 // leaves [1e-290, 1e290] (nearly flat or huge data) each side divides alone,
 // and an exactly flat window (den = 0) returns its central candidate.
 __device__ __forceinline__ void weno_iface(double e1, double e2, double e3, double e4, double e5, double floor_raw,
-                                           double inv_dx, double& pp_j, double& pm_j1) {
+                                           double& pp_j, double& pm_j1) {
     const double k = 3.0 / 13.0;
     const double tA = fma(-2.0, e2, e1) + e3;
     const double tB = fma(-2.0, e3, e2) + e4;
@@ -127,11 +128,11 @@ __device__ __forceinline__ void weno_iface(double e1, double e2, double e3, doub
     const int expo = (int)((bits >> 52) & 0x7ff);  // 1e-290 < den2 < 1e290 (integer test)
     if (expo > 60 && expo < 1986) {
         const double r = rcp_newton(den2);
-        pm_j1 = fma(numL * denR, r, phi2) * inv_dx;
-        pp_j = fma(-numR * denL, r, psi2) * inv_dx;
+        pm_j1 = fma(numL * denR, r, phi2);
+        pp_j = fma(-numR * denL, r, psi2);
     } else {
-        pm_j1 = (denL > 0.0 ? phi2 + numL / denL : phi2) * inv_dx;
-        pp_j = (denR > 0.0 ? psi2 - numR / denR : psi2) * inv_dx;
+        pm_j1 = denL > 0.0 ? phi2 + numL / denL : phi2;
+        pp_j = denR > 0.0 ? psi2 - numR / denR : psi2;
     }
 }
 
