@@ -11,6 +11,10 @@ whole grid; the metric is cell-updates/s (one node advanced one RK3 step).
   fp64   : the same in FP64
   e2e    : hj_solve through the C ABI with pinned host buffers: V0 uploaded,
            the first time slice (tau = 0.28) integrated, V downloaded, per step
+  batched / served : the 64-instance mix in one batched solve; Poisson-arriving
+           requests through the server
+  large_grids : the expanding sphere on 512^3 (FP32) and the Dubins car on
+           81^4 (FP32, FP64), device-resident steps, with their HBM fraction
   cpu_baseline / --impl reference : the FP64 CPU oracle on the host cores
 
 Run: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
@@ -210,10 +214,11 @@ def run_steps(ctx, spec, m, V, bufs, dt, K, flush, events):
     return step_ms, stage_ms
 
 
-def bench_dtype(ctx, spec, V0, dtype, K, W_, world, flush):
+def bench_dtype(ctx, spec, V0, dtype, K, W_, world, flush, m=None):
     import torch
     from paper_2507_11542_gb300 import solver
-    m = solver.method(dynamics=2, params=(5.0, 5.0, 1.0, 1.0), brt=1)
+    if m is None:
+        m = solver.method(dynamics=2, params=(5.0, 5.0, 1.0, 1.0), brt=1)
     sbi = solver.step_bound(ctx, spec, m)
     dt = 0.8 / sbi
     tdt = getattr(torch, dtype)
@@ -256,6 +261,26 @@ def bench_e2e(ctx, spec, V0, dtype, K, W_, world):
             "h2d_bytes_per_step": int(v0.numel() * v0.element_size()),
             "d2h_bytes_per_step": int(out.numel() * out.element_size()),
             "rk3_steps_per_step": steps // K, "launches": launches}
+
+
+def bench_large(ctx, world, flush):
+    """The grids far larger than L2: the expanding sphere on 512^3 (FP32) and
+    the Dubins car on 81^4 (FP32 and FP64), device-resident RK3 steps. Their
+    HBM fraction counts the algorithmic 8 words per cell-update."""
+    from paper_2507_11542_gb300 import solver, workloads as W
+    hbm, _ = measured_hbm_gbs()
+    out = {}
+    cases = [("sphere512_f32", W.expanding_sphere(512), solver.method(dynamics=4, params=(1.0,), brt=0), "float32", 10),
+             ("dubins81_f32", W.dubins4d(81), solver.method(dynamics=3, params=(1.0, 0.5), brt=1), "float32", 6),
+             ("dubins81_f64", W.dubins4d(81), solver.method(dynamics=3, params=(1.0, 0.5), brt=1), "float64", 3)]
+    for name, (spec, V0), m, dtype, K in cases:
+        n = int(np.prod(spec.n))
+        r = bench_dtype(ctx, spec, V0, dtype, K, 3, world, flush, m=m)
+        rate = world * n / (r["ms_per_step"] / 1e3)
+        gbs = 8 * (4 if dtype == "float32" else 8) * n / (r["ms_per_step"] / 1e3) / 1e9
+        out[name] = {"value": rate, "unit": "cell-updates/s", "ms_per_step": r["ms_per_step"], "steps": K,
+                     "cells": n, "hbm_achieved_gbs": gbs, "hbm_frac": gbs / hbm}
+    return out
 
 
 def _mix_problems(mix, dtype):
@@ -417,7 +442,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-steps", type=int, default=24, help="oracle steps for the cpu_baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--legs", default="f32,f64,e2e,batch,serve",
+    ap.add_argument("--legs", default="f32,f64,e2e,batch,serve,large",
                     help="comma list of legs to run; f32 always runs, and a run without all of them "
                          "(a profiling run: --legs f32 or f32,f64) prints timings instead of the JSON line")
     ap.add_argument("--serve-requests", type=int, default=100)
@@ -436,7 +461,7 @@ def main():
     ctx = solver.Context(local)
     K, W_ = args.steps, max(args.warmup, 3)
     legs = set(args.legs.split(","))
-    full = {"f64", "e2e", "batch", "serve"} <= legs
+    full = {"f64", "e2e", "batch", "serve", "large"} <= legs
     with ClockSampler(local) as clk:
         r32 = bench_dtype(ctx, spec, V0, "float32", K, W_, world, flush)
         r64 = bench_dtype(ctx, spec, V0, "float64", max(3, K // 4), 3, world, flush) if "f64" in legs else None
@@ -450,6 +475,7 @@ def main():
         e2e = bench_e2e(ctx, spec, V0, "float32", max(3, K // 4), 2, world)
         batch = bench_batch(ctx, rank=rank, world=world)
         serve = bench_serve(ctx, args.serve_requests) if world == 1 else None
+        large = bench_large(ctx, world, flush)
     value = world * K * N_CELLS / (r32["total_ms"] / 1e3)
     hbm, hbm_kind = measured_hbm_gbs()
     launch_s = r32["launch_ms_mean"] / 1e3
@@ -486,6 +512,7 @@ def main():
         line["batched"] = batch
     if serve:
         line["served"] = serve
+    line["large_grids"] = large
     if rank == 0 and not args.no_cpu_baseline:
         rate, el = cpu_oracle_rate(spec, V0, args.cpu_steps)
         line["cpu_baseline"] = {"value": rate, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",

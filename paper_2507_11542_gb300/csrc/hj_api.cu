@@ -352,13 +352,13 @@ std::vector<RowsCfg> rows_candidates(hj_ctx* ctx, const StageParams& P, int dtyp
     std::sort(scored.begin(), scored.end(),
               [](const std::pair<double, RowsCfg>& a, const std::pair<double, RowsCfg>& b) { return a.first < b.first; });
     std::vector<RowsCfg> out;
-    for (size_t k = 0; k < scored.size() && k < 10; ++k) out.push_back(scored[k].second);
+    for (size_t k = 0; k < scored.size() && k < 16; ++k) out.push_back(scored[k].second);
     return out;
 }
 
 // The launch shape for this grid: measured once per (shape, dtype, dynamics)
-// over the model's best candidates (a first-stage launch writing to a
-// scratch buffer, best of three), then cached in the context. HJ_TUNE=0 keeps the model's
+// over the model's best candidates (groups of first-stage launches writing
+// to a scratch buffer, best of two groups), then cached in the context. HJ_TUNE=0 keeps the model's
 // first choice without timing.
 hj_status rows_config(hj_ctx* ctx, const StageParams& P, int dtype, RowsCfg* out) {
     const GridDev& G = P.g;
@@ -397,13 +397,16 @@ hj_status rows_config(hj_ctx* ctx, const StageParams& P, int dtype, RowsCfg* out
         cudaEvent_t e0, e1;
         HJ_CUDA(ctx, cudaEventCreate(&e0));
         HJ_CUDA(ctx, cudaEventCreate(&e1));
+        // Launches of a few tens of microseconds are timed in groups: the
+        // event clock advances in steps of about two microseconds.
+        const int group = G.total < (4LL << 20) ? 6 : 2;
         float best_ms = 1e30f;
         for (const RowsCfg& c : cands) {
             cudaError_t e = rows_launch(ctx, T, c, dtype);  // warm-up
             float ms_min = 1e30f;
-            for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+            for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
                 cudaEventRecord(e0, ctx->stream);
-                e = rows_launch(ctx, T, c, dtype);
+                for (int k = 0; k < group && e == cudaSuccess; ++k) e = rows_launch(ctx, T, c, dtype);
                 cudaEventRecord(e1, ctx->stream);
                 if (e == cudaSuccess) e = cudaEventSynchronize(e1);
                 float ms = 0.f;

@@ -205,11 +205,23 @@ __device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T
     // the ghost rule) and, from the spare thread, the row's x-ghost sources
     // (periodic: the wrapped nodes into the ghost cells; extrapolated: the
     // two outermost nodes at each end into the row-end slots).
+    // this thread's first halo row (the same in every plane): destination and source row
+    const bool h0_on = halo_thread && r < n_extra;
+    const int h0_rr = (r < 3) ? r - 3 : rows_valid + (r - 3);
+    const int h0_dst = (h0_rr + 3) * W + 3 + x;
+    int h0_yy = y0 + h0_rr;
+    if (per1 && (h0_yy < 0 || h0_yy >= ny)) h0_yy = (h0_yy % ny + ny) % ny;
+    const bool h0_in = h0_yy >= 0 && h0_yy < ny;
+    const int h0_src = plane0 + x + (h0_in ? h0_yy * nx : 0);
     auto stage_rest = [&](int p, T* b) {
         const int fp = p * sS;
+        if (h0_on) {
+            if (h0_in) cp_async_elem(b + h0_dst, u + h0_src + fp);
+            else b[h0_dst] = line_value(u + plane0 + fp + x, h0_yy, ny, (long long)nx, false, extrap);
+        }
         if (halo_thread) {
             const T* base = u + plane0 + fp + x;
-            for (int h = r; h < n_extra; h += NR) {
+            for (int h = r + NR; h < n_extra; h += NR) {  // further halo rows (small blocks, ragged tiles)
                 const int rr = (h < 3) ? h - 3 : rows_valid + (h - 3);
                 int yy = y0 + rr;
                 T* dst = b + (rr + 3) * W + 3 + x;
