@@ -46,6 +46,12 @@ E2E_TAU = 0.28
 # stage input and V^n and write one array: 3 words).
 FLOPS_PER_NODE_STAGE = 475
 WORDS_PER_NODE_STEP = 8
+# DRAM bytes (read + write) of one stage-2 launch of the FP32 row kernel on this
+# workload, from the ncu capture summarised in profiles/rows_kernel_f32_air3d101.md
+# (the 4.1 MB arrays stay in L2, so DRAM traffic is below the algorithmic bytes);
+# executed flops per node from that capture's instruction counts (interfaces shared).
+NCU_TRAFFIC_BYTES_F32 = 8.29e6
+NCU_EXECUTED_FLOPS_PER_NODE_F32 = 330
 # GB300 unit counts: 152 SMs, 128 FP32 lanes and 2 FP64 lanes per SM, FMA = 2 flops, max SM clock 2070 MHz
 SM_COUNT, SM_MAX_MHZ = 152, 2070.0
 FP32_PEAK_TFLOPS = SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
@@ -492,7 +498,11 @@ def main():
                    "l2": "flushed (256 MiB write) before every timed step",
                    "time": "FP64 t, dt and CFL bound", "parallelism": "replicas" if world > 1 else "single"},
         "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved_tflops / FP32_PEAK_TFLOPS, "traffic": None,
+                     "frac": achieved_tflops / FP32_PEAK_TFLOPS, "traffic": NCU_TRAFFIC_BYTES_F32,
+                     "flops_per_node": FLOPS_PER_NODE_STAGE,
+                     "flops_note": "two-sided WENO5 per dimension as the method states it; the kernel shares each "
+                                   "interface between its two nodes and executes about %d"
+                                   % NCU_EXECUTED_FLOPS_PER_NODE_F32,
                      "kernel": "rows_kernel<float,3,AIR3D> (fused WENO5 stage)",
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (unit counts x max clock)",
                      "hbm_achieved_gbs": achieved_gbs, "hbm_peak_gbs": hbm, "hbm_peak_source": hbm_kind,
