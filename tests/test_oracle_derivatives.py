@@ -92,15 +92,23 @@ def test_weno5_non_oscillatory_across_jump():
     assert np.all(np.abs(pm) <= 1.0 / dx + 1e-9)
 
 
+def _golden(name):
+    import os
+    vals = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                key, rest = line.split(":", 1)
+                vals[key.strip()] = [float(t) for t in rest.split()]
+    return vals
+
+
 def test_eno2_tie_picks_left_candidate():
-    # Reading R2 worked by hand: v_{i-2} = v_{i-1} = 0, v_i = v_{i+1} = 1, dx = 1.
-    # Left stencil k = i-1: D1_{k-1/2} = 0, D1_{k+1/2} = 1, D1_{k+3/2} = 0 so
-    # D2_k = 0.5 and D2_{k+1} = -0.5 tie in magnitude; the left candidate gives
-    # p- = D1_{k+1/2} + D2_k * dx = 1.5 (the right one would give 0.5).
-    padded = np.array([0, 0, 0, 0, 0, 1, 1, 1, 1, 1], dtype=float)  # nodes -3..6
-    pm, _ = O.upwind_line(padded, 1.0, O.ENO2)
-    i = 2  # node 2: v0=0, v1=0, v2=1, v3=1
-    assert pm[i] == 1.5
+    # Reading R2, worked by hand in tests/golden/eno2_tie.txt
+    g = _golden("eno2_tie.txt")
+    pm, _ = O.upwind_line(np.array(g["padded"]), g["dx"][0], O.ENO2)
+    assert pm[int(g["node"][0])] == g["pminus"][0]
 
 
 def test_periodic_padding_matches_wrap():
@@ -112,16 +120,14 @@ def test_periodic_padding_matches_wrap():
 
 
 def test_extrapolation_worked_examples():
-    # Reading R3 by hand: slope |v0 - v1| * sign(v0), continued outward.
-    out = O.pad_line(np.array([2.0, 3.0, 5.0]), periodic=False)
-    np.testing.assert_array_equal(out[:3], [5.0, 4.0, 3.0])        # nodes -3, -2, -1
-    np.testing.assert_array_equal(out[-3:], [7.0, 9.0, 11.0])     # nodes 3, 4, 5
-    out = O.pad_line(np.array([-2.0, -3.0, -1.0]), periodic=False)
-    np.testing.assert_array_equal(out[:3], [-5.0, -4.0, -3.0])
-    np.testing.assert_array_equal(out[-3:], [-3.0, -5.0, -7.0])
-    # the plain linear variant keeps the signed slope
-    out = O.pad_line(np.array([2.0, 3.0, 5.0]), periodic=False, extrap=O.EXTRAP_LINEAR)
-    np.testing.assert_array_equal(out[:3], [-1.0, 0.0, 1.0])
+    # Reading R3, worked by hand in tests/golden/ghost_extrapolation.txt
+    g = _golden("ghost_extrapolation.txt")
+    for k in ("a", "b"):
+        out = O.pad_line(np.array(g["line_" + k]), periodic=False)
+        np.testing.assert_array_equal(out[:3], g["away_low_" + k])    # nodes -3, -2, -1
+        np.testing.assert_array_equal(out[-3:], g["away_high_" + k])  # nodes n, n+1, n+2
+    out = O.pad_line(np.array(g["line_a"]), periodic=False, extrap=O.EXTRAP_LINEAR)
+    np.testing.assert_array_equal(out[:3], g["linear_low_a"])
 
 
 def test_extrapolation_never_crosses_zero():
