@@ -22,9 +22,6 @@ __global__ void __launch_bounds__(RowsLimits<T>::kMaxThreads)
     const BatchTile t = tiles[blockIdx.x];
     const BatchInst& I = insts[t.inst];
     if (I.k >= I.steps_total) return;  // this instance has finished (block-uniform)
-    const int nx = I.P.g.n[0];
-    const int x = (int)threadIdx.x % (nx + 1);
-    const int r = (int)threadIdx.x / (nx + 1);
     StageRun<T> R;
     R.dt = batch_dt<T>(I);
     R.brt0 = I.brt == HJ_BRT_MIN0;
@@ -51,8 +48,7 @@ __global__ void __launch_bounds__(RowsLimits<T>::kMaxThreads)
         R.cu = T(2.0 / 3.0);
         R.minv = I.brt == HJ_BRT_MINV;
     }
-    const int nr = (int)blockDim.x / (nx + 1);
-    rows_tile<T, D, DYN, KIND>(I.P, R, I.ty, nr, I.tz, t.row_tile, t.i2, t.chunk, x, r,
+    rows_tile<T, D, DYN, KIND>(I.P, R, I.ty, (int)blockDim.x, I.tz, t.row_tile, t.i2, t.chunk, (int)threadIdx.x,
                                reinterpret_cast<T*>(smem_raw));
 }
 

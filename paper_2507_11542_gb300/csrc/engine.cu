@@ -327,8 +327,9 @@ hj_status Engine::activate(std::vector<int>* failed) {
 namespace {
 void tile_shape(const Slot& S, int threads, int tz_target, int* ty, int* tz) {
     const int nx = S.G.n[0], ny = S.G.n[1];
-    const int nr = std::max(1, threads / (nx + 1));  // thread rows of the block
-    int t = std::min(nr >= 2 ? nr - 1 : 1, ny);       // node rows: one thread row left for the last interfaces
+    // node rows: the most whose block (rows_block_threads) fits `threads`
+    int t = 1;
+    while (t < ny && rows_block_threads(nx, t + 1, threads) <= threads) ++t;
     while (t > 1 && rows_smem(nx, t, S.es) > 200 * 1024) --t;
     *ty = t;
     const int D = S.G.ndim;

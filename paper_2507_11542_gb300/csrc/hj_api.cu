@@ -293,7 +293,8 @@ bool rows_eligible(const GridDev& G, int scheme, int dynamics, int dtype) {
 RowsCfg make_rows_cfg(const GridDev& G, int ty, int tz, int dtype) {
     RowsCfg c;
     c.ty = ty;
-    c.nr = rows_thread_rows(G.n[0], ty, rows_max_threads(dtype == HJ_F64));
+    c.nt = rows_block_threads(G.n[0], ty, rows_max_threads(dtype == HJ_F64));
+    c.occ = 1;
     c.row_tiles = (G.n[1] + ty - 1) / ty;
     const int ns = G.ndim >= 3 ? G.n[G.ndim - 1] : 1;
     c.tz = G.ndim >= 3 ? tz : 1;
@@ -320,7 +321,7 @@ std::vector<RowsCfg> rows_candidates(hj_ctx* ctx, const StageParams& P, int dtyp
     const int D = G.ndim;
     const int ns = D >= 3 ? G.n[D - 1] : 1;
     const size_t es = dtype == HJ_F64 ? 8 : 4;
-    static const int tys[] = {1, 2, 3, 4, 5, 6, 8, 10, 12, 16, 24, 32};
+    static const int tys[] = {1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 12, 16, 24, 32};
     static const int tzs[] = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64, 128, 256};
     std::vector<std::pair<double, RowsCfg>> scored;
     for (int ty : tys) {
@@ -334,15 +335,20 @@ std::vector<RowsCfg> rows_candidates(hj_ctx* ctx, const StageParams& P, int dtyp
         } else {
             zs.push_back(1);
         }
-        for (int tz : zs) {
+        for (int k = 0; k < 2 * (int)zs.size(); ++k) {
+            const int tz = zs[k / 2];
             RowsCfg c = make_rows_cfg(G, ty, tz, dtype);
+            if (k % 2 == 1) {  // the FP32 variant for two blocks per SM
+                if (dtype == HJ_F64 || c.nt > kRowsOcc2Threads) continue;
+                c.occ = 2;
+            }
             if (c.nchunks > 65535 || c.row_tiles > (1 << 30)) continue;
             const int bps = rows_bps(P, c, dtype);
             if (bps <= 0) continue;
             const double blocks = (double)c.row_tiles * c.nchunks * (D == 4 ? G.n[2] : 1);
             const double slots = (double)ctx->sm_count * bps;
             const double waves = std::ceil(blocks / slots);
-            const double warps = std::ceil((double)(nx + 1) * c.nr / 32.0);
+            const double warps = std::ceil((double)c.nt / 32.0);
             const double rows_valid = std::min(ty, ny);
             const double plane = warps * (1.0 + 0.1 * (6.0 + ty - rows_valid) / ty);
             const double planes = D >= 3 ? (double)std::min(tz, ns) + 1.0 : 1.0;
@@ -358,17 +364,20 @@ std::vector<RowsCfg> rows_candidates(hj_ctx* ctx, const StageParams& P, int dtyp
 
 // The launch shape for this grid: measured once per (shape, dtype, dynamics)
 // over the model's best candidates (groups of first-stage launches writing
-// to a scratch buffer, best of two groups), then cached in the context. HJ_TUNE=0 keeps the model's
-// first choice without timing.
+// to a scratch buffer, best of two groups), then cached in the context.
+// HJ_TUNE=0 keeps the model's first choice without timing.
 hj_status rows_config(hj_ctx* ctx, const StageParams& P, int dtype, RowsCfg* out) {
     const GridDev& G = P.g;
-    // HJ_ROWS_CFG="ty,tz" pins the shape (used to check that results do not depend on it)
+    // HJ_ROWS_CFG="ty,tz" or "ty,tz,occ" pins the shape (used to check that results do not depend on it)
     if (const char* pin = std::getenv("HJ_ROWS_CFG")) {
-        int ty = 0, tz = 0;
-        if (std::sscanf(pin, "%d,%d", &ty, &tz) == 2 && ty >= 1 && tz >= 1 && ty <= G.n[1] &&
+        int ty = 0, tz = 0, occ = 1;
+        const int got = std::sscanf(pin, "%d,%d,%d", &ty, &tz, &occ);
+        if (got >= 2 && ty >= 1 && tz >= 1 && ty <= G.n[1] && (occ == 1 || occ == 2) &&
             (G.n[0] + 1) * ty <= rows_max_threads(dtype == HJ_F64)) {
             *out = make_rows_cfg(G, ty, tz, dtype);
-            if (out->nchunks <= 65535 && rows_bps(P, *out, dtype) > 0) return HJ_OK;
+            out->occ = occ;
+            if (occ == 2 && (dtype == HJ_F64 || out->nt > kRowsOcc2Threads)) out->occ = 0;
+            if (out->occ && out->nchunks <= 65535 && rows_bps(P, *out, dtype) > 0) return HJ_OK;
         }
         return fail(ctx, HJ_EINVAL, "HJ_ROWS_CFG=%s does not fit this grid", pin);
     }

@@ -15,6 +15,9 @@ constexpr int kMaxDim = 4;
 constexpr int kRowsMaxThreadsF32 = 1024;
 constexpr int kRowsMaxThreadsF64 = 512;
 inline int rows_max_threads(int dtype_is_f64) { return dtype_is_f64 ? kRowsMaxThreadsF64 : kRowsMaxThreadsF32; }
+// The FP32 row kernel also exists compiled for two resident blocks per SM
+// (<= 56 registers a thread) of at most this many threads.
+constexpr int kRowsOcc2Threads = 544;
 
 // Grid as the kernels see it. Spacing and its inverse are computed once on
 // the host from the hj_grid (periodic: (hi-lo)/n, else (hi-lo)/(n-1)).
@@ -96,18 +99,21 @@ struct UpwindParams {
 
 // Launch configuration of the row-tiled WENO5 stage kernel (rows_kernel.cuh).
 struct RowsCfg {
-    int ty;         // node rows per tile; blockDim.x = n0 + 1
-    int nr;         // thread rows (blockDim.y): ty + 1 where it fits, else ty
+    int ty;         // node rows per tile
+    int nt;         // threads per block (1-D): rows_block_threads(n0, ty, ...)
     int tz;         // planes per chunk along the streamed (last) dimension
     int nchunks;    // chunks along the streamed dimension
     int row_tiles;  // ceil(n1 / ty)
+    int occ;        // 1, or 2: FP32 kernel compiled for two resident blocks of <= kRowsOcc2Threads threads per SM
 };
 
-// Thread rows of a row-kernel block with ty node rows: one more than ty
-// (the extra row evaluates the tile's last dimension-1 interfaces) where the
-// block size allows it, else ty (then thread row 0 evaluates those as well).
-inline int rows_thread_rows(int nx, int ty, int max_threads) {
-    return (nx + 1) * (ty + 1) <= max_threads ? ty + 1 : ty;
+// Threads of a row-kernel block with ty node rows of n0 nodes: one thread per
+// node, one per row for the row's last dimension-0 interface and ghost cells,
+// and, where the block size allows it, one per column for the tile's last
+// dimension-1 interface (without them thread row 0 evaluates those).
+inline bool rows_gap_threads(int nx, int ty, int threads) { return nx * ty + ty + nx <= threads; }
+inline int rows_block_threads(int nx, int ty, int max_threads) {
+    return nx * ty + ty + (rows_gap_threads(nx, ty, max_threads) ? nx : 0);
 }
 
 // Elements of one of the two alternating shared buffers of a rows_kernel

@@ -23,6 +23,8 @@
 // 6.1) and the TVD-RK3 stage combination (Sec. 5), one store per node.
 #pragma once
 
+#include <type_traits>
+
 #include "stencil.cuh"
 #include "weno_iface.cuh"
 
@@ -31,6 +33,10 @@ namespace hj {
 template <typename T> struct RowsLimits;
 template <> struct RowsLimits<float> { static constexpr int kMaxThreads = kRowsMaxThreadsF32; };
 template <> struct RowsLimits<double> { static constexpr int kMaxThreads = kRowsMaxThreadsF64; };
+// Launch bounds of a row-kernel variant: OCC resident blocks per SM.
+template <typename T, int OCC> struct RowsBounds {
+    static constexpr int kThreads = OCC == 2 ? kRowsOcc2Threads : RowsLimits<T>::kMaxThreads;
+};
 
 template <typename T>
 __device__ __forceinline__ T ghost_value(T edge, T inner, int m, int extrap) {
@@ -98,22 +104,27 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 // One tile: rows y0 = row_tile*TY .. +TY-1 of the plane(s) at dimension-2 index
 // i2 (4-D) and the planes of chunk `chunk` along the streamed dimension
-// (planes chunk*tz .. +tz-1). The block has NR thread rows; (x, r) is this
-// thread's position, x in 0..n0, r in 0..NR-1 (threads with r >= NR only
-// take part in the barriers).
+// (planes chunk*tz .. +tz-1), computed by the NT threads of a 1-D block.
+// Thread t has one role, so that roles change only between whole warps
+// (except one warp at each boundary):
+//   t <  n0*TY          node (x, r) = (t mod n0, t div n0);
+//   t <  n0*TY + TY     row end of row r = t - n0*TY (x = n0);
+//   t <  n0*TY+TY+n0    gap thread of column x (present when the block has
+//                       room: NT >= n0*TY + TY + n0);
+//   others              barriers only.
 //
 // Interfaces along dimensions 0 and 1 are each evaluated once per plane and
 // shared through shared memory:
-//   x-interfaces: n0+1 per node row (row r by thread row r),
-//   y-interfaces: TY+1 per column (gap k, between tile rows k-1 and k, by
-//                 thread row k; without an extra thread row, thread row 0
-//                 also takes the last gap),
-// so with NR = TY+1 every thread evaluates at most one of each. The p- half
-// of the interface a thread evaluates for its own row or gap belongs to its
-// own node and stays in a register; the p+ half belongs to the neighbour
-// (x-1 or row k-1) and goes through shared memory. Derivatives stay raw
-// (undivided differences) until the node combines them, scaled by 1/(2 dx),
-// into the means and half differences the Hamiltonian takes.
+//   x-interfaces: node (x, r) takes the one between nodes x-1 and x, the row
+//                 end the row's last one;
+//   y-interfaces: node (x, r) takes gap r (between tile rows r-1 and r), the
+//                 gap thread of column x the tile's last gap (without gap
+//                 threads: an idle node row of a ragged tile, else row 0).
+// The p- half of the interface a thread evaluates for its own node stays in a
+// register; the p+ half belongs to the neighbour (x-1 or row r-1) and goes
+// through shared memory. Derivatives stay raw (undivided differences) until
+// the node combines them, scaled by 1/(2 dx), into the means and half
+// differences the Hamiltonian takes.
 //
 // Planes are software-pipelined through two shared buffers (plane p in
 // buffer p mod 2) with one barrier per plane:
@@ -125,9 +136,9 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 //               asynchronously), two planes ahead of its use.
 // Flat indices are 32-bit (the grid has fewer than 2^31 nodes).
 template <typename T, int D, int DYN, int KIND>
-__device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T>& R, const int TY, const int NR,
+__device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T>& R, const int TY, const int NT,
                                           const int tz, const int row_tile, const int i2_in, const int chunk_in,
-                                          const int x, const int r, T* const smem) {
+                                          const int t, T* const smem) {
     const GridDev& g = P.g;
     const int nx = g.n[0], ny = g.n[1];
     const int W = nx + 6;  // shared row: 3 ghost cells, nx nodes, 3 ghost cells
@@ -146,15 +157,35 @@ __device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T
     const int extrap = g.extrap;
 
     const int y0 = row_tile * TY;
-    const int y = y0 + r;
     const int rows_valid = min(TY, ny - y0);
-    const bool in_rows = r < NR;
-    const bool node = (x < nx) && (r < rows_valid);
-    const bool do_xrow = in_rows && r < rows_valid;
-    const bool do_ygap = in_rows && x < nx && r <= rows_valid;
-    const bool do_ylast = NR <= rows_valid && r == 0 && x < nx;
-    const bool spare = in_rows && x == nx && r < rows_valid;  // the spare thread of node row r
-    const bool halo_thread = in_rows && x < nx;
+    // roles
+    const int n_node = nx * TY;
+    const int n_end = n_node + TY;
+    const bool gaps = nx * TY + TY + nx <= NT;
+    const bool is_node = t < n_node;
+    const bool is_end = t >= n_node && t < n_end;
+    const bool is_gap = gaps && t >= n_end && t < n_end + nx;
+    int x, r;
+    if (is_node) {
+        r = t / nx;
+        x = t - r * nx;
+    } else if (is_end) {
+        r = t - n_node;
+        x = nx;
+    } else {
+        r = TY;
+        x = is_gap ? t - n_end : nx;
+    }
+    const int y = y0 + r;
+    const bool node = is_node && r < rows_valid;
+    const bool do_xrow = (is_node || is_end) && r < rows_valid;
+    // this thread's gap (tile row boundary) along dimension 1, or -1
+    int gk = -1;
+    if (is_node && r < rows_valid) gk = r;
+    else if (is_gap) gk = rows_valid;
+    else if (!gaps && is_node && r == rows_valid) gk = rows_valid;  // an idle row of a ragged tile
+    const bool do_ylast = !gaps && rows_valid == TY && is_node && r == 0;  // full tile, no gap threads
+    const bool spare = is_end && r < rows_valid;  // the row end of node row r
 
     const int i2 = (D == 4) ? i2_in : 0;
     const int chunk = (D >= 3) ? chunk_in : 0;
@@ -173,10 +204,11 @@ __device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T
     // shared-memory offsets within a buffer
     const int s_center = (r + 3) * W + 3 + x;
     const int s_xrow = (r + 3) * W + x;        // value at node x - 3 of row r
-    const int s_ycol = r * W + 3 + x;          // value at tile row r - 3 of column x
-    const int s_ylast = NR * W + 3 + x;
+    const int s_ycol = gk * W + 3 + x;         // value at tile row gk - 3 of column x
+    const int s_ylast = TY * W + 3 + x;
     const int s_pxp = o_pxp + r * (nx + 1) + x;  // p+ of node x - 1 of row r (written); + 1: of node x (read)
-    const int s_pyp = o_pyp + r * nx + x;        // p+ of tile row r - 1 (written); + nx: of row r (read)
+    const int s_pyw = o_pyp + gk * nx + x;       // p+ of tile row gk - 1 (written)
+    const int s_pyr = o_pyp + (r + 1) * nx + x;  // p+ of tile row r (read)
 
     const T h0 = SP<T>::half_inv_dx(P, 0), h1 = SP<T>::half_inv_dx(P, 1), hS = SP<T>::half_inv_dx(P, SD);
     const T dt = R.dt, cv = R.cv, cu = R.cu;
@@ -197,39 +229,43 @@ __device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T
     }
 
     // Halo rows (three above, three below, and rows past the grid edge in a
-    // ragged last tile), loaded by thread rows in turn: row h of n_extra.
+    // ragged last tile): slot s = h * nx + hx of the n_extra * nx halo values
+    // goes to thread s, s - NT, ... (node threads take their own column).
     const int n_extra = 3 + (TY + 3 - rows_valid);
+    const int n_halo = n_extra * nx;
 
     // Plane p into buffer b, except the node values: halo rows (in-grid or
     // periodic rows copied asynchronously, rows past an extrapolated edge by
-    // the ghost rule) and, from the spare thread, the row's x-ghost sources
+    // the ghost rule) and, from the row ends, the row's x-ghost sources
     // (periodic: the wrapped nodes into the ghost cells; extrapolated: the
     // two outermost nodes at each end into the row-end slots).
-    // this thread's first halo row (the same in every plane): destination and source row
-    const bool h0_on = halo_thread && r < n_extra;
-    const int h0_rr = (r < 3) ? r - 3 : rows_valid + (r - 3);
-    const int h0_dst = (h0_rr + 3) * W + 3 + x;
+    auto halo_slot = [&](int sidx, int fp, T* b) {
+        const int h = sidx / nx, hx = sidx - h * nx;
+        const int rr = (h < 3) ? h - 3 : rows_valid + (h - 3);
+        int yy = y0 + rr;
+        T* dst = b + (rr + 3) * W + 3 + hx;
+        if (per1 && (yy < 0 || yy >= ny)) yy = (yy % ny + ny) % ny;
+        const T* base = u + plane0 + fp + hx;
+        if (yy >= 0 && yy < ny) cp_async_elem(dst, base + yy * nx);
+        else *dst = line_value(base, yy, ny, (long long)nx, false, extrap);
+    };
+    // this thread's first halo slot (the same in every plane): destination and source
+    const bool h0_on = t < n_halo;
+    const int h0_h = t / nx, h0_x = t - (t / nx) * nx;
+    const int h0_rr = (h0_h < 3) ? h0_h - 3 : rows_valid + (h0_h - 3);
+    const int h0_dst = (h0_rr + 3) * W + 3 + h0_x;
     int h0_yy = y0 + h0_rr;
     if (per1 && (h0_yy < 0 || h0_yy >= ny)) h0_yy = (h0_yy % ny + ny) % ny;
     const bool h0_in = h0_yy >= 0 && h0_yy < ny;
-    const int h0_src = plane0 + x + (h0_in ? h0_yy * nx : 0);
+    const int h0_src = plane0 + h0_x + (h0_in ? h0_yy * nx : 0);
     auto stage_rest = [&](int p, T* b) {
         const int fp = p * sS;
         if (h0_on) {
             if (h0_in) cp_async_elem(b + h0_dst, u + h0_src + fp);
-            else b[h0_dst] = line_value(u + plane0 + fp + x, h0_yy, ny, (long long)nx, false, extrap);
+            else b[h0_dst] = line_value(u + plane0 + fp + h0_x, h0_yy, ny, (long long)nx, false, extrap);
         }
-        if (halo_thread) {
-            const T* base = u + plane0 + fp + x;
-            for (int h = r + NR; h < n_extra; h += NR) {  // further halo rows (small blocks, ragged tiles)
-                const int rr = (h < 3) ? h - 3 : rows_valid + (h - 3);
-                int yy = y0 + rr;
-                T* dst = b + (rr + 3) * W + 3 + x;
-                if (per1 && (yy < 0 || yy >= ny)) yy = (yy % ny + ny) % ny;
-                if (yy >= 0 && yy < ny) cp_async_elem(dst, base + yy * nx);
-                else *dst = line_value(base, yy, ny, (long long)nx, false, extrap);
-            }
-        } else if (spare) {
+        for (int sidx = t + NT; sidx < n_halo; sidx += NT) halo_slot(sidx, fp, b);  // small blocks, ragged tiles
+        if (spare) {
             const T* rowg = u + plane0 + fp + y * nx;
             if (per0) {
                 T* rows = b + (r + 3) * W;
@@ -247,7 +283,7 @@ __device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T
             }
         }
     };
-    // Spare thread, after its copies into b have landed: the extrapolated x-ghost cells of its row.
+    // Row end, after its copies into b have landed: the extrapolated x-ghost cells of its row.
     auto finish_ghosts = [&](T* b) {
         if (spare && !per0) {
             const T* e = b + o_ends + 4 * r;
@@ -312,20 +348,20 @@ __device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T
             weno_iface(a[1] - a[0], a[2] - a[1], a[3] - a[2], a[4] - a[3], a[5] - a[4], floor_raw, ppj, pmx);
             bz[s_pxp] = ppj;
         }
-        // y-interface of gap r (between tile rows r-1 and r) of column x
-        if (do_ygap) {
+        // y-interface of gap gk (between tile rows gk-1 and gk) of column x
+        if (gk >= 0) {
             const T* c = bz + s_ycol;
             T ppj;
             weno_iface(c[W] - c[0], c[2 * W] - c[W], c[3 * W] - c[2 * W], c[4 * W] - c[3 * W], c[5 * W] - c[4 * W],
                        floor_raw, ppj, pmy);
-            bz[s_pyp] = ppj;
+            bz[s_pyw] = ppj;
         }
         if (do_ylast) {
             const T* c = bz + s_ylast;
             T ppj, unused;
             weno_iface(c[W] - c[0], c[2 * W] - c[W], c[3 * W] - c[2 * W], c[4 * W] - c[3 * W], c[5 * W] - c[4 * W],
                        floor_raw, ppj, unused);
-            bz[o_pyp + NR * nx + x] = ppj;
+            bz[o_pyp + TY * nx + x] = ppj;
         }
         cp_async_wait_all();  // this thread's copies into plane z+1
         if (z + 1 < zend) finish_ghosts(bn);
@@ -340,7 +376,7 @@ __device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T
             const T center = (D >= 3) ? q[2] : ld(ucol);
             T pb[D], dd[D];
             const T ppx = bz[s_pxp + 1];
-            const T ppy = bz[s_pyp + nx];
+            const T ppy = bz[s_pyr];
             pb[0] = (pmx + ppx) * h0;
             dd[0] = (ppx - pmx) * h0;
             pb[1] = (pmy + ppy) * h1;
@@ -389,13 +425,13 @@ __device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T
     }
 }
 
-template <typename T, int D, int DYN, int KIND>
-__global__ void __launch_bounds__(RowsLimits<T>::kMaxThreads) rows_kernel(const StageParams P, const RowsCfg C) {
+template <typename T, int D, int DYN, int KIND, int OCC>
+__global__ void __launch_bounds__(RowsBounds<T, OCC>::kThreads, OCC) rows_kernel(const StageParams P, const RowsCfg C) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const StageRun<T> R = stage_run<T>(P);
     const int i2 = (D == 4) ? (int)blockIdx.y : 0;
     const int chunk = (D == 3) ? (int)blockIdx.y : ((D == 4) ? (int)blockIdx.z : 0);
-    rows_tile<T, D, DYN, KIND>(P, R, C.ty, C.nr, C.tz, blockIdx.x, i2, chunk, threadIdx.x, threadIdx.y,
+    rows_tile<T, D, DYN, KIND>(P, R, C.ty, C.nt, C.tz, blockIdx.x, i2, chunk, threadIdx.x,
                                reinterpret_cast<T*>(smem_raw));
 }
 
@@ -407,34 +443,43 @@ inline size_t rows_smem_bytes(int nx, int ty) {
 
 template <typename T, int D, int DYN>
 inline void rows_shape(const StageParams& p, const RowsCfg& c, dim3& grid, dim3& block, size_t& smem) {
-    block = dim3((unsigned)(p.g.n[0] + 1), (unsigned)c.nr, 1);
+    block = dim3((unsigned)c.nt, 1, 1);
     grid = dim3((unsigned)c.row_tiles, 1, 1);
     if (D == 3) grid.y = (unsigned)c.nchunks;
     if (D == 4) { grid.y = (unsigned)p.g.n[2]; grid.z = (unsigned)c.nchunks; }
     smem = rows_smem_bytes<T>(p.g.n[0], c.ty);
 }
 
-template <typename T, int D, int DYN, int KIND>
+template <typename T, int D, int DYN, int KIND, int OCC>
 inline cudaError_t rows_prepare() {
     static bool done = false;  // benign race: setting the attribute twice is harmless
     if (!done) {
-        cudaError_t e = cudaFuncSetAttribute(rows_kernel<T, D, DYN, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             200 * 1024);
+        cudaError_t e = cudaFuncSetAttribute(rows_kernel<T, D, DYN, KIND, OCC>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         if (e != cudaSuccess) return e;
         done = true;
     }
     return cudaSuccess;
 }
 
-template <typename T, int D, int DYN, int KIND>
-cudaError_t launch_rows_kind(const StageParams& p, const RowsCfg& c, cudaStream_t s) {
+template <typename T, int D, int DYN, int KIND, int OCC>
+cudaError_t launch_rows_occ(const StageParams& p, const RowsCfg& c, cudaStream_t s) {
     dim3 grid, block;
     size_t smem;
     rows_shape<T, D, DYN>(p, c, grid, block, smem);
-    cudaError_t e = rows_prepare<T, D, DYN, KIND>();
+    cudaError_t e = rows_prepare<T, D, DYN, KIND, OCC>();
     if (e != cudaSuccess) return e;
-    rows_kernel<T, D, DYN, KIND><<<grid, block, smem, s>>>(p, c);
+    rows_kernel<T, D, DYN, KIND, OCC><<<grid, block, smem, s>>>(p, c);
     return cudaGetLastError();
+}
+
+// The variant for two blocks per SM exists for FP32 only.
+template <typename T, int D, int DYN, int KIND>
+cudaError_t launch_rows_kind(const StageParams& p, const RowsCfg& c, cudaStream_t s) {
+    if constexpr (std::is_same<T, float>::value) {
+        if (c.occ == 2) return launch_rows_occ<T, D, DYN, KIND, 2>(p, c, s);
+    }
+    return launch_rows_occ<T, D, DYN, KIND, 1>(p, c, s);
 }
 
 template <typename T, int D, int DYN>
@@ -446,24 +491,28 @@ cudaError_t launch_rows_dyn(const StageParams& p, const RowsCfg& c, cudaStream_t
     }
 }
 
-template <typename T, int D, int DYN, int KIND>
-int rows_bps_kind(const StageParams& p, const RowsCfg& c) {
+template <typename T, int D, int DYN, int OCC>
+int rows_bps_occ(const StageParams& p, const RowsCfg& c) {
     dim3 grid, block;
     size_t smem;
     rows_shape<T, D, DYN>(p, c, grid, block, smem);
-    if (rows_prepare<T, D, DYN, KIND>() != cudaSuccess) return 0;
+    if ((int)block.x > RowsBounds<T, OCC>::kThreads) return 0;
+    if (rows_prepare<T, D, DYN, kKindCombine, OCC>() != cudaSuccess) return 0;
     int bps = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, rows_kernel<T, D, DYN, KIND>, (int)(block.x * block.y),
-                                                      smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, rows_kernel<T, D, DYN, kKindCombine, OCC>,
+                                                      (int)block.x, smem) != cudaSuccess)
         return 0;
     return bps;
 }
 
-// Resident blocks per SM of the stage kernels (the combining stages, the
-// largest of the three kinds).
+// Resident blocks per SM of the stage kernels of a configuration (the
+// combining stages, the largest of the three kinds); 0 if it cannot launch.
 template <typename T, int D, int DYN>
 int rows_bps_dyn(const StageParams& p, const RowsCfg& c) {
-    return rows_bps_kind<T, D, DYN, kKindCombine>(p, c);
+    if constexpr (std::is_same<T, float>::value) {
+        if (c.occ == 2) return rows_bps_occ<T, D, DYN, 2>(p, c);
+    }
+    return rows_bps_occ<T, D, DYN, 1>(p, c);
 }
 
 // Dispatch over the (dimension, dynamics) pairs the row kernel is built for.

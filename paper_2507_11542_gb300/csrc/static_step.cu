@@ -102,7 +102,8 @@ bool pick_rows(const StageParams& P, int dtype, int sm_count, RowsCfg* c) {
     const size_t es = dtype == HJ_F64 ? 8 : 4;
     if (rows_smem(nx, ty, es) > 200 * 1024) return false;
     c->ty = ty;
-    c->nr = rows_thread_rows(nx, ty, max_threads);
+    c->nt = rows_block_threads(nx, ty, max_threads);
+    c->occ = 1;
     c->row_tiles = (ny + ty - 1) / ty;
     const int ns = D >= 3 ? G.n[D - 1] : 1;
     const long long per_plane = (long long)c->row_tiles * (D == 4 ? G.n[2] : 1);
