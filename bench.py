@@ -269,6 +269,31 @@ def bench_e2e(ctx, spec, V0, dtype, K, W_, world):
             "rk3_steps_per_step": steps // K, "launches": launches}
 
 
+def bench_surface(ctx, hbm, reps=20):
+    """hj_implicit_surface on the 512^3 grid (FP32): the union of two spheres
+    written to HBM; bytes written = 4 per node."""
+    import torch
+    from paper_2507_11542_gb300 import solver, workloads as W
+    spec, _ = W.expanding_sphere(512)
+    shapes = [{"kind": 1, "center": (-0.3, 0.0, 0.0), "radius": 0.25},
+              {"kind": 1, "op": 1, "center": (0.3, 0.1, 0.0), "radius": 0.2}]
+    n = int(np.prod(spec.n))
+    out = torch.empty(n, dtype=torch.float32, device="cuda")
+    for _ in range(3):
+        solver.implicit_surface(ctx, spec, shapes, out=out)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        solver.implicit_surface(ctx, spec, shapes, out=out)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    gbs = 4 * n / (ms / 1e3) / 1e9
+    return {"ms": ms, "cells": n, "hbm_achieved_gbs": gbs, "hbm_frac": gbs / hbm, "bound": "hbm",
+            "what": "initial surface (union of two spheres) written by the device, FP32"}
+
+
 def bench_large(ctx, world, flush):
     """The grids far larger than L2: the expanding sphere on 512^3 (FP32) and
     the Dubins car on 81^4 (FP32 and FP64), device-resident RK3 steps. Their
@@ -279,6 +304,7 @@ def bench_large(ctx, world, flush):
     cases = [("sphere512_f32", W.expanding_sphere(512), solver.method(dynamics=4, params=(1.0,), brt=0), "float32", 10),
              ("dubins81_f32", W.dubins4d(81), solver.method(dynamics=3, params=(1.0, 0.5), brt=1), "float32", 6),
              ("dubins81_f64", W.dubins4d(81), solver.method(dynamics=3, params=(1.0, 0.5), brt=1), "float64", 3)]
+    out["surface512_f32"] = bench_surface(ctx, hbm)
     for name, (spec, V0), m, dtype, K in cases:
         n = int(np.prod(spec.n))
         r = bench_dtype(ctx, spec, V0, dtype, K, 3, world, flush, m=m)

@@ -290,6 +290,42 @@ void hj_server_destroy(hj_server* srv);
 hj_status hj_rk3_step_static(void* cuda_stream, int32_t device, const hj_grid* grid, const hj_method* method,
                              int32_t dtype, void* v, double dt);
 
+/* Initial surfaces on the device (Sec. 2.2: implicit surfaces built on the
+ * grid container, geometric primitives and Boolean operations; the ellipsoid
+ * listing of that section). ------------------------------------------------ */
+
+enum { HJ_SHAPE_SPHERE = 1, HJ_SHAPE_ELLIPSOID = 2, HJ_SHAPE_RECTANGLE = 3 };
+enum { HJ_SHAPE_UNION = 1, HJ_SHAPE_INTERSECT = 2, HJ_SHAPE_SUBTRACT = 3 };
+#define HJ_MAX_SHAPES 32
+
+/* One primitive, over the dimensions in dims_mask (bit d); the others are
+ * ignored, which turns a sphere into a cylinder and a rectangle into a slab.
+ * With s_d = x_d - center[d]:
+ *   SPHERE     sqrt(sum_d s_d^2) - radius           (signed distance)
+ *   ELLIPSOID  sum_d axes[d] s_d^2 - radius         (the section's listing: an
+ *              implicit quadratic, not a distance; axes[d] > 0)
+ *   RECTANGLE  max_d (|s_d| - axes[d])              (axes = half-widths; the
+ *              signed distance inside and along the face normals)
+ * op says how the shape joins the shapes before it (ignored for the first):
+ *   UNION min(v, s), INTERSECT max(v, s), SUBTRACT max(v, -s). */
+typedef struct hj_shape {
+    int32_t kind;       /* HJ_SHAPE_SPHERE .. HJ_SHAPE_RECTANGLE */
+    int32_t op;         /* HJ_SHAPE_UNION .. HJ_SHAPE_SUBTRACT */
+    uint32_t dims_mask; /* nonzero, within the grid's dimensions */
+    double center[4];
+    double axes[4];
+    double radius;
+} hj_shape;
+
+/* V(x) of n_shapes (1..HJ_MAX_SHAPES) primitives combined in order, at every
+ * grid node, into out (prod(n) elements of dtype; device memory if
+ * out_on_device, else host memory, which makes the call synchronous). FP64
+ * output is computed in FP64, FP32 output in FP32. Asynchronous for device
+ * output. Errors: HJ_EINVAL (grid, dtype, a shape's kind, op, mask or
+ * parameters, n_shapes, NULL pointers), HJ_ENOMEM, HJ_ECUDA. */
+hj_status hj_implicit_surface(hj_ctx* ctx, const hj_grid* grid, int32_t n_shapes, const hj_shape* shapes,
+                              int32_t dtype, void* out, int32_t out_on_device);
+
 #ifdef __cplusplus
 }
 #endif

@@ -33,7 +33,10 @@ HJ_EXTRAP_AWAY_FROM_ZERO, HJ_EXTRAP_LINEAR = 0, 1
 EXPORTS = ["hj_ctx_create", "hj_ctx_destroy", "hj_status_str", "hj_ctx_last_error", "hj_version",
            "hj_upwind", "hj_term", "hj_step_bound", "hj_rk3_step", "hj_rk3_stage", "hj_solve",
            "hj_rk3_step_static", "hj_solve_batch", "hj_server_create", "hj_server_submit", "hj_server_wait",
-           "hj_server_cancel", "hj_server_counters", "hj_server_destroy"]
+           "hj_server_cancel", "hj_server_counters", "hj_server_destroy", "hj_implicit_surface"]
+HJ_SHAPE_SPHERE, HJ_SHAPE_ELLIPSOID, HJ_SHAPE_RECTANGLE = 1, 2, 3
+HJ_SHAPE_UNION, HJ_SHAPE_INTERSECT, HJ_SHAPE_SUBTRACT = 1, 2, 3
+HJ_MAX_SHAPES = 32
 HJ_STATIC_MAX_NODES = 1 << 20
 HJ_STATIC_MAX_ANGLES = 4096
 
@@ -69,6 +72,11 @@ class hj_server_info(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class hj_shape(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("op", ctypes.c_int32), ("dims_mask", ctypes.c_uint32),
+                ("center", ctypes.c_double * 4), ("axes", ctypes.c_double * 4), ("radius", ctypes.c_double)]
 
 
 class HJError(RuntimeError):
@@ -122,6 +130,8 @@ def load():
             L.hj_server_destroy.restype = None
             L.hj_rk3_step_static.argtypes = [_vp, ctypes.c_int32, _P(hj_grid), _P(hj_method), ctypes.c_int32, _vp,
                                              ctypes.c_double]
+            L.hj_implicit_surface.argtypes = [_vp, _P(hj_grid), ctypes.c_int32, _P(hj_shape), ctypes.c_int32, _vp,
+                                              ctypes.c_int32]
             _lib = L
     return _lib
 
@@ -322,3 +332,33 @@ def make_problem(spec, method: hj_method, dtype: int, v0_ptr: int, v0_on_device:
     p.n_slices = ts.size
     p.slice_times = ts.ctypes.data_as(_P(ctypes.c_double))
     return p, ts
+
+
+def make_shapes(shapes):
+    """shapes: sequence of dicts {kind, op, dims, center, axes, radius}; dims is
+    a sequence of dimension indices (default: all four bits up to the center's
+    length), center/axes sequences of up to 4 numbers."""
+    arr = (hj_shape * len(shapes))()
+    for k, sh in enumerate(shapes):
+        a = arr[k]
+        a.kind = int(sh["kind"])
+        a.op = int(sh.get("op", HJ_SHAPE_UNION))
+        dims = sh.get("dims", range(len(sh.get("center", ()))))
+        a.dims_mask = sum(1 << int(d) for d in dims)
+        for d, v in enumerate(sh.get("center", ())):
+            a.center[d] = float(v)
+        for d, v in enumerate(sh.get("axes", ())):
+            a.axes[d] = float(v)
+        a.radius = float(sh.get("radius", 0.0))
+    return arr
+
+
+def hj_implicit_surface(ctx, grid: hj_grid, shapes, dtype: int, out, out_on_device: bool = True) -> None:
+    """out: a CUDA tensor (out_on_device) or a host numpy array / tensor of prod(n) elements."""
+    arr = make_shapes(shapes)
+    if out_on_device:
+        ptr = _ptr(out)
+    else:
+        ptr = out.ctypes.data if isinstance(out, np.ndarray) else int(out.data_ptr())
+    _check(ctx, load().hj_implicit_surface(_vp(ctx), ctypes.byref(grid), len(shapes), arr, dtype, _vp(ptr),
+                                           1 if out_on_device else 0))

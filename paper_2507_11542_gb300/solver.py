@@ -184,3 +184,17 @@ class Server:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def implicit_surface(ctx: Context, spec, shapes, dtype="float32", out=None):
+    """V0 from implicit primitives (Sec. 2.2), built on the device: a flat CUDA
+    tensor of prod(n) elements. shapes: dicts {kind, op, dims, center, axes,
+    radius} (see include/hj.h, hj_shape)."""
+    import torch
+    tdt = getattr(torch, dtype) if isinstance(dtype, str) else dtype
+    n = int(np.prod(spec.n))
+    if out is None:
+        out = torch.empty(n, dtype=tdt, device="cuda:%d" % ctx.device)
+    _check_tensor(out, spec, "out")
+    L.hj_implicit_surface(ctx.handle, L.make_grid(spec), shapes, L.dtype_code(out.dtype), out)
+    return out
