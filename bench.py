@@ -294,6 +294,32 @@ def bench_surface(ctx, hbm, reps=20):
             "what": "initial surface (union of two spheres) written by the device, FP32"}
 
 
+def bench_rockets(ctx):
+    """The paper's rockets game as it runs it: 100^3 over [-64, 64], 11 slices
+    over a 2.5 s horizon, BRT with the positive rule; one hj_solve with host
+    input and output (V0 up, 11 slices down), FP64 ENO2 as the paper, and
+    FP32 WENO5."""
+    import torch
+    from paper_2507_11542_gb300 import solver, workloads as W
+    spec, V0 = W.rockets(100)
+    ts = list(W.slice_times(2.5))
+    out = {}
+    for name, dtype, scheme in (("fp64_eno2", "float64", 2), ("fp32_weno5", "float32", 5)):
+        m = solver.method(scheme=scheme, dynamics=7, params=(1.0, 32.0, 1.0, 1.0), brt=1)
+        tdt = getattr(torch, dtype)
+        v0 = torch.from_numpy(np.ascontiguousarray(V0.ravel(order="F"))).to(tdt).pin_memory()
+        res = torch.empty((len(ts), v0.numel()), dtype=tdt).pin_memory()
+        solver.solve(ctx, spec, m, v0, ts[:2], out=res[:2])  # warm-up (tuning, tables)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, _, st = solver.solve(ctx, spec, m, v0, ts, out=res)
+        el = time.perf_counter() - t0
+        out[name] = {"seconds": el, "steps": st["steps"], "cell_updates_per_s": st["cell_updates"] / el}
+    out["context"] = ("the paper's Table 1: 11.52 s (global) on a Quadro RTX 4000 with CuPy in FP64, "
+                      "ENO2; another machine, quoted as context")
+    return out
+
+
 def bench_large(ctx, world, flush):
     """The grids far larger than L2: the expanding sphere on 512^3 (FP32) and
     the Dubins car on 81^4 (FP32 and FP64), device-resident RK3 steps. Their
@@ -508,6 +534,7 @@ def main():
         batch = bench_batch(ctx, rank=rank, world=world)
         serve = bench_serve(ctx, args.serve_requests) if world == 1 else None
         large = bench_large(ctx, world, flush)
+        rockets = bench_rockets(ctx) if world == 1 else None
     value = world * K * N_CELLS / (r32["total_ms"] / 1e3)
     hbm, hbm_kind = measured_hbm_gbs()
     launch_s = r32["launch_ms_mean"] / 1e3
@@ -549,6 +576,8 @@ def main():
     if serve:
         line["served"] = serve
     line["large_grids"] = large
+    if rockets:
+        line["rockets"] = rockets
     if rank == 0 and not args.no_cpu_baseline:
         rate, el = cpu_oracle_rate(spec, V0, args.cpu_steps)
         line["cpu_baseline"] = {"value": rate, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",

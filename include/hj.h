@@ -54,6 +54,11 @@ enum { HJ_ENO1 = 1, HJ_ENO2 = 2, HJ_ENO3 = 3, HJ_WENO5 = 5 };
  *   NORM (1..3-D)            params {c}:                 Hg = -c |p|
  *   ADVECT (1..3-D)          params {c0, c1, c2}:        Hg = -c . p
  *   ROTATE (2..3-D)          params {omega}:             Hg = -p . omega(-x1, x0, 0)
+ *   ROCKETS (3-D)            params {a, g, ue_max, up_max}: the rockets game of
+ *                            Sec. 6.1, state (x, z, theta), f = (a cos th + ue x,
+ *                            a sin th + a - g + up x, up - ue), evader ue maximising,
+ *                            pursuer up minimising: Hg = a p0 cos th + p1 (a sin th
+ *                            + a - g) + ue_max |p0 x - p2| - up_max |p1 x + p2|
  * The dissipation alpha_d(x) is the maximum of |f_d| over the controls
  * (Sec. 4, "alpha = max |H_p|"), evaluated per node. */
 enum {
@@ -62,7 +67,8 @@ enum {
     HJ_DYN_DUBINS4D = 3,
     HJ_DYN_NORM = 4,
     HJ_DYN_ADVECT = 5,
-    HJ_DYN_ROTATE = 6
+    HJ_DYN_ROTATE = 6,
+    HJ_DYN_ROCKETS = 7
 };
 
 /* Backward-reachable-tube rule (Sec. 6.1): none, V_tau = min(0, Hg_LF) at each

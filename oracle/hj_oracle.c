@@ -263,6 +263,17 @@ int orc_hamiltonian(const orc_method* m, int ndim, const double* x, const double
         if (ndim < 2) return ORC_EINVAL;
         *hg = -(p[0] * (-q[0] * x[1]) + p[1] * (q[0] * x[0]));
         return 0;
+    case ORC_DYN_ROCKETS: {
+        /* Sec. 6.1, dynamics as they stand inside the game's Hamiltonian (reading):
+         * x' = a cos th + ue x, z' = a sin th + a - g + up x, th' = up - ue, the
+         * evader's thrust ue maximising and the pursuer's up minimising:
+         * p . f = p0 a cos th + p1 (a sin th + a - g) + ue (p0 x - p2) + up (p1 x + p2). */
+        if (ndim != 3) return ORC_EINVAL;
+        double a = q[0], g = q[1], ue = q[2], up = q[3];
+        *hg = p[0] * a * cos(x[2]) + p[1] * (a * sin(x[2]) + a - g) + ue * fabs(p[0] * x[0] - p[2]) -
+              up * fabs(p[1] * x[0] + p[2]);
+        return 0;
+    }
     default:
         return ORC_EINVAL;
     }
@@ -304,6 +315,14 @@ int orc_alpha(const orc_method* m, int ndim, const double* x, double* alpha) {
         alpha[1] = fabs(q[0] * x[0]);
         for (int d = 2; d < ndim; ++d) alpha[d] = 0.0;
         return 0;
+    case ORC_DYN_ROCKETS: {
+        if (ndim != 3) return ORC_EINVAL;
+        double a = q[0], g = q[1], ue = q[2], up = q[3];
+        alpha[0] = fabs(a * cos(x[2])) + ue * fabs(x[0]);
+        alpha[1] = fabs(a * sin(x[2]) + a - g) + up * fabs(x[0]);
+        alpha[2] = up + ue;
+        return 0;
+    }
     default:
         return ORC_EINVAL;
     }

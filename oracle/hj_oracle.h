@@ -45,7 +45,8 @@ enum {
     ORC_DYN_DUBINS4D = 3,          /* params: wmax, accmax */
     ORC_DYN_NORM = 4,              /* params: speed c  (Hg = -c |p|) */
     ORC_DYN_ADVECT = 5,            /* params: c0..c3   (Hg = -c . p) */
-    ORC_DYN_ROTATE = 6             /* params: omega    (Hg = -p . omega(-x1, x0)) */
+    ORC_DYN_ROTATE = 6,            /* params: omega    (Hg = -p . omega(-x1, x0)) */
+    ORC_DYN_ROCKETS = 7            /* params: a, g, ue_max, up_max (Sec. 6.1 rockets game) */
 };
 /* backward-reachable-tube rule (Sec. 6.1) */
 enum { ORC_BRT_NONE = 0, ORC_BRT_MIN0 = 1, ORC_BRT_MINV = 2 };

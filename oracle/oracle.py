@@ -24,7 +24,7 @@ HDR = os.path.join(HERE, "hj_oracle.h")
 LIB = os.path.join(HERE, "liboracle.so")
 
 ENO1, ENO2, ENO3, WENO5 = 1, 2, 3, 5
-DYN_DOUBLE_INTEGRATOR, DYN_AIR3D, DYN_DUBINS4D, DYN_NORM, DYN_ADVECT, DYN_ROTATE = 1, 2, 3, 4, 5, 6
+DYN_DOUBLE_INTEGRATOR, DYN_AIR3D, DYN_DUBINS4D, DYN_NORM, DYN_ADVECT, DYN_ROTATE, DYN_ROCKETS = 1, 2, 3, 4, 5, 6, 7
 BRT_NONE, BRT_MIN0, BRT_MINV = 0, 1, 2
 EXTRAP_AWAY_FROM_ZERO, EXTRAP_LINEAR = 0, 1
 

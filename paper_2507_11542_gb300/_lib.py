@@ -24,7 +24,7 @@ LIB_PATH = os.path.join(PKG, "libhj.so")
 HJ_OK, HJ_EINVAL, HJ_ENOMEM, HJ_ECUDA, HJ_ENONFINITE, HJ_ETIMEOUT, HJ_ECANCELLED, HJ_EBUSY = range(8)
 HJ_ENO1, HJ_ENO2, HJ_ENO3, HJ_WENO5 = 1, 2, 3, 5
 (HJ_DYN_DOUBLE_INTEGRATOR, HJ_DYN_AIR3D, HJ_DYN_DUBINS4D, HJ_DYN_NORM, HJ_DYN_ADVECT,
- HJ_DYN_ROTATE) = 1, 2, 3, 4, 5, 6
+ HJ_DYN_ROTATE, HJ_DYN_ROCKETS) = 1, 2, 3, 4, 5, 6, 7
 HJ_BRT_NONE, HJ_BRT_MIN0, HJ_BRT_MINV = 0, 1, 2
 HJ_F32, HJ_F64 = 1, 2
 HJ_EXTRAP_AWAY_FROM_ZERO, HJ_EXTRAP_LINEAR = 0, 1

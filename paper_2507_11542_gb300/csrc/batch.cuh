@@ -81,6 +81,7 @@ cudaError_t launch_batch_dyn(const BatchTile* tiles, int ntiles, const BatchInst
     case 2 * 16 + HJ_DYN_ADVECT: return launch_batch_dyn<T, 2, HJ_DYN_ADVECT>(tiles, ntiles, insts, stage, threads, smem, s); \
     case 2 * 16 + HJ_DYN_ROTATE: return launch_batch_dyn<T, 2, HJ_DYN_ROTATE>(tiles, ntiles, insts, stage, threads, smem, s); \
     case 3 * 16 + HJ_DYN_AIR3D: return launch_batch_dyn<T, 3, HJ_DYN_AIR3D>(tiles, ntiles, insts, stage, threads, smem, s); \
+    case 3 * 16 + HJ_DYN_ROCKETS: return launch_batch_dyn<T, 3, HJ_DYN_ROCKETS>(tiles, ntiles, insts, stage, threads, smem, s); \
     case 3 * 16 + HJ_DYN_NORM: return launch_batch_dyn<T, 3, HJ_DYN_NORM>(tiles, ntiles, insts, stage, threads, smem, s); \
     case 3 * 16 + HJ_DYN_ADVECT: return launch_batch_dyn<T, 3, HJ_DYN_ADVECT>(tiles, ntiles, insts, stage, threads, smem, s); \
     case 3 * 16 + HJ_DYN_ROTATE: return launch_batch_dyn<T, 3, HJ_DYN_ROTATE>(tiles, ntiles, insts, stage, threads, smem, s); \

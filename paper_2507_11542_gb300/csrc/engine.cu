@@ -12,7 +12,7 @@ namespace {
 constexpr size_t kAlign = 256;
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 int max_block_threads(int dtype) { return rows_max_threads(dtype == HJ_F64); }
-bool uses_angles(int dyn) { return dyn == HJ_DYN_AIR3D || dyn == HJ_DYN_DUBINS4D; }
+bool uses_angles(int dyn) { return dyn == HJ_DYN_AIR3D || dyn == HJ_DYN_DUBINS4D || dyn == HJ_DYN_ROCKETS; }
 long long nodes_of(const hj_grid& g) {
     long long n = 1;
     for (int d = 0; d < g.ndim; ++d) n *= g.n[d];

@@ -91,6 +91,10 @@ hj_status check_method(hj_ctx* ctx, const hj_grid* g, const hj_method* m) {
     case HJ_DYN_ROTATE:
         if (D < 2 || D > 3) return fail(ctx, HJ_EINVAL, "rotation supports ndim 2..3");
         break;
+    case HJ_DYN_ROCKETS:
+        if (D != 3) return fail(ctx, HJ_EINVAL, "rockets needs ndim 3");
+        if (q[2] < 0 || q[3] < 0) return fail(ctx, HJ_EINVAL, "control bounds < 0");
+        break;
     default:
         return fail(ctx, HJ_EINVAL, "unknown dynamics %d", m->dynamics);
     }
@@ -227,7 +231,7 @@ void plan_schedule(const hj_method* m, double sbi, int n_slices, const double* s
 }
 
 hj_status upload_trig(hj_ctx* ctx, const hj_grid* g, int dynamics) {
-    if (dynamics != HJ_DYN_AIR3D && dynamics != HJ_DYN_DUBINS4D) return HJ_OK;
+    if (dynamics != HJ_DYN_AIR3D && dynamics != HJ_DYN_DUBINS4D && dynamics != HJ_DYN_ROCKETS) return HJ_OK;
     const int n = (int)g->n[2];
     const bool periodic = (g->periodic_mask >> 2) & 1u;
     const double dx = (g->hi[2] - g->lo[2]) / (periodic ? (double)n : (double)(n - 1));

@@ -26,6 +26,13 @@ __device__ double node_bound(const GridDev& g, int dyn, const double* q, const d
         a[2] = __dadd_rn(q[2], q[3]);
         break;
     }
+    case HJ_DYN_ROCKETS: {
+        const double c = trig[idx[2]], s = trig[g.n[2] + idx[2]];
+        a[0] = __dadd_rn(fabs(__dmul_rn(q[0], c)), __dmul_rn(q[2], fabs(x[0])));
+        a[1] = __dadd_rn(fabs(__dadd_rn(__dadd_rn(__dmul_rn(q[0], s), q[0]), -q[1])), __dmul_rn(q[3], fabs(x[0])));
+        a[2] = __dadd_rn(q[3], q[2]);
+        break;
+    }
     case HJ_DYN_DUBINS4D: {
         const double c = trig[idx[2]], s = trig[g.n[2] + idx[2]];
         a[0] = fabs(__dmul_rn(x[3], c));

@@ -9,6 +9,7 @@ bool rows_supported(int ndim, int dyn) {
     case 2 * 16 + HJ_DYN_ADVECT:
     case 2 * 16 + HJ_DYN_ROTATE:
     case 3 * 16 + HJ_DYN_AIR3D:
+    case 3 * 16 + HJ_DYN_ROCKETS:
     case 3 * 16 + HJ_DYN_NORM:
     case 3 * 16 + HJ_DYN_ADVECT:
     case 3 * 16 + HJ_DYN_ROTATE:

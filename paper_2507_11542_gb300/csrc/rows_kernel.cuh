@@ -523,6 +523,7 @@ int rows_bps_dyn(const StageParams& p, const RowsCfg& c) {
     case 2 * 16 + HJ_DYN_ADVECT: return FN<T, 2, HJ_DYN_ADVECT>(__VA_ARGS__);         \
     case 2 * 16 + HJ_DYN_ROTATE: return FN<T, 2, HJ_DYN_ROTATE>(__VA_ARGS__);         \
     case 3 * 16 + HJ_DYN_AIR3D: return FN<T, 3, HJ_DYN_AIR3D>(__VA_ARGS__);           \
+    case 3 * 16 + HJ_DYN_ROCKETS: return FN<T, 3, HJ_DYN_ROCKETS>(__VA_ARGS__);       \
     case 3 * 16 + HJ_DYN_NORM: return FN<T, 3, HJ_DYN_NORM>(__VA_ARGS__);             \
     case 3 * 16 + HJ_DYN_ADVECT: return FN<T, 3, HJ_DYN_ADVECT>(__VA_ARGS__);         \
     case 3 * 16 + HJ_DYN_ROTATE: return FN<T, 3, HJ_DYN_ROTATE>(__VA_ARGS__);         \

@@ -81,6 +81,7 @@ bool method_valid(const hj_grid* g, const hj_method* m) {
     case HJ_DYN_NORM: return D <= 3 && m->params[0] >= 0;
     case HJ_DYN_ADVECT: return D <= 3;
     case HJ_DYN_ROTATE: return D >= 2 && D <= 3;
+    case HJ_DYN_ROCKETS: return D == 3 && m->params[2] >= 0 && m->params[3] >= 0;
     default: return false;
     }
 }
@@ -133,7 +134,8 @@ extern "C" hj_status hj_rk3_step_static(void* cuda_stream, int32_t device, const
         total *= grid->n[d];
         if (total > HJ_STATIC_MAX_NODES) return HJ_EINVAL;  // beyond the fixed scratch
     }
-    const bool angles = method->dynamics == HJ_DYN_AIR3D || method->dynamics == HJ_DYN_DUBINS4D;
+    const bool angles = method->dynamics == HJ_DYN_AIR3D || method->dynamics == HJ_DYN_DUBINS4D ||
+                        method->dynamics == HJ_DYN_ROCKETS;
     if (angles && grid->n[2] > HJ_STATIC_MAX_ANGLES) return HJ_EINVAL;
 
     int prev = -1;

@@ -232,7 +232,7 @@ template <> struct Trig<float>  { static __device__ __forceinline__ const float*
 // angle table of the launch).
 template <int D, int DYN>
 __host__ __device__ constexpr bool uses_angle() {
-    return (DYN == HJ_DYN_AIR3D && D == 3) || (DYN == HJ_DYN_DUBINS4D && D == 4);
+    return (DYN == HJ_DYN_AIR3D && D == 3) || (DYN == HJ_DYN_DUBINS4D && D == 4) || (DYN == HJ_DYN_ROCKETS && D == 3);
 }
 
 // ydot from node coordinates xc, cos/sin (c, s) of the dimension-2
@@ -250,6 +250,11 @@ __device__ __forceinline__ T lf_combine(const StageParams& P, const T* xc, T c, 
         const T f0 = -va + vb * c, f1 = vb * s;
         y = pb[0] * f0 + pb[1] * f1 + amax * fabs(pb[0] * xc[1] - pb[1] * xc[0] - pb[2]) - bmax * fabs(pb[2]);
         y += (fabs(f0) + amax * fabs(xc[1])) * dd[0] + (fabs(f1) + amax * fabs(xc[0])) * dd[1] + (amax + bmax) * dd[2];
+    } else if constexpr (DYN == HJ_DYN_ROCKETS && D == 3) {
+        const T a = q(0), g = q(1), ue = q(2), up = q(3);
+        const T f0 = a * c, f1 = a * s + a - g;
+        y = pb[0] * f0 + pb[1] * f1 + ue * fabs(pb[0] * xc[0] - pb[2]) - up * fabs(pb[1] * xc[0] + pb[2]);
+        y += (fabs(f0) + ue * fabs(xc[0])) * dd[0] + (fabs(f1) + up * fabs(xc[0])) * dd[1] + (ue + up) * dd[2];
     } else if constexpr (DYN == HJ_DYN_DUBINS4D && D == 4) {
         const T wmax = q(0), accmax = q(1);
         const T f0 = xc[3] * c, f1 = xc[3] * s;
@@ -276,7 +281,7 @@ __device__ __forceinline__ T lf_combine(const StageParams& P, const T* xc, T c, 
 template <int D, int DYN>
 __host__ __device__ constexpr bool uses_coord(int d) {
     return (DYN == HJ_DYN_DOUBLE_INTEGRATOR && d == 1) || (DYN == HJ_DYN_AIR3D && d <= 1) ||
-           (DYN == HJ_DYN_DUBINS4D && d == 3) || (DYN == HJ_DYN_ROTATE && d <= 1);
+           (DYN == HJ_DYN_DUBINS4D && d == 3) || (DYN == HJ_DYN_ROTATE && d <= 1) || (DYN == HJ_DYN_ROCKETS && d == 0);
 }
 
 // ydot at grid index idx from the one-sided derivatives (already divided by dx).
@@ -304,6 +309,7 @@ __device__ __forceinline__ T lf_term(const StageParams& P, const int* idx, const
     case HJ_DYN_DOUBLE_INTEGRATOR: return lf_term_dyn<T, D, HJ_DYN_DOUBLE_INTEGRATOR>(P, idx, pm, pp);
     case HJ_DYN_AIR3D: return lf_term_dyn<T, D, HJ_DYN_AIR3D>(P, idx, pm, pp);
     case HJ_DYN_DUBINS4D: return lf_term_dyn<T, D, HJ_DYN_DUBINS4D>(P, idx, pm, pp);
+    case HJ_DYN_ROCKETS: return lf_term_dyn<T, D, HJ_DYN_ROCKETS>(P, idx, pm, pp);
     case HJ_DYN_NORM: return lf_term_dyn<T, D, HJ_DYN_NORM>(P, idx, pm, pp);
     case HJ_DYN_ADVECT: return lf_term_dyn<T, D, HJ_DYN_ADVECT>(P, idx, pm, pp);
     case HJ_DYN_ROTATE: return lf_term_dyn<T, D, HJ_DYN_ROTATE>(P, idx, pm, pp);

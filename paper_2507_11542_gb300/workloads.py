@@ -80,6 +80,14 @@ def dubins4d(n: int = 81, seed: int = 1, radius: float = 1.0):
     return g, sphere(g, (float(c[0]), float(c[1])), radius, dims=(0, 1))
 
 
+def rockets(n: int = 100, radius: float = 1.5):
+    """Rockets game (Sec. 6.1): (x, z) in [-64, 64]^2, theta in [-pi/2, pi/2],
+    extrapolated boundaries; target = the capture cylinder x^2 + z^2 = 1.5^2
+    along theta."""
+    g = GridSpec((n, n, n), (-64.0, -64.0, -0.5 * math.pi), (64.0, 64.0, 0.5 * math.pi))
+    return g, sphere(g, (0.0, 0.0), radius, dims=(0, 1))
+
+
 def expanding_sphere(n: int = 512, radius: float = 0.25):
     """3-D sphere on [-1,1]^3 for the H = |p| closed-form check."""
     g = GridSpec((n, n, n), (-1.0, -1.0, -1.0), (1.0, 1.0, 1.0))

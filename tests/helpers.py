@@ -12,9 +12,9 @@ from paper_2507_11542_gb300 import workloads as W
 
 # The oracle and the library number schemes, dynamics and BRT modes alike;
 # both sides are always built from these neutral settings.
-DI, AIR3D, DUBINS, NORM, ADVECT, ROTATE = 1, 2, 3, 4, 5, 6
+DI, AIR3D, DUBINS, NORM, ADVECT, ROTATE, ROCKETS = 1, 2, 3, 4, 5, 6, 7
 PARAMS = {DI: (1.0,), AIR3D: (5.0, 5.0, 1.0, 1.0), DUBINS: (1.0, 0.5), NORM: (1.0,),
-          ADVECT: (0.7, -1.3, 0.4), ROTATE: (1.3,)}
+          ADVECT: (0.7, -1.3, 0.4), ROTATE: (1.3,), ROCKETS: (1.0, 32.0, 1.0, 1.0)}
 
 
 def oracle_method(scheme=5, dynamics=DI, params=None, brt=1, extrap=0, cfl=0.8, max_step=math.inf):

@@ -12,8 +12,8 @@ import pytest
 from oracle import oracle as O
 from paper_2507_11542_gb300 import workloads as W
 
-from helpers import (ADVECT, AIR3D, DI, DUBINS, NORM, PARAMS, ROTATE, crossing_displacement, lib_method, oracle_method,
-                     oracle_window_step, rel_err, to_dev, to_host, zero_set_displacement)
+from helpers import (ADVECT, AIR3D, DI, DUBINS, NORM, PARAMS, ROCKETS, ROTATE, crossing_displacement, lib_method,
+                     oracle_method, oracle_window_step, rel_err, to_dev, to_host, zero_set_displacement)
 
 pytestmark = pytest.mark.gpu
 TOL64 = 1e-12
@@ -38,6 +38,7 @@ SPECS = {
     NORM: W.GridSpec((21, 18, 9), (-1.0, -1.0, -1.0), (1.0, 1.0, 1.0), (1,)),
     ADVECT: W.GridSpec((70,), (0.0,), (1.0,), (0,)),
     ROTATE: W.GridSpec((33, 40), (-1.0, -1.0), (1.0, 1.0)),
+    ROCKETS: W.GridSpec((23, 19, 17), (-64.0, -64.0, -0.5 * math.pi), (64.0, 64.0, 0.5 * math.pi)),
 }
 
 
@@ -77,7 +78,7 @@ def test_upwind_parity_fp32(ctx, scheme):
     assert rel_err(to_host(pp, spec.n), pp_o) < 2e-4
 
 
-@pytest.mark.parametrize("dyn", [DI, AIR3D, DUBINS, NORM, ADVECT, ROTATE])
+@pytest.mark.parametrize("dyn", [DI, AIR3D, DUBINS, NORM, ADVECT, ROTATE, ROCKETS])
 @pytest.mark.parametrize("scheme", [2, 5])
 @pytest.mark.parametrize("brt", [0, 1])
 def test_term_parity_fp64(ctx, dyn, scheme, brt):
@@ -89,14 +90,14 @@ def test_term_parity_fp64(ctx, dyn, scheme, brt):
     assert rel_err(to_host(y, spec.n), y_o) <= TOL64
 
 
-@pytest.mark.parametrize("dyn", [DI, AIR3D, DUBINS, NORM, ADVECT, ROTATE])
+@pytest.mark.parametrize("dyn", [DI, AIR3D, DUBINS, NORM, ADVECT, ROTATE, ROCKETS])
 def test_step_bound_is_bit_exact(ctx, dyn):
     from paper_2507_11542_gb300 import solver
     spec = SPECS[dyn]
     assert solver.step_bound(ctx, spec, lib_method(dynamics=dyn)) == O.step_bound_inv(spec, oracle_method(dynamics=dyn))
 
 
-@pytest.mark.parametrize("dyn", [DI, AIR3D, DUBINS, NORM, ROTATE])
+@pytest.mark.parametrize("dyn", [DI, AIR3D, DUBINS, NORM, ROTATE, ROCKETS])
 @pytest.mark.parametrize("brt", [0, 1, 2])
 def test_rk3_step_parity_fp64(ctx, dyn, brt):
     from paper_2507_11542_gb300 import solver
@@ -149,6 +150,19 @@ def test_solve_dubins_full_horizon_fp64_host_io(ctx):
     ts = W.slice_times(2.0, 3)
     got, ref, stats, steps_o, times, times_o = _solve_both(ctx, spec, V0, DUBINS, ts, host_io=True)
     assert stats["steps"] == steps_o
+    for k in range(len(ts)):
+        assert rel_err(got[k], ref[k]) <= TOL64, k
+
+
+@pytest.mark.parametrize("scheme", [2, 5])
+def test_solve_rockets_full_horizon_fp64(ctx, scheme):
+    # the rockets game as the paper runs it (ENO2, BRT with the positive rule,
+    # 11 slices over a 2.5 s horizon) on a coarser grid, and with WENO5
+    spec, V0 = W.rockets(31)
+    ts = W.slice_times(2.5)
+    got, ref, stats, steps_o, times, times_o = _solve_both(ctx, spec, V0, ROCKETS, ts, scheme=scheme)
+    assert stats["steps"] == steps_o > 100
+    np.testing.assert_array_equal(times, times_o)
     for k in range(len(ts)):
         assert rel_err(got[k], ref[k]) <= TOL64, k
 
@@ -206,7 +220,7 @@ def _sample_nodes(spec, rng, k):
 
 @pytest.mark.parametrize("which,dtype", [("air3d", "float64"), ("air3d", "float32"),
                                          ("dubins", "float64"), ("dubins", "float32"),
-                                         ("sphere", "float32")])
+                                         ("sphere", "float32"), ("rockets", "float64"), ("rockets", "float32")])
 def test_full_size_step_sampled(ctx, which, dtype):
     from paper_2507_11542_gb300 import solver
     if which == "air3d":
@@ -215,6 +229,9 @@ def test_full_size_step_sampled(ctx, which, dtype):
     elif which == "dubins":
         spec, V0 = W.dubins4d(81)
         dyn, brt = DUBINS, 1
+    elif which == "rockets":
+        spec, V0 = W.rockets(100)
+        dyn, brt = ROCKETS, 1
     else:
         spec, V0 = W.expanding_sphere(512)
         dyn, brt = NORM, 0

@@ -37,6 +37,18 @@ def _brute_hg(dyn, params, x, p):
         X, Y, th, v = x
         return min(float(np.dot(p, (v * math.cos(th), v * math.sin(th), w, acc)))
                    for w in wmax * U for acc in accmax * U)
+    if dyn == O.DYN_ROCKETS:
+        # Sec. 6.1 game: the evader's thrust ue maximises, the pursuer's up minimises
+        a, g, uemax, upmax = params
+        X, Z, th = x
+        best = -np.inf
+        for ue in uemax * U:
+            worst = np.inf
+            for up in upmax * U:
+                f = (a * math.cos(th) + ue * X, a * math.sin(th) + a - g + up * X, up - ue)
+                worst = min(worst, float(np.dot(p, f)))
+            best = max(best, worst)
+        return best
     raise AssertionError
 
 
@@ -55,6 +67,12 @@ def _brute_alpha(dyn, params, x):
         X, Y, th, v = x
         fs = [(v * math.cos(th), v * math.sin(th), w, acc) for w in wmax * U for acc in accmax * U]
         return list(np.max(np.abs(np.array(fs)), axis=0))
+    if dyn == O.DYN_ROCKETS:
+        a, g, uemax, upmax = params
+        X, Z, th = x
+        fs = [(a * math.cos(th) + ue * X, a * math.sin(th) + a - g + up * X, up - ue)
+              for ue in uemax * U for up in upmax * U]
+        return list(np.max(np.abs(np.array(fs)), axis=0))
     raise AssertionError
 
 
@@ -63,6 +81,8 @@ CASES = [
     (O.DYN_AIR3D, (5.0, 5.0, 1.0, 1.0), 3),
     (O.DYN_AIR3D, (3.0, 4.0, 0.7, 1.3), 3),
     (O.DYN_DUBINS4D, (1.0, 0.5), 4),
+    (O.DYN_ROCKETS, (1.0, 32.0, 1.0, 1.0), 3),
+    (O.DYN_ROCKETS, (1.5, 9.8, 0.7, 1.2), 3),
 ]
 
 
