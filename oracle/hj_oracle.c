@@ -336,16 +336,35 @@ static void node_coords(const orc_grid* g, int64_t idx, double* x) {
     }
 }
 
+/* alpha_max[d] = max over nodes of alpha_d(x): the dissipation of the global
+ * Lax-Friedrichs scheme (the listing of the rockets game names it). */
+int orc_alpha_max(const orc_grid* g, const orc_method* m, double* alpha_max) {
+    if (!grid_ok(g) || !m || !alpha_max) return ORC_EINVAL;
+    int64_t total = orc_num_nodes(g);
+    for (int d = 0; d < 4; ++d) alpha_max[d] = 0.0;
+    for (int64_t idx = 0; idx < total; ++idx) {
+        double x[4], alpha[4];
+        node_coords(g, idx, x);
+        int rc = orc_alpha(m, g->ndim, x, alpha);
+        if (rc) return rc;
+        for (int d = 0; d < g->ndim; ++d)
+            if (alpha[d] > alpha_max[d]) alpha_max[d] = alpha[d];
+    }
+    return 0;
+}
+
 /* Lax-Friedrichs term (Sec. 4, Listing 5) in time-to-go form:
- *   ydot = Hg(x, (p- + p+)/2) + sum_d alpha_d(x) (p+_d - p-_d)/2
- * followed by the BRT clamp min(0, ydot) in ORC_BRT_MIN0 mode (R7). */
+ *   ydot = Hg(x, (p- + p+)/2) + sum_d alpha_d (p+_d - p-_d)/2
+ * with alpha_d = alpha_d(x) (local, R5) or its maximum over the grid
+ * (global), followed by the BRT clamp min(0, ydot) in ORC_BRT_MIN0 mode (R7). */
 int orc_term(const orc_grid* g, const orc_method* m, const double* V, double* ydot) {
     if (!grid_ok(g) || !m || !V || !ydot) return ORC_EINVAL;
     int64_t total = orc_num_nodes(g);
     int D = g->ndim;
     double* pm[4] = {0, 0, 0, 0};
     double* pp[4] = {0, 0, 0, 0};
-    int rc = 0;
+    double amax[4];
+    int rc = m->alpha_global ? orc_alpha_max(g, m, amax) : 0;
     for (int d = 0; d < D && rc == 0; ++d) {
         pm[d] = (double*)malloc(sizeof(double) * (size_t)total);
         pp[d] = (double*)malloc(sizeof(double) * (size_t)total);
@@ -359,6 +378,8 @@ int orc_term(const orc_grid* g, const orc_method* m, const double* V, double* yd
         rc = orc_hamiltonian(m, D, x, pbar, &hg);
         if (rc == 0) rc = orc_alpha(m, D, x, alpha);
         if (rc != 0) break;
+        if (m->alpha_global)
+            for (int d = 0; d < D; ++d) alpha[d] = amax[d];
         double y = hg;
         for (int d = 0; d < D; ++d) y += alpha[d] * (pp[d][idx] - pm[d][idx]) / 2.0;
         if (m->brt == ORC_BRT_MIN0 && y > 0.0) y = 0.0;
@@ -368,9 +389,19 @@ int orc_term(const orc_grid* g, const orc_method* m, const double* V, double* yd
     return rc;
 }
 
-/* CFL bound (Sec. 4): dt * max_x { sum_d |H_{p_d}| / dx_d } < 1. */
+/* CFL bound (Sec. 4): dt * max_x { sum_d |H_{p_d}| / dx_d } < 1; with the
+ * global scheme, sum_d max_x |H_{p_d}| / dx_d. */
 int orc_step_bound_inv(const orc_grid* g, const orc_method* m, double* out) {
     if (!grid_ok(g) || !m || !out) return ORC_EINVAL;
+    if (m->alpha_global) {
+        double amax[4];
+        int rc = orc_alpha_max(g, m, amax);
+        if (rc) return rc;
+        double s = 0.0;
+        for (int d = 0; d < g->ndim; ++d) s += amax[d] / orc_spacing(g, d);
+        *out = s;
+        return 0;
+    }
     int64_t total = orc_num_nodes(g);
     double best = 0.0;
     for (int64_t idx = 0; idx < total; ++idx) {
@@ -419,6 +450,41 @@ int orc_rk3_step(const orc_grid* g, const orc_method* m, double dt, double* V) {
     return rc;
 }
 
+/* Forward Euler and the two-stage Shu-Osher scheme (Sec. 5 names the TVD-RK
+ * family; third order is the default):
+ *   order 1:  Vnew = V + dt L(V)
+ *   order 2:  V1 = V + dt L(V);  V2 = V1 + dt L(V1);  Vnew = (V + V2) / 2
+ * ORC_BRT_MINV then keeps min(Vnew, V) (R7). */
+int orc_rk_step(const orc_grid* g, const orc_method* m, double dt, double* V) {
+    if (!grid_ok(g) || !m || !V) return ORC_EINVAL;
+    int order = m->order == 0 ? 3 : m->order;
+    if (order == 3) return orc_rk3_step(g, m, dt, V);
+    if (order != 1 && order != 2) return ORC_EINVAL;
+    int64_t total = orc_num_nodes(g);
+    size_t bytes = sizeof(double) * (size_t)total;
+    double* V0 = (double*)malloc(bytes);
+    double* U = (double*)malloc(bytes);
+    double* ydot = (double*)malloc(bytes);
+    if (!V0 || !U || !ydot) { free(V0); free(U); free(ydot); return ORC_ENOMEM; }
+    memcpy(V0, V, bytes);
+    int rc = orc_term(g, m, V0, ydot);
+    for (int64_t i = 0; i < total && rc == 0; ++i) U[i] = V0[i] + dt * ydot[i];
+    if (rc == 0 && order == 2) {
+        rc = orc_term(g, m, U, ydot);
+        for (int64_t i = 0; i < total && rc == 0; ++i) {
+            double v2 = U[i] + dt * ydot[i];
+            U[i] = (V0[i] + v2) / 2.0;
+        }
+    }
+    for (int64_t i = 0; i < total && rc == 0; ++i) {
+        double vn = U[i];
+        if (m->brt == ORC_BRT_MINV && V0[i] < vn) vn = V0[i];
+        V[i] = vn;
+    }
+    free(V0); free(U); free(ydot);
+    return rc;
+}
+
 double orc_time_eps(void) { return 100.0 * DBL_EPSILON; }
 
 /* Time loop (Sec. 5, Listing 6), R6: per slice, step while
@@ -450,7 +516,7 @@ int orc_solve(const orc_grid* g, const orc_method* m, const double* V0, int n_sl
             double dt = ts - t;
             if (m->max_step < dt) dt = m->max_step;
             if (m->cfl * step_bound < dt) dt = m->cfl * step_bound;
-            rc = orc_rk3_step(g, m, dt, V);
+            rc = orc_rk_step(g, m, dt, V);
             t += dt;
             ++steps;
         }

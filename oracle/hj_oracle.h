@@ -63,6 +63,8 @@ typedef struct {
     int weno_ideal;      /* test hook: 1 = WENO5 with the ideal weights (0.1, 0.6, 0.3) */
     double cfl;          /* CFL factor (0.8) */
     double max_step;     /* upper bound on dt (use +inf for none) */
+    int order;           /* TVD-RK order of a time step: 1, 2 or 3 (0 means 3) */
+    int alpha_global;    /* 1: global Lax-Friedrichs, alpha_d = max over the grid of alpha_d(x) */
 } orc_method;
 
 int64_t orc_num_nodes(const orc_grid* g);
@@ -97,6 +99,11 @@ int orc_step_bound_inv(const orc_grid* g, const orc_method* m, double* out);
 
 /* One TVD-RK3 step of size dt, in place (Sec. 5, Listing 6). */
 int orc_rk3_step(const orc_grid* g, const orc_method* m, double dt, double* V);
+/* One TVD-RK step of the method's order (Sec. 5: forward Euler, the
+ * two-stage and the three-stage Shu-Osher schemes). */
+int orc_rk_step(const orc_grid* g, const orc_method* m, double dt, double* V);
+/* alpha_max[d] = max over the grid's nodes of alpha_d(x) (global LF). */
+int orc_alpha_max(const orc_grid* g, const orc_method* m, double* alpha_max);
 
 /* Integrate V0 from tau = 0 through each slice time; out has n_slices*prod(n)
  * doubles. out_steps (may be NULL) receives the number of RK3 steps taken,

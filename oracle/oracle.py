@@ -52,7 +52,8 @@ class _Grid(ctypes.Structure):
 class _Method(ctypes.Structure):
     _fields_ = [("scheme", ctypes.c_int), ("dynamics", ctypes.c_int), ("params", ctypes.c_double * 8),
                 ("brt", ctypes.c_int), ("extrap", ctypes.c_int), ("weno_ideal", ctypes.c_int),
-                ("cfl", ctypes.c_double), ("max_step", ctypes.c_double)]
+                ("cfl", ctypes.c_double), ("max_step", ctypes.c_double), ("order", ctypes.c_int),
+                ("alpha_global", ctypes.c_int)]
 
 
 _DP = ctypes.POINTER(ctypes.c_double)
@@ -77,6 +78,8 @@ def lib():
             L.orc_term.argtypes = [P(_Grid), P(_Method), _DP, _DP]
             L.orc_step_bound_inv.argtypes = [P(_Grid), P(_Method), _DP]
             L.orc_rk3_step.argtypes = [P(_Grid), P(_Method), ctypes.c_double, _DP]
+            L.orc_rk_step.argtypes = [P(_Grid), P(_Method), ctypes.c_double, _DP]
+            L.orc_alpha_max.argtypes = [P(_Grid), P(_Method), _DP]
             L.orc_solve.argtypes = [P(_Grid), P(_Method), _DP, ctypes.c_int, _DP, _DP,
                                     P(ctypes.c_int64), _DP]
             L.orc_time_eps.restype = ctypes.c_double
@@ -99,7 +102,8 @@ def _grid(g) -> _Grid:
 
 
 def method(scheme=WENO5, dynamics=DYN_DOUBLE_INTEGRATOR, params=(), brt=BRT_MIN0,
-           extrap=EXTRAP_AWAY_FROM_ZERO, weno_ideal=False, cfl=0.8, max_step=float("inf")) -> _Method:
+           extrap=EXTRAP_AWAY_FROM_ZERO, weno_ideal=False, cfl=0.8, max_step=float("inf"), order=3,
+           alpha_global=False) -> _Method:
     M = _Method()
     M.scheme = scheme
     M.dynamics = dynamics
@@ -110,6 +114,8 @@ def method(scheme=WENO5, dynamics=DYN_DOUBLE_INTEGRATOR, params=(), brt=BRT_MIN0
     M.weno_ideal = 1 if weno_ideal else 0
     M.cfl = float(cfl)
     M.max_step = float(max_step)
+    M.order = int(order)
+    M.alpha_global = 1 if alpha_global else 0
     return M
 
 
@@ -199,6 +205,19 @@ def rk3_step(g, m: _Method, V, dt: float) -> np.ndarray:
     W = np.array(_f64(V, g.n), order="F", copy=True)
     _check(lib().orc_rk3_step(ctypes.byref(_grid(g)), ctypes.byref(m), float(dt), _ptr(W)), "rk3_step")
     return W
+
+
+def rk_step(g, m: _Method, V, dt: float) -> np.ndarray:
+    """One TVD-RK step of the method's order (1, 2 or 3)."""
+    W = np.array(_f64(V, g.n), order="F", copy=True)
+    _check(lib().orc_rk_step(ctypes.byref(_grid(g)), ctypes.byref(m), float(dt), _ptr(W)), "rk_step")
+    return W
+
+
+def alpha_max(g, m: _Method) -> np.ndarray:
+    out = np.zeros(4)
+    _check(lib().orc_alpha_max(ctypes.byref(_grid(g)), ctypes.byref(m), _ptr(out)), "alpha_max")
+    return out[:len(g.n)]
 
 
 def solve(g, m: _Method, V0, slice_times):

@@ -13,6 +13,7 @@ import numpy as np
 import pytest
 
 from oracle import oracle as O
+from paper_2507_11542_gb300 import workloads as W
 
 U = np.linspace(-1.0, 1.0, 41)  # controls, endpoints included
 
@@ -198,6 +199,56 @@ def test_rk3_of_linear_operator_is_taylor_polynomial():
     A = dt * L
     taylor = V + A @ V + A @ (A @ V) / 2 + A @ (A @ (A @ V)) / 6
     np.testing.assert_allclose(O.rk3_step(g, m, V, dt), taylor, rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("order", [1, 2, 3])
+def test_rk_orders_of_linear_operator_are_taylor_polynomials(order):
+    # forward Euler, the two-stage and the three-stage Shu-Osher schemes applied
+    # to V' = L V (L linear) equal the Taylor polynomial of exp(dt L) of their order
+    n, c, dt = 24, 0.9, 0.013
+    g = Line(n)
+    dx = 1.0 / n
+    L = -c * (np.eye(n) - np.roll(np.eye(n), -1, axis=1)) / dx
+    rng = np.random.default_rng(5)
+    V = rng.normal(size=n)
+    m = O.method(scheme=O.ENO1, dynamics=O.DYN_ADVECT, params=(c,), brt=O.BRT_NONE, order=order)
+    A = dt * L
+    terms, T = [V], V
+    for k in range(1, order + 1):
+        T = A @ T / k
+        terms.append(T)
+    np.testing.assert_allclose(O.rk_step(g, m, V, dt), sum(terms), rtol=1e-12, atol=1e-12)
+    # and they differ from each other at the next order
+    if order < 3:
+        higher = O.rk_step(g, O.method(scheme=O.ENO1, dynamics=O.DYN_ADVECT, params=(c,), brt=O.BRT_NONE,
+                                       order=order + 1), V, dt)
+        assert np.max(np.abs(higher - sum(terms))) > 1e-8
+
+
+def test_global_lax_friedrichs_uses_the_grid_maximum():
+    # double integrator on [-1, 1]^2: alpha = (|x1|, umax), so the global
+    # alpha is (1, umax) (|x1| = 1 on the edge rows); on the rows x1 = +-1
+    # local and global terms coincide, elsewhere the global one adds
+    # (1 - |x1|) (p+_0 - p-_0) / 2
+    g = W.GridSpec((21, 17), (-1.0, -1.0), (1.0, 1.0))
+    rng = np.random.default_rng(6)
+    V = np.asfortranarray(rng.normal(size=g.n))
+    loc = O.method(dynamics=O.DYN_DOUBLE_INTEGRATOR, params=(0.7,), brt=O.BRT_NONE)
+    glo = O.method(dynamics=O.DYN_DOUBLE_INTEGRATOR, params=(0.7,), brt=O.BRT_NONE, alpha_global=True)
+    np.testing.assert_array_equal(O.alpha_max(g, loc), [1.0, 0.7])
+    yl, yg = O.term(g, loc, V), O.term(g, glo, V)
+    np.testing.assert_array_equal(yl[:, 0], yg[:, 0])
+    np.testing.assert_array_equal(yl[:, -1], yg[:, -1])
+    pm, pp = O.upwind(g, loc, V, 0)
+    x1 = np.linspace(-1.0, 1.0, 17)[None, :]
+    np.testing.assert_allclose(yg - yl, (1.0 - np.abs(x1)) * (pp - pm) / 2, rtol=0, atol=1e-12)
+    # CFL bound of the global scheme: sum_d max alpha_d / dx_d = 1/0.1 + 0.7/0.125
+    assert O.step_bound_inv(g, glo) == pytest.approx(1.0 / 0.1 + 0.7 / 0.125, rel=1e-15)
+    # air3D (va = vb = 5, |a|, |b| <= 1) on a grid holding psi = pi and |y| = 10:
+    # max alpha = (|-5 + 5 cos psi| + 10, 5 |sin psi| + 20, 2) = (20, 25, 2)
+    ga = W.GridSpec((27, 21, 8), (-6.0, -10.0, 0.0), (20.0, 10.0, 2 * np.pi), (2,))
+    ma = O.method(dynamics=O.DYN_AIR3D, params=(5.0, 5.0, 1.0, 1.0), alpha_global=True)
+    np.testing.assert_allclose(O.alpha_max(ga, ma), [20.0, 25.0, 2.0], rtol=1e-15)
 
 
 def test_brt_minv_keeps_the_pointwise_minimum():
