@@ -84,6 +84,11 @@ enum { HJ_F32 = 1, HJ_F64 = 2 };
  * g_m = v_0 + m |v_0 - v_1| sign(v_0), or the plain signed slope v_0 - v_1. */
 enum { HJ_EXTRAP_AWAY_FROM_ZERO = 0, HJ_EXTRAP_LINEAR = 1 };
 
+/* Lax-Friedrichs dissipation (Sec. 4): alpha_d(x) at each node (the default),
+ * or its maximum over the grid (global LF, the rockets listing's
+ * artificialDissipationGLF); the CFL bound is then sum_d max_x alpha_d / dx_d. */
+enum { HJ_ALPHA_NODE = 0, HJ_ALPHA_GLOBAL = 1 };
+
 /* A dense Cartesian grid (Sec. 2.1, Listing 1: createGrid(min, max, N, pdim)).
  * ndim in 1..4; n[d] >= 2 for an extrapolated dimension, >= 1 for a periodic
  * one. A periodic dimension covers [lo, hi) with spacing (hi-lo)/n, any other
@@ -105,6 +110,8 @@ typedef struct hj_method {
     int32_t extrap;    /* HJ_EXTRAP_* */
     double cfl;        /* CFL factor in (0, 1]; Sec. 4-5 (0.8 in the workloads) */
     double max_step;   /* upper bound on dt; +inf for none (Listing 6 maxStep) */
+    int32_t order;     /* TVD-RK order of a time step: 1 (forward Euler), 2 or 3 (Shu-Osher); 0 means 3 */
+    int32_t alpha_mode;/* HJ_ALPHA_NODE or HJ_ALPHA_GLOBAL */
 } hj_method;
 
 /* One reachability / level-set solve (Sec. 5, Listing 6: odeCFL3(func, tspan, v0)). */
@@ -165,9 +172,10 @@ hj_status hj_term(hj_ctx* ctx, const hj_grid* grid, const hj_method* method, int
  * Errors: HJ_EINVAL, HJ_ECUDA. */
 hj_status hj_step_bound(hj_ctx* ctx, const hj_grid* grid, const hj_method* method, double* out);
 
-/* One TVD-RK3 step of size dt (Sec. 5, Listing 6), in place on the device
- * array v: three fused stage kernels (upwind + Hamiltonian + dissipation +
- * BRT rule + stage combination). Stage buffers come from the context.
+/* One TVD-RK step of size dt (Sec. 5, Listing 6) of the method's order
+ * (three stages by default), in place on the device array v: one fused stage
+ * kernel per stage (upwind + Hamiltonian + dissipation + BRT rule + stage
+ * combination). Stage buffers come from the context.
  * Asynchronous. Errors: HJ_EINVAL (dt < 0 or not finite, ...), HJ_ENOMEM, HJ_ECUDA. */
 hj_status hj_rk3_step(hj_ctx* ctx, const hj_grid* grid, const hj_method* method, int32_t dtype,
                       void* v, double dt);
@@ -199,7 +207,8 @@ hj_status hj_solve(hj_ctx* ctx, const hj_problem* problem, void* out_slices, int
  * host memory), its slice times to out_times[i] (may be NULL, or out_times
  * itself NULL) and its statistics to stats[i] (stats may be NULL).
  * WENO5 instances of the row kernel's (dimension, dynamics) pairs with
- * n0 < 1024 (FP32) or n0 < 512 (FP64) advance together: one launch per RK
+ * n0 < 1024 (FP32) or n0 < 512 (FP64), the three-stage scheme and per-node
+ * dissipation advance together: one launch per RK
  * stage and (element type, dimension, dynamics) group covers every tile of
  * every active instance, a small kernel advances each instance's own dt and
  * slice cursor, and blocks of steps replay as CUDA graphs. Other problems are
@@ -291,8 +300,10 @@ void hj_server_destroy(hj_server* srv);
  *    on the GPU (e.g. on two streams at once) race on it; serialise them.
  *  - Asynchronous: returns after enqueueing.
  * Errors: HJ_EINVAL for a malformed argument, for prod(n) > HJ_STATIC_MAX_NODES,
- * or for more than HJ_STATIC_MAX_ANGLES nodes along dimension 2 with air3D or
- * Dubins4D dynamics (nothing is enqueued); HJ_ECUDA if a CUDA call fails. */
+ * for more than HJ_STATIC_MAX_ANGLES nodes along dimension 2 with air3D,
+ * Dubins4D or rockets dynamics, or for a method other than the three-stage
+ * scheme with per-node dissipation (nothing is enqueued); HJ_ECUDA if a CUDA
+ * call fails. */
 hj_status hj_rk3_step_static(void* cuda_stream, int32_t device, const hj_grid* grid, const hj_method* method,
                              int32_t dtype, void* v, double dt);
 

@@ -28,6 +28,7 @@ HJ_ENO1, HJ_ENO2, HJ_ENO3, HJ_WENO5 = 1, 2, 3, 5
 HJ_BRT_NONE, HJ_BRT_MIN0, HJ_BRT_MINV = 0, 1, 2
 HJ_F32, HJ_F64 = 1, 2
 HJ_EXTRAP_AWAY_FROM_ZERO, HJ_EXTRAP_LINEAR = 0, 1
+HJ_ALPHA_NODE, HJ_ALPHA_GLOBAL = 0, 1
 
 # every function include/hj.h declares (checked by the test-suite against the .so)
 EXPORTS = ["hj_ctx_create", "hj_ctx_destroy", "hj_status_str", "hj_ctx_last_error", "hj_version",
@@ -49,7 +50,7 @@ class hj_grid(ctypes.Structure):
 class hj_method(ctypes.Structure):
     _fields_ = [("scheme", ctypes.c_int32), ("dynamics", ctypes.c_int32), ("params", ctypes.c_double * 8),
                 ("brt", ctypes.c_int32), ("extrap", ctypes.c_int32), ("cfl", ctypes.c_double),
-                ("max_step", ctypes.c_double)]
+                ("max_step", ctypes.c_double), ("order", ctypes.c_int32), ("alpha_mode", ctypes.c_int32)]
 
 
 class hj_problem(ctypes.Structure):
@@ -162,7 +163,8 @@ def make_grid(spec) -> hj_grid:
 
 
 def make_method(scheme=HJ_WENO5, dynamics=HJ_DYN_DOUBLE_INTEGRATOR, params=(), brt=HJ_BRT_MIN0,
-                extrap=HJ_EXTRAP_AWAY_FROM_ZERO, cfl=0.8, max_step=math.inf) -> hj_method:
+                extrap=HJ_EXTRAP_AWAY_FROM_ZERO, cfl=0.8, max_step=math.inf, order=3,
+                alpha_mode=HJ_ALPHA_NODE) -> hj_method:
     m = hj_method()
     m.scheme = scheme
     m.dynamics = dynamics
@@ -172,6 +174,8 @@ def make_method(scheme=HJ_WENO5, dynamics=HJ_DYN_DOUBLE_INTEGRATOR, params=(), b
     m.extrap = extrap
     m.cfl = float(cfl)
     m.max_step = float(max_step)
+    m.order = int(order)
+    m.alpha_mode = int(alpha_mode)
     return m
 
 

@@ -102,7 +102,8 @@ hj_status Engine::init(hj_ctx* ctx, cudaStream_t stream, int max_slots, size_t a
 
 bool Engine::eligible(const hj_problem* p) {
     const GridDev G = make_grid(&p->grid, p->method.extrap);
-    return rows_eligible(G, p->method.scheme, p->method.dynamics, p->dtype) &&
+    const bool rk3_node = (p->method.order == 0 || p->method.order == 3) && p->method.alpha_mode == HJ_ALPHA_NODE;
+    return rk3_node && rows_eligible(G, p->method.scheme, p->method.dynamics, p->dtype) &&
            G.n[0] + 1 <= max_block_threads(p->dtype);
 }
 
@@ -179,7 +180,7 @@ hj_status Engine::admit(const hj_problem* p, void* out, bool out_on_device, doub
                         : launch_nonfinite_f32(reinterpret_cast<const float*>(A + S.o_v), S.N, reinterpret_cast<int*>(w + 1), stream_);
     if (e == cudaSuccess)
         e = launch_step_bound(S.G, p->method.dynamics, p->method.params,
-                              S.angles ? reinterpret_cast<const double*>(A + S.o_td) : nullptr, w, stream_);
+                              S.angles ? reinterpret_cast<const double*>(A + S.o_td) : nullptr, w, 0, stream_);
     launches += 2;
     ctx_->launches += 2;
     if (e != cudaSuccess) return cuda_fail(ctx_, e, "admission launch");

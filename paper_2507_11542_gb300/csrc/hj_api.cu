@@ -66,6 +66,9 @@ hj_status check_method(hj_ctx* ctx, const hj_grid* g, const hj_method* m) {
         return fail(ctx, HJ_EINVAL, "unknown extrapolation %d", m->extrap);
     for (int k = 0; k < 8; ++k)
         if (!std::isfinite(m->params[k])) return fail(ctx, HJ_EINVAL, "params[%d] is not finite", k);
+    if (m->order < 0 || m->order > 3) return fail(ctx, HJ_EINVAL, "order %d not in 1..3 (0 = 3)", m->order);
+    if (m->alpha_mode != HJ_ALPHA_NODE && m->alpha_mode != HJ_ALPHA_GLOBAL)
+        return fail(ctx, HJ_EINVAL, "unknown alpha_mode %d", m->alpha_mode);
     const int D = g->ndim;
     const double* q = m->params;
     switch (m->dynamics) {
@@ -458,6 +461,38 @@ cudaError_t launch_stage(hj_ctx* ctx, const StageParams& P, int scheme, int dtyp
 // Three fused stage launches of one TVD-RK3 step (Listing 6):
 //   V1 = V + dt L(V);  V2 = 3/4 V + 1/4 (V1 + dt L(V1));  V <- 1/3 V + 2/3 (V2 + dt L(V2))
 // with V <- min(V_new, V_old) in the last stage for the BRT min-V rule.
+hj_status rk3_launch(hj_ctx* ctx, StageParams P, int scheme, int dtype, int brt, void* v, double dt);
+
+// One TVD-RK step of order 1, 2 or 3 (0 = 3), in place on v:
+//   1: v <- v + dt L(v)                              (one launch, then a copy)
+//   2: V1 = v + dt L(v);  v <- 1/2 v + 1/2 (V1 + dt L(V1))
+//   3: rk3_launch
+// with v <- min(v_new, v_old) for the BRT min-V rule.
+hj_status rk_launch(hj_ctx* ctx, const StageParams& P0, int scheme, int dtype, int brt, int order, void* v,
+                    double dt, size_t bytes) {
+    if (order == 0 || order == 3) return rk3_launch(ctx, P0, scheme, dtype, brt, v, dt);
+    StageParams P = P0;
+    P.mode = kStage;
+    P.dt = dt;
+    if (order == 1) {
+        P.u = v; P.out = ctx->work[0]; P.cv = 0.0; P.cu = 1.0;
+        P.minv_after = (brt == HJ_BRT_MINV);
+        P.vn = P.minv_after ? v : nullptr;
+        cudaError_t e = launch_stage(ctx, P, scheme, dtype);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "stage launch");
+        HJ_CUDA(ctx, cudaMemcpyAsync(v, ctx->work[0], bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+        return HJ_OK;
+    }
+    P.u = v; P.vn = nullptr; P.out = ctx->work[0]; P.cv = 0.0; P.cu = 1.0; P.minv_after = 0;
+    cudaError_t e = launch_stage(ctx, P, scheme, dtype);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "stage 1 launch");
+    P.u = ctx->work[0]; P.vn = v; P.out = v; P.cv = 0.5; P.cu = 0.5;
+    P.minv_after = (brt == HJ_BRT_MINV);
+    e = launch_stage(ctx, P, scheme, dtype);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "stage 2 launch");
+    return HJ_OK;
+}
+
 hj_status rk3_launch(hj_ctx* ctx, StageParams P, int scheme, int dtype, int brt, void* v, double dt) {
     P.mode = kStage;
     P.dt = dt;
@@ -474,12 +509,43 @@ hj_status rk3_launch(hj_ctx* ctx, StageParams P, int scheme, int dtype, int brt,
     return HJ_OK;
 }
 
+// alpha_max[d] = max over the grid of alpha_d(x) (global Lax-Friedrichs).
+// Synchronises the stream.
+hj_status alpha_max(hj_ctx* ctx, const hj_grid* g, const hj_method* m, double* amax) {
+    hj_status st = upload_trig(ctx, g, m->dynamics);
+    if (st) return st;
+    const GridDev G = make_grid(g, m->extrap);
+    unsigned long long* acc = ctx->aux + 2;
+    HJ_CUDA(ctx, cudaMemsetAsync(acc, 0, 4 * sizeof(unsigned long long), ctx->stream));
+    cudaError_t e = launch_step_bound(G, m->dynamics, m->params, ctx->trig_d, acc, 1, ctx->stream);
+    ctx->launches += 1;
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "alpha maximum launch");
+    unsigned long long bits[4] = {0, 0, 0, 0};
+    HJ_CUDA(ctx, cudaMemcpyAsync(bits, acc, sizeof bits, cudaMemcpyDeviceToHost, ctx->stream));
+    HJ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int d = 0; d < 4; ++d) std::memcpy(&amax[d], &bits[d], sizeof(double));
+    for (int d = G.ndim; d < 4; ++d) amax[d] = 0.0;
+    return HJ_OK;
+}
+
+// CFL bound: max over nodes of sum_d alpha_d(x)/dx_d, or with global
+// dissipation sum_d max_x alpha_d / dx_d (left to right, as the oracle).
 hj_status step_bound(hj_ctx* ctx, const hj_grid* g, const hj_method* m, double* out) {
+    if (m->alpha_mode == HJ_ALPHA_GLOBAL) {
+        double amax[4];
+        hj_status st = alpha_max(ctx, g, m, amax);
+        if (st) return st;
+        const GridDev G = make_grid(g, m->extrap);
+        double s = 0.0;
+        for (int d = 0; d < G.ndim; ++d) s += amax[d] / G.dx[d];
+        *out = s;
+        return HJ_OK;
+    }
     hj_status st = upload_trig(ctx, g, m->dynamics);
     if (st) return st;
     const GridDev G = make_grid(g, m->extrap);
     HJ_CUDA(ctx, cudaMemsetAsync(ctx->aux, 0, sizeof(unsigned long long), ctx->stream));
-    cudaError_t e = launch_step_bound(G, m->dynamics, m->params, ctx->trig_d, ctx->aux, ctx->stream);
+    cudaError_t e = launch_step_bound(G, m->dynamics, m->params, ctx->trig_d, ctx->aux, 0, ctx->stream);
     ctx->launches += 1;
     if (e != cudaSuccess) return cuda_fail(ctx, e, "step bound launch");
     unsigned long long bits = 0;
@@ -488,6 +554,19 @@ hj_status step_bound(hj_ctx* ctx, const hj_grid* g, const hj_method* m, double* 
     double v;
     std::memcpy(&v, &bits, sizeof v);
     *out = v;
+    return HJ_OK;
+}
+
+// The launch parameters of a method on a grid: with global dissipation, the
+// grid maxima of alpha (one reduction).
+hj_status method_params(hj_ctx* ctx, const hj_grid* g, const GridDev& G, const hj_method* m, int dtype,
+                        StageParams* P) {
+    *P = stage_params(ctx, G, m, dtype);
+    if (m->alpha_mode == HJ_ALPHA_GLOBAL) {
+        hj_status st = alpha_max(ctx, g, m, P->alpha_g);
+        if (st) return st;
+        P->alpha_global = 1;
+    }
     return HJ_OK;
 }
 
@@ -608,7 +687,8 @@ hj_status hj_term(hj_ctx* ctx, const hj_grid* grid, const hj_method* method, int
     if (!v || !ydot) return fail(ctx, HJ_EINVAL, "NULL array");
     DeviceGuard guard(ctx->device);
     if ((st = upload_trig(ctx, grid, method->dynamics))) return st;
-    StageParams P = stage_params(ctx, make_grid(grid, method->extrap), method, dtype);
+    StageParams P;
+    if ((st = method_params(ctx, grid, make_grid(grid, method->extrap), method, dtype, &P))) return st;
     P.mode = kTerm;
     P.u = v;
     P.out = ydot;
@@ -640,8 +720,10 @@ hj_status hj_rk3_step(hj_ctx* ctx, const hj_grid* grid, const hj_method* method,
     const GridDev G = make_grid(grid, method->extrap);
     if ((st = ensure_work(ctx, (size_t)G.total * elem_size(dtype)))) return st;
     if ((st = upload_trig(ctx, grid, method->dynamics))) return st;
-    StageParams P = stage_params(ctx, G, method, dtype);
-    return rk3_launch(ctx, P, method->scheme, dtype, method->brt, v, dt);
+    StageParams P;
+    if ((st = method_params(ctx, grid, G, method, dtype, &P))) return st;
+    return rk_launch(ctx, P, method->scheme, dtype, method->brt, method->order, v, dt,
+                     (size_t)G.total * elem_size(dtype));
 }
 
 hj_status hj_rk3_stage(hj_ctx* ctx, const hj_grid* grid, const hj_method* method, int32_t dtype, int32_t stage,
@@ -657,7 +739,8 @@ hj_status hj_rk3_stage(hj_ctx* ctx, const hj_grid* grid, const hj_method* method
     if (!(dt >= 0.0) || !std::isfinite(dt)) return fail(ctx, HJ_EINVAL, "dt must be finite and >= 0");
     DeviceGuard guard(ctx->device);
     if ((st = upload_trig(ctx, grid, method->dynamics))) return st;
-    StageParams P = stage_params(ctx, make_grid(grid, method->extrap), method, dtype);
+    StageParams P;
+    if ((st = method_params(ctx, grid, make_grid(grid, method->extrap), method, dtype, &P))) return st;
     P.mode = kStage;
     P.dt = dt;
     P.u = u;
@@ -698,14 +781,17 @@ hj_status hj_solve(hj_ctx* ctx, const hj_problem* pr, void* out_slices, int32_t 
     if (bad) return fail(ctx, HJ_ENONFINITE, "v0 holds NaN or Inf");
     double sbi = 0.0;
     if ((st = step_bound(ctx, &pr->grid, &pr->method, &sbi))) return st;  // also uploads the angle tables
-    StageParams P = stage_params(ctx, G, &pr->method, pr->dtype);
+    StageParams P;
+    if ((st = method_params(ctx, &pr->grid, G, &pr->method, pr->dtype, &P))) return st;
     Schedule S;
     plan_schedule(&pr->method, sbi, pr->n_slices, pr->slice_times, &S);
     const cudaMemcpyKind out_kind = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     size_t k = 0;
     for (int s = 0; s < pr->n_slices; ++s) {
         for (; k < (size_t)S.slice_steps[s]; ++k)
-            if ((st = rk3_launch(ctx, P, pr->method.scheme, pr->dtype, pr->method.brt, V, S.dts[k]))) return st;
+            if ((st = rk_launch(ctx, P, pr->method.scheme, pr->dtype, pr->method.brt, pr->method.order, V, S.dts[k],
+                                bytes)))
+                return st;
         HJ_CUDA(ctx, cudaMemcpyAsync(static_cast<char*>(out_slices) + (size_t)s * bytes, V, bytes, out_kind,
                                      ctx->stream));
         if (out_times) out_times[s] = S.slice_t[s];

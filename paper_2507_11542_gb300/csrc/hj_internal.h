@@ -55,8 +55,10 @@ struct StageParams {
     const float* trig_f;
     double weno_floor;     // additive floor of the WENO5 epsilon, in raw-difference units
     double half_inv_dx[kMaxDim];  // 1 / (2 dx): raw differences to (p- + p+)/2 and (p+ - p-)/2
+    int alpha_global;             // dissipation alpha_d = alpha_g[d] (global LF) instead of alpha_d(x)
+    double alpha_g[kMaxDim];
     // FP32 copies of the scalars above, so that FP32 kernels do no FP64 arithmetic
-    float lo_f[kMaxDim], dx_f[kMaxDim], inv_dx_f[kMaxDim], half_inv_dx_f[kMaxDim];
+    float lo_f[kMaxDim], dx_f[kMaxDim], inv_dx_f[kMaxDim], half_inv_dx_f[kMaxDim], alpha_g_f[kMaxDim];
     float params_f[8];
     float dt_f, cv_f, cu_f, weno_floor_f;
     int has_vn;            // the stage reads Vn (cv != 0 or minv_after)
@@ -70,6 +72,7 @@ inline StageParams finalize(StageParams p) {
         p.inv_dx_f[d] = (float)p.g.inv_dx[d];
         p.half_inv_dx[d] = 0.5 * p.g.inv_dx[d];
         p.half_inv_dx_f[d] = (float)p.half_inv_dx[d];
+        p.alpha_g_f[d] = (float)p.alpha_g[d];
     }
     for (int k = 0; k < 8; ++k) p.params_f[k] = (float)p.params[k];
     p.dt_f = (float)p.dt;
@@ -188,7 +191,7 @@ cudaError_t launch_batch_advance(BatchInst* insts, int n, cudaStream_t s);
 // max over nodes of sum_d alpha_d(x)/dx_d, as the FP64 bit pattern, atomically
 // max-ed into *acc (which the caller zeroes first).
 cudaError_t launch_step_bound(const GridDev& g, int dynamics, const double* params, const double* trig_d,
-                              unsigned long long* acc, cudaStream_t s);
+                              unsigned long long* acc, int per_dim, cudaStream_t s);
 // Sets *flag to 1 if any of the n elements is NaN or +-Inf.
 cudaError_t launch_nonfinite_f64(const double* v, long long n, int* flag, cudaStream_t s);
 cudaError_t launch_nonfinite_f32(const float* v, long long n, int* flag, cudaStream_t s);

@@ -7,13 +7,14 @@
 
 namespace hj {
 
-// alpha_d(x)/dx_d summed over d, in FP64, with every product and sum rounded
-// separately in the order alpha_0/dx_0 + alpha_1/dx_1 + ..., so that the bound
-// equals the plain left-to-right evaluation bit for bit.
-__device__ double node_bound(const GridDev& g, int dyn, const double* q, const double* trig, const int* idx) {
+// alpha_d(x), the maximum over the controls of |f_d| at the node, in FP64
+// with every product and sum rounded separately (the plain left-to-right
+// evaluation, bit for bit).
+__device__ void node_alpha(const GridDev& g, int dyn, const double* q, const double* trig, const int* idx,
+                           double* a) {
     double x[4];
     for (int d = 0; d < g.ndim; ++d) x[d] = __dadd_rn(g.lo[d], __dmul_rn((double)idx[d], g.dx[d]));
-    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int d = 0; d < 4; ++d) a[d] = 0.0;
     switch (dyn) {
     case HJ_DYN_DOUBLE_INTEGRATOR:
         a[0] = fabs(x[1]);
@@ -54,6 +55,12 @@ __device__ double node_bound(const GridDev& g, int dyn, const double* q, const d
     default:
         break;
     }
+}
+
+// alpha_d(x)/dx_d summed over d in the order alpha_0/dx_0 + alpha_1/dx_1 + ...
+__device__ double node_bound(const GridDev& g, int dyn, const double* q, const double* trig, const int* idx) {
+    double a[4];
+    node_alpha(g, dyn, q, trig, idx, a);
     double s = 0.0;
     for (int d = 0; d < g.ndim; ++d) s = __dadd_rn(s, __ddiv_rn(a[d], g.dx[d]));
     return s;
@@ -62,37 +69,52 @@ __device__ double node_bound(const GridDev& g, int dyn, const double* q, const d
 struct BoundArgs {
     GridDev g;
     int dyn;
+    int per_dim;  // 0: max over nodes of the sum (one word); 1: max over nodes of each alpha_d (ndim words)
     double q[8];
     const double* trig;
     unsigned long long* acc;
 };
 
+__device__ __forceinline__ double block_max(double v, double* scratch) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();  // scratch is reused across calls
+    if ((threadIdx.x & 31) == 0) scratch[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double b = scratch[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) b = fmax(b, scratch[w]);
+    return b;
+}
+
 __global__ void __launch_bounds__(256) step_bound_kernel(const BoundArgs A) {
-    double best = 0.0;
+    double best[4] = {0.0, 0.0, 0.0, 0.0};
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long flat = (long long)blockIdx.x * blockDim.x + threadIdx.x; flat < A.g.total; flat += stride) {
         int idx[4] = {0, 0, 0, 0};
         long long r = flat;
         for (int d = 0; d < A.g.ndim; ++d) { idx[d] = (int)(r % A.g.n[d]); r /= A.g.n[d]; }
-        best = fmax(best, node_bound(A.g, A.dyn, A.q, A.trig, idx));
+        if (A.per_dim) {
+            double a[4];
+            node_alpha(A.g, A.dyn, A.q, A.trig, idx, a);
+            for (int d = 0; d < 4; ++d) best[d] = fmax(best[d], a[d]);
+        } else {
+            best[0] = fmax(best[0], node_bound(A.g, A.dyn, A.q, A.trig, idx));
+        }
     }
-    for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
     __shared__ double warp_best[8];
-    if ((threadIdx.x & 31) == 0) warp_best[threadIdx.x >> 5] = best;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double b = warp_best[0];
-        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) b = fmax(b, warp_best[w]);
+    const int words = A.per_dim ? A.g.ndim : 1;
+    for (int d = 0; d < words; ++d) {
+        const double b = block_max(best[d], warp_best);
         // non-negative doubles order like their bit patterns
-        atomicMax(A.acc, (unsigned long long)__double_as_longlong(b));
+        if (threadIdx.x == 0) atomicMax(A.acc + d, (unsigned long long)__double_as_longlong(b));
     }
 }
 
 cudaError_t launch_step_bound(const GridDev& g, int dynamics, const double* params, const double* trig_d,
-                              unsigned long long* acc, cudaStream_t s) {
+                              unsigned long long* acc, int per_dim, cudaStream_t s) {
     BoundArgs A;
     A.g = g;
     A.dyn = dynamics;
+    A.per_dim = per_dim;
     for (int k = 0; k < 8; ++k) A.q[k] = params[k];
     A.trig = trig_d;
     A.acc = acc;

@@ -73,6 +73,7 @@ bool method_valid(const hj_grid* g, const hj_method* m) {
     if (m->extrap != HJ_EXTRAP_AWAY_FROM_ZERO && m->extrap != HJ_EXTRAP_LINEAR) return false;
     for (int k = 0; k < 8; ++k)
         if (!std::isfinite(m->params[k])) return false;
+    if ((m->order != 0 && m->order != 3) || m->alpha_mode != HJ_ALPHA_NODE) return false;
     const int D = g->ndim;
     switch (m->dynamics) {
     case HJ_DYN_DOUBLE_INTEGRATOR: return D == 2 && m->params[0] >= 0;

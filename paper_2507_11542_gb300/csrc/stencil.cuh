@@ -202,6 +202,7 @@ template <> struct SP<double> {
     static __device__ __forceinline__ double dx(const StageParams& P, int d) { return P.g.dx[d]; }
     static __device__ __forceinline__ double inv_dx(const StageParams& P, int d) { return P.g.inv_dx[d]; }
     static __device__ __forceinline__ double half_inv_dx(const StageParams& P, int d) { return P.half_inv_dx[d]; }
+    static __device__ __forceinline__ double alpha_g(const StageParams& P, int d) { return P.alpha_g[d]; }
     static __device__ __forceinline__ double param(const StageParams& P, int k) { return P.params[k]; }
     static __device__ __forceinline__ double dt(const StageParams& P) { return P.dt; }
     static __device__ __forceinline__ double cv(const StageParams& P) { return P.cv; }
@@ -213,6 +214,7 @@ template <> struct SP<float> {
     static __device__ __forceinline__ float dx(const StageParams& P, int d) { return P.dx_f[d]; }
     static __device__ __forceinline__ float inv_dx(const StageParams& P, int d) { return P.inv_dx_f[d]; }
     static __device__ __forceinline__ float half_inv_dx(const StageParams& P, int d) { return P.half_inv_dx_f[d]; }
+    static __device__ __forceinline__ float alpha_g(const StageParams& P, int d) { return P.alpha_g_f[d]; }
     static __device__ __forceinline__ float param(const StageParams& P, int k) { return P.params_f[k]; }
     static __device__ __forceinline__ float dt(const StageParams& P) { return P.dt_f; }
     static __device__ __forceinline__ float cv(const StageParams& P) { return P.cv_f; }
@@ -238,42 +240,69 @@ __host__ __device__ constexpr bool uses_angle() {
 // ydot from node coordinates xc, cos/sin (c, s) of the dimension-2
 // coordinate (dynamics with uses_angle), the mean derivatives
 // pb = (p- + p+)/2 and the half differences dd = (p+ - p-)/2.
+// ydot from node coordinates xc, cos/sin (c, s) of the dimension-2
+// coordinate (dynamics with uses_angle), the mean derivatives
+// pb = (p- + p+)/2 and the half differences dd = (p+ - p-)/2:
+// Hg(x, pb) + sum_d alpha_d dd_d, with alpha_d = alpha_d(x) (the maximum of
+// |f_d| over the controls at the node) or, for global LF, the launch's
+// alpha_g (its maximum over the grid).
 template <typename T, int D, int DYN>
 __device__ __forceinline__ T lf_combine(const StageParams& P, const T* xc, T c, T s, const T* pb, const T* dd) {
     const auto q = [&P](int k) { return SP<T>::param(P, k); };
-    T y = T(0);
+    T h = T(0);
+    T a[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) a[d] = T(0);
     if constexpr (DYN == HJ_DYN_DOUBLE_INTEGRATOR && D == 2) {
         const T umax = q(0);
-        y = pb[0] * xc[1] - umax * fabs(pb[1]) + fabs(xc[1]) * dd[0] + umax * dd[1];
+        h = pb[0] * xc[1] - umax * fabs(pb[1]);
+        a[0] = fabs(xc[1]);
+        a[1] = umax;
     } else if constexpr (DYN == HJ_DYN_AIR3D && D == 3) {
         const T va = q(0), vb = q(1), amax = q(2), bmax = q(3);
         const T f0 = -va + vb * c, f1 = vb * s;
-        y = pb[0] * f0 + pb[1] * f1 + amax * fabs(pb[0] * xc[1] - pb[1] * xc[0] - pb[2]) - bmax * fabs(pb[2]);
-        y += (fabs(f0) + amax * fabs(xc[1])) * dd[0] + (fabs(f1) + amax * fabs(xc[0])) * dd[1] + (amax + bmax) * dd[2];
+        h = pb[0] * f0 + pb[1] * f1 + amax * fabs(pb[0] * xc[1] - pb[1] * xc[0] - pb[2]) - bmax * fabs(pb[2]);
+        a[0] = fabs(f0) + amax * fabs(xc[1]);
+        a[1] = fabs(f1) + amax * fabs(xc[0]);
+        a[2] = amax + bmax;
     } else if constexpr (DYN == HJ_DYN_ROCKETS && D == 3) {
-        const T a = q(0), g = q(1), ue = q(2), up = q(3);
-        const T f0 = a * c, f1 = a * s + a - g;
-        y = pb[0] * f0 + pb[1] * f1 + ue * fabs(pb[0] * xc[0] - pb[2]) - up * fabs(pb[1] * xc[0] + pb[2]);
-        y += (fabs(f0) + ue * fabs(xc[0])) * dd[0] + (fabs(f1) + up * fabs(xc[0])) * dd[1] + (ue + up) * dd[2];
+        const T ac = q(0), g = q(1), ue = q(2), up = q(3);
+        const T f0 = ac * c, f1 = ac * s + ac - g;
+        h = pb[0] * f0 + pb[1] * f1 + ue * fabs(pb[0] * xc[0] - pb[2]) - up * fabs(pb[1] * xc[0] + pb[2]);
+        a[0] = fabs(f0) + ue * fabs(xc[0]);
+        a[1] = fabs(f1) + up * fabs(xc[0]);
+        a[2] = ue + up;
     } else if constexpr (DYN == HJ_DYN_DUBINS4D && D == 4) {
         const T wmax = q(0), accmax = q(1);
         const T f0 = xc[3] * c, f1 = xc[3] * s;
-        y = pb[0] * f0 + pb[1] * f1 - wmax * fabs(pb[2]) - accmax * fabs(pb[3]);
-        y += fabs(f0) * dd[0] + fabs(f1) * dd[1] + wmax * dd[2] + accmax * dd[3];
+        h = pb[0] * f0 + pb[1] * f1 - wmax * fabs(pb[2]) - accmax * fabs(pb[3]);
+        a[0] = fabs(f0);
+        a[1] = fabs(f1);
+        a[2] = wmax;
+        a[3] = accmax;
     } else if constexpr (DYN == HJ_DYN_NORM) {
-        const T c = q(0);
-        T s2 = T(0), diss = T(0);
+        const T cn = q(0);
+        T s2 = T(0);
 #pragma unroll
-        for (int d = 0; d < D; ++d) { s2 += pb[d] * pb[d]; diss += dd[d]; }
-        y = -c * sqrt(s2) + c * diss;
+        for (int d = 0; d < D; ++d) { s2 += pb[d] * pb[d]; a[d] = cn; }
+        h = -cn * sqrt(s2);
     } else if constexpr (DYN == HJ_DYN_ADVECT) {
 #pragma unroll
-        for (int d = 0; d < D; ++d) { const T c = q(d); y += -c * pb[d] + fabs(c) * dd[d]; }
+        for (int d = 0; d < D; ++d) { const T cd = q(d); h += -cd * pb[d]; a[d] = fabs(cd); }
     } else if constexpr (DYN == HJ_DYN_ROTATE && D >= 2) {
         const T w = q(0);
         const T f0 = -w * xc[1], f1 = w * xc[0];
-        y = -(pb[0] * f0 + pb[1] * f1) + fabs(f0) * dd[0] + fabs(f1) * dd[1];
+        h = -(pb[0] * f0 + pb[1] * f1);
+        a[0] = fabs(f0);
+        a[1] = fabs(f1);
     }
+    if (P.alpha_global) {
+#pragma unroll
+        for (int d = 0; d < D; ++d) a[d] = SP<T>::alpha_g(P, d);
+    }
+    T y = h;
+#pragma unroll
+    for (int d = 0; d < D; ++d) y += a[d] * dd[d];
     return y;
 }
 

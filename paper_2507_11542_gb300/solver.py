@@ -40,8 +40,9 @@ class Context:
 
 
 def method(scheme=L.HJ_WENO5, dynamics=L.HJ_DYN_DOUBLE_INTEGRATOR, params=(), brt=L.HJ_BRT_MIN0,
-           extrap=L.HJ_EXTRAP_AWAY_FROM_ZERO, cfl=0.8, max_step=math.inf) -> L.hj_method:
-    return L.make_method(scheme, dynamics, params, brt, extrap, cfl, max_step)
+           extrap=L.HJ_EXTRAP_AWAY_FROM_ZERO, cfl=0.8, max_step=math.inf, order=3,
+           alpha_mode=L.HJ_ALPHA_NODE) -> L.hj_method:
+    return L.make_method(scheme, dynamics, params, brt, extrap, cfl, max_step, order, alpha_mode)
 
 
 def _check_tensor(t, spec, name):

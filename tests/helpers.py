@@ -17,15 +17,18 @@ PARAMS = {DI: (1.0,), AIR3D: (5.0, 5.0, 1.0, 1.0), DUBINS: (1.0, 0.5), NORM: (1.
           ADVECT: (0.7, -1.3, 0.4), ROTATE: (1.3,), ROCKETS: (1.0, 32.0, 1.0, 1.0)}
 
 
-def oracle_method(scheme=5, dynamics=DI, params=None, brt=1, extrap=0, cfl=0.8, max_step=math.inf):
+def oracle_method(scheme=5, dynamics=DI, params=None, brt=1, extrap=0, cfl=0.8, max_step=math.inf, order=3,
+                  alpha_global=False):
     return O.method(scheme=scheme, dynamics=dynamics, params=PARAMS[dynamics] if params is None else params,
-                    brt=brt, extrap=extrap, cfl=cfl, max_step=max_step)
+                    brt=brt, extrap=extrap, cfl=cfl, max_step=max_step, order=order, alpha_global=alpha_global)
 
 
-def lib_method(scheme=5, dynamics=DI, params=None, brt=1, extrap=0, cfl=0.8, max_step=math.inf):
+def lib_method(scheme=5, dynamics=DI, params=None, brt=1, extrap=0, cfl=0.8, max_step=math.inf, order=3,
+               alpha_global=False):
     from paper_2507_11542_gb300 import solver
     return solver.method(scheme=scheme, dynamics=dynamics, params=PARAMS[dynamics] if params is None else params,
-                         brt=brt, extrap=extrap, cfl=cfl, max_step=max_step)
+                         brt=brt, extrap=extrap, cfl=cfl, max_step=max_step, order=order,
+                         alpha_mode=1 if alpha_global else 0)
 
 
 def to_dev(V, dtype="float64"):

@@ -51,8 +51,31 @@ def test_null_context_is_rejected(lib):
     assert L.hj_ctx_create(0, None, None) == lib.HJ_EINVAL
 
 
-def test_struct_layout_matches_header(lib):
-    # sizes of the ABI structs as a C compiler lays them out
-    assert ctypes.sizeof(lib.hj_grid) == 4 + 4 + 32 + 32 + 32 + 4 + 4
-    assert ctypes.sizeof(lib.hj_method) == 4 + 4 + 64 + 4 + 4 + 8 + 8
-    assert ctypes.sizeof(lib.hj_stats) == 6 * 8
+def test_struct_layout_matches_header(lib, tmp_path):
+    # sizes and field offsets of the ABI structs as the C compiler lays them
+    # out from include/hj.h, against the ctypes mirrors
+    import os
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    structs = {"hj_grid": lib.hj_grid, "hj_method": lib.hj_method, "hj_problem": lib.hj_problem,
+               "hj_stats": lib.hj_stats, "hj_server_info": lib.hj_server_info, "hj_shape": lib.hj_shape}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "hj.h"', 'int main(void) {']
+    for name, cls in structs.items():
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (name, name))
+        for field, _ in cls._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (name, field, name, field))
+    lines += ['return 0;', '}']
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(root, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                        check=True).stdout.splitlines())
+    for name, cls in structs.items():
+        assert int(got[name]) == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert int(got["%s.%s" % (name, field)]) == getattr(cls, field).offset, (name, field)

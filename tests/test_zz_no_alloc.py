@@ -72,3 +72,7 @@ def test_static_step_rejects_what_does_not_fit(ctx):
     ok = W.GridSpec((64, 64), (-1.0, -1.0), (1.0, 1.0))
     assert L.hj_rk3_step_static(ctx.stream.cuda_stream, 0, L.make_grid(ok), m, L.HJ_F64, v, -1.0) == L.HJ_EINVAL
     assert L.hj_rk3_step_static(ctx.stream.cuda_stream, 0, L.make_grid(ok), m, 7, v, 0.01) == L.HJ_EINVAL
+    # only the three-stage scheme with per-node dissipation
+    for other in (lib_method(dynamics=DI, brt=1, order=2), lib_method(dynamics=DI, brt=1, alpha_global=True)):
+        assert L.hj_rk3_step_static(ctx.stream.cuda_stream, 0, L.make_grid(ok), other, L.HJ_F64, v, 0.01) == \
+            L.HJ_EINVAL
