@@ -413,9 +413,9 @@ hj_status rows_config(hj_ctx* ctx, const StageParams& P, int dtype, RowsCfg* out
         cudaEvent_t e0, e1;
         HJ_CUDA(ctx, cudaEventCreate(&e0));
         HJ_CUDA(ctx, cudaEventCreate(&e1));
-        // Launches of a few tens of microseconds are timed in groups: the
+        // FP32 launches of a few tens of microseconds are timed in groups: the
         // event clock advances in steps of about two microseconds.
-        const int group = G.total < (4LL << 20) ? 6 : 2;
+        const int group = dtype == HJ_F64 ? 1 : (G.total < (4LL << 20) ? 6 : 2);
         float best_ms = 1e30f;
         for (const RowsCfg& c : cands) {
             cudaError_t e = rows_launch(ctx, T, c, dtype);  // warm-up
