@@ -4,8 +4,9 @@
 Workload: the air3D pursuit-evasion game on a 101^3 grid over
 [-6,20]x[-10,10]x[0,2pi) (psi periodic), va = vb = 5, |a|,|b| <= 1,
 V0 = sqrt(x^2+y^2) - 5, WENO5 + Lax-Friedrichs + TVD-RK3, CFL 0.8, BRT
-min(0, H). One step = one full RK3 step (three fused stage kernels) over the
-whole grid; the metric is cell-updates/s (one node advanced one RK3 step).
+min(0, H). One step = one full RK3 step (one hj_rk3_step call: three fused stage
+kernels) over the whole grid; the metric is cell-updates/s (one node advanced
+one RK3 step).
 
   value  : FP32 device-resident throughput, L2 flushed between timed steps
   fp64   : the same in FP64
@@ -184,9 +185,11 @@ def workload():
     return spec, V0
 
 
-def run_steps(ctx, spec, m, V, bufs, dt, K, flush, events):
-    """K RK3 steps (three hj_rk3_stage calls each) with an L2 flush before every
-    step. Returns per-step and per-stage-launch durations in ms."""
+def run_steps(ctx, spec, m, V, bufs, dt, K, flush, events, per_stage=False):
+    """K RK3 steps with an L2 flush before every step: one hj_rk3_step call per
+    step (the library's step entry point: its three fused stage kernels), or,
+    with per_stage, three hj_rk3_stage calls with an event between stages.
+    Returns per-step and (per_stage) per-stage-launch durations in ms."""
     import ctypes
     import torch
     from paper_2507_11542_gb300 import _lib
@@ -205,22 +208,33 @@ def run_steps(ctx, spec, m, V, bufs, dt, K, flush, events):
         ev = events[k] if events is not None else None
         if ev:
             ev[0].record()
-        for s, (stage, u, vn, out) in enumerate(calls):
-            st = lib.hj_rk3_stage(h, g, mm, code, stage, u, vn, out, dt)
+        if per_stage:
+            for s, (stage, u, vn, out) in enumerate(calls):
+                st = lib.hj_rk3_stage(h, g, mm, code, stage, u, vn, out, dt)
+                if st != 0:
+                    raise _lib.HJError(st, _lib.hj_ctx_last_error(ctx.handle))
+                if ev:
+                    ev[s + 1].record()
+        else:
+            st = lib.hj_rk3_step(h, g, mm, code, pv, dt)
             if st != 0:
                 raise _lib.HJError(st, _lib.hj_ctx_last_error(ctx.handle))
             if ev:
-                ev[s + 1].record()
+                ev[3].record()
     torch.cuda.synchronize()
     if events is not None:
         for k in range(K):
             ev = events[k]
             step_ms.append(ev[0].elapsed_time(ev[3]))
-            stage_ms.extend([ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3])])
+            if per_stage:
+                stage_ms.extend([ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3])])
     return step_ms, stage_ms
 
 
 def bench_dtype(ctx, spec, V0, dtype, K, W_, world, flush, m=None):
+    """Timed: K steps through hj_rk3_step (the metric). Then K steps through
+    hj_rk3_stage with events between the stages, for the per-launch duration
+    of the stage kernel (the roofline)."""
     import torch
     from paper_2507_11542_gb300 import solver
     if m is None:
@@ -231,12 +245,14 @@ def bench_dtype(ctx, spec, V0, dtype, K, W_, world, flush, m=None):
     V = torch.from_numpy(np.ascontiguousarray(V0.ravel(order="F"))).to("cuda", tdt)
     u1, u2 = torch.empty_like(V), torch.empty_like(V)
     run_steps(ctx, spec, m, V, (u1, u2), dt, W_, flush, None)
+    run_steps(ctx, spec, m, V, (u1, u2), dt, W_, flush, None, per_stage=True)
     events = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
     barrier(world)
     torch.cuda.synchronize()
-    step_ms, stage_ms = run_steps(ctx, spec, m, V, (u1, u2), dt, K, flush, events)
+    step_ms, _ = run_steps(ctx, spec, m, V, (u1, u2), dt, K, flush, events)
     torch.cuda.synchronize()
     barrier(world)
+    _, stage_ms = run_steps(ctx, spec, m, V, (u1, u2), dt, K, flush, events, per_stage=True)
     assert torch.isfinite(V).all().item()
     total_ms = max_over_ranks(sum(step_ms), world)
     return {"total_ms": total_ms, "ms_per_step": total_ms / K, "stage_ms": stage_ms,
