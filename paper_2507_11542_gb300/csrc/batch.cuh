@@ -48,8 +48,8 @@ __global__ void __launch_bounds__(RowsLimits<T>::kMaxThreads)
         R.cu = T(2.0 / 3.0);
         R.minv = I.brt == HJ_BRT_MINV;
     }
-    rows_tile<T, D, DYN, KIND>(I.P, R, I.ty, (int)blockDim.x, I.tz, t.row_tile, t.i2, t.chunk, (int)threadIdx.x,
-                               reinterpret_cast<T*>(smem_raw));
+    rows_tile<T, D, DYN, HJ_WENO5, KIND>(I.P, R, I.ty, (int)blockDim.x, I.tz, t.row_tile, t.i2, t.chunk,
+                                         (int)threadIdx.x, reinterpret_cast<T*>(smem_raw));
 }
 
 template <typename T, int D, int DYN, int KIND>

@@ -286,7 +286,7 @@ StageParams stage_params(hj_ctx* ctx, const GridDev& G, const hj_method* m, int 
 
 
 bool rows_eligible(const GridDev& G, int scheme, int dynamics, int dtype) {
-    if (scheme != HJ_WENO5 || !rows_supported(G.ndim, dynamics)) return false;
+    if ((scheme != HJ_WENO5 && scheme != HJ_ENO2) || !rows_supported(G.ndim, dynamics)) return false;
     if (const char* env = std::getenv("HJ_ROWS"))  // HJ_ROWS=0: always the one-node-per-thread kernel
         if (env[0] == '0') return false;
     for (int d = 0; d < G.ndim; ++d)
@@ -388,7 +388,7 @@ hj_status rows_config(hj_ctx* ctx, const StageParams& P, int dtype, RowsCfg* out
         }
         return fail(ctx, HJ_EINVAL, "HJ_ROWS_CFG=%s does not fit this grid", pin);
     }
-    std::vector<long long> key = {G.ndim, P.dynamics, dtype, G.n[0], G.n[1], G.n[2], G.n[3]};
+    std::vector<long long> key = {G.ndim, P.dynamics, P.scheme, dtype, G.n[0], G.n[1], G.n[2], G.n[3]};
     auto it = ctx->rows_cache.find(key);
     if (it != ctx->rows_cache.end()) {
         *out = it->second;
@@ -449,9 +449,11 @@ hj_status rows_config(hj_ctx* ctx, const StageParams& P, int dtype, RowsCfg* out
 
 cudaError_t launch_stage(hj_ctx* ctx, const StageParams& P, int scheme, int dtype) {
     if (rows_eligible(P.g, scheme, P.dynamics, dtype)) {
+        StageParams Q = P;
+        Q.scheme = scheme;
         RowsCfg c;
-        if (rows_config(ctx, P, dtype, &c) != HJ_OK) return cudaErrorInvalidConfiguration;
-        return rows_launch(ctx, P, c, dtype);
+        if (rows_config(ctx, Q, dtype, &c) != HJ_OK) return cudaErrorInvalidConfiguration;
+        return rows_launch(ctx, Q, c, dtype);
     }
     ctx->launches += 1;
     const StageParams Q = finalize(P);

@@ -46,6 +46,7 @@ struct StageParams {
     int brt_min0;     // clamp ydot at zero (BRT min(0, H))
     int minv_after;   // out = min(out, Vn)
     int mode;         // StageMode
+    int scheme;       // HJ_WENO5 or HJ_ENO2 (row kernel); the one-node kernel takes it as an argument
     double dt;
     double cv, cu;    // stage combination coefficients
     const void* u;    // stencil input

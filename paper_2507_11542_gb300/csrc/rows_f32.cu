@@ -1,13 +1,19 @@
-// FP32 instantiations of the row-tiled WENO5 stage kernel.
+// FP32 instantiations of the row-tiled stage kernel (WENO5 here, ENO2 in
+// rows_f32_eno2.cu).
 #include "rows_kernel.cuh"
 
 namespace hj {
+cudaError_t launch_rows_f32_eno2(const StageParams& p, const RowsCfg& c, cudaStream_t s);
+int rows_blocks_per_sm_f32_eno2(const StageParams& p, const RowsCfg& c);
+
 cudaError_t launch_rows_f32(const StageParams& p, const RowsCfg& c, cudaStream_t s) {
-    HJ_ROWS_DISPATCH(launch_rows_dyn, float, p, c, s)
+    if (p.scheme == HJ_ENO2) return launch_rows_f32_eno2(p, c, s);
+    HJ_ROWS_DISPATCH(launch_rows_weno5, float, p, c, s)
     return cudaErrorInvalidValue;
 }
 int rows_blocks_per_sm_f32(const StageParams& p, const RowsCfg& c) {
-    HJ_ROWS_DISPATCH(rows_bps_dyn, float, p, c)
+    if (p.scheme == HJ_ENO2) return rows_blocks_per_sm_f32_eno2(p, c);
+    HJ_ROWS_DISPATCH(rows_bps_weno5, float, p, c)
     return 0;
 }
 }  // namespace hj

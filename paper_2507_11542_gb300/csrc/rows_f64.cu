@@ -1,4 +1,5 @@
-// FP64 instantiations of the row-tiled WENO5 stage kernel.
+// FP64 instantiations of the row-tiled stage kernel (WENO5 here, ENO2 in
+// rows_f64_eno2.cu), and the (dimension, dynamics) pairs it is built for.
 #include "rows_kernel.cuh"
 
 namespace hj {
@@ -19,12 +20,17 @@ bool rows_supported(int ndim, int dyn) {
         return false;
     }
 }
+cudaError_t launch_rows_f64_eno2(const StageParams& p, const RowsCfg& c, cudaStream_t s);
+int rows_blocks_per_sm_f64_eno2(const StageParams& p, const RowsCfg& c);
+
 cudaError_t launch_rows_f64(const StageParams& p, const RowsCfg& c, cudaStream_t s) {
-    HJ_ROWS_DISPATCH(launch_rows_dyn, double, p, c, s)
+    if (p.scheme == HJ_ENO2) return launch_rows_f64_eno2(p, c, s);
+    HJ_ROWS_DISPATCH(launch_rows_weno5, double, p, c, s)
     return cudaErrorInvalidValue;
 }
 int rows_blocks_per_sm_f64(const StageParams& p, const RowsCfg& c) {
-    HJ_ROWS_DISPATCH(rows_bps_dyn, double, p, c)
+    if (p.scheme == HJ_ENO2) return rows_blocks_per_sm_f64_eno2(p, c);
+    HJ_ROWS_DISPATCH(rows_bps_weno5, double, p, c)
     return 0;
 }
 }  // namespace hj

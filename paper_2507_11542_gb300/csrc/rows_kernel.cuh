@@ -135,7 +135,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 //               from the column queues, halo rows and row ends copied
 //               asynchronously), two planes ahead of its use.
 // Flat indices are 32-bit (the grid has fewer than 2^31 nodes).
-template <typename T, int D, int DYN, int KIND>
+template <typename T, int D, int DYN, int SCHEME, int KIND>
 __device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T>& R, const int TY, const int NT,
                                           const int tz, const int row_tile, const int i2_in, const int chunk_in,
                                           const int t, T* const smem) {
@@ -307,7 +307,7 @@ __device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T
 #pragma unroll
         for (int k = 0; k < 6; ++k) q[k] = line_value(ucol, zbeg - 3 + k, ns, (long long)sS, perS, extrap);
         T unused;
-        weno_iface(q[1] - q[0], q[2] - q[1], q[3] - q[2], q[4] - q[3], q[5] - q[4], floor_raw, unused, carry);
+        iface_at<SCHEME>(q[0], q[1], q[2], q[3], q[4], q[5], floor_raw, unused, carry);
 #pragma unroll
         for (int k = 0; k < 5; ++k) q[k] = q[k + 1];
     }
@@ -345,22 +345,20 @@ __device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T
         if (do_xrow) {
             const T* a = bz + s_xrow;
             T ppj;
-            weno_iface(a[1] - a[0], a[2] - a[1], a[3] - a[2], a[4] - a[3], a[5] - a[4], floor_raw, ppj, pmx);
+            iface_at<SCHEME>(a[0], a[1], a[2], a[3], a[4], a[5], floor_raw, ppj, pmx);
             bz[s_pxp] = ppj;
         }
         // y-interface of gap gk (between tile rows gk-1 and gk) of column x
         if (gk >= 0) {
             const T* c = bz + s_ycol;
             T ppj;
-            weno_iface(c[W] - c[0], c[2 * W] - c[W], c[3 * W] - c[2 * W], c[4 * W] - c[3 * W], c[5 * W] - c[4 * W],
-                       floor_raw, ppj, pmy);
+            iface_at<SCHEME>(c[0], c[W], c[2 * W], c[3 * W], c[4 * W], c[5 * W], floor_raw, ppj, pmy);
             bz[s_pyw] = ppj;
         }
         if (do_ylast) {
             const T* c = bz + s_ylast;
             T ppj, unused;
-            weno_iface(c[W] - c[0], c[2 * W] - c[W], c[3 * W] - c[2 * W], c[4 * W] - c[3 * W], c[5 * W] - c[4 * W],
-                       floor_raw, ppj, unused);
+            iface_at<SCHEME>(c[0], c[W], c[2 * W], c[3 * W], c[4 * W], c[5 * W], floor_raw, ppj, unused);
             bz[o_pyp + TY * nx + x] = ppj;
         }
         cp_async_wait_all();  // this thread's copies into plane z+1
@@ -384,7 +382,7 @@ __device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T
             T next = T(0);
             if constexpr (D >= 3) {
                 T pps;
-                weno_iface(q[1] - q[0], q[2] - q[1], q[3] - q[2], q[4] - q[3], q[5] - q[4], floor_raw, pps, next);
+                iface_at<SCHEME>(q[0], q[1], q[2], q[3], q[4], q[5], floor_raw, pps, next);
                 pb[SD] = (carry + pps) * hS;
                 dd[SD] = (pps - carry) * hS;
             }
@@ -393,8 +391,8 @@ __device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T
                 T v[7];
                 gather7<T>(u, (long long)(col + fz), i2, g.n[2], g.stride[2], (g.periodic_mask >> 2) & 1u, extrap, v);
                 T pm2, pp2, unused0, unused1;
-                weno_iface(v[1] - v[0], v[2] - v[1], v[3] - v[2], v[4] - v[3], v[5] - v[4], floor_raw, unused0, pm2);
-                weno_iface(v[2] - v[1], v[3] - v[2], v[4] - v[3], v[5] - v[4], v[6] - v[5], floor_raw, pp2, unused1);
+                iface_at<SCHEME>(v[0], v[1], v[2], v[3], v[4], v[5], floor_raw, unused0, pm2);
+                iface_at<SCHEME>(v[1], v[2], v[3], v[4], v[5], v[6], floor_raw, pp2, unused1);
                 const T h2 = SP<T>::half_inv_dx(P, 2);
                 pb[2] = (pm2 + pp2) * h2;
                 dd[2] = (pp2 - pm2) * h2;
@@ -425,14 +423,14 @@ __device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T
     }
 }
 
-template <typename T, int D, int DYN, int KIND, int OCC>
+template <typename T, int D, int DYN, int SCHEME, int KIND, int OCC>
 __global__ void __launch_bounds__(RowsBounds<T, OCC>::kThreads, OCC) rows_kernel(const StageParams P, const RowsCfg C) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const StageRun<T> R = stage_run<T>(P);
     const int i2 = (D == 4) ? (int)blockIdx.y : 0;
     const int chunk = (D == 3) ? (int)blockIdx.y : ((D == 4) ? (int)blockIdx.z : 0);
-    rows_tile<T, D, DYN, KIND>(P, R, C.ty, C.nt, C.tz, blockIdx.x, i2, chunk, threadIdx.x,
-                               reinterpret_cast<T*>(smem_raw));
+    rows_tile<T, D, DYN, SCHEME, KIND>(P, R, C.ty, C.nt, C.tz, blockIdx.x, i2, chunk, threadIdx.x,
+                                       reinterpret_cast<T*>(smem_raw));
 }
 
 // Shared memory of a rows_kernel block.
@@ -450,11 +448,11 @@ inline void rows_shape(const StageParams& p, const RowsCfg& c, dim3& grid, dim3&
     smem = rows_smem_bytes<T>(p.g.n[0], c.ty);
 }
 
-template <typename T, int D, int DYN, int KIND, int OCC>
+template <typename T, int D, int DYN, int SCHEME, int KIND, int OCC>
 inline cudaError_t rows_prepare() {
     static bool done = false;  // benign race: setting the attribute twice is harmless
     if (!done) {
-        cudaError_t e = cudaFuncSetAttribute(rows_kernel<T, D, DYN, KIND, OCC>,
+        cudaError_t e = cudaFuncSetAttribute(rows_kernel<T, D, DYN, SCHEME, KIND, OCC>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         if (e != cudaSuccess) return e;
         done = true;
@@ -462,44 +460,52 @@ inline cudaError_t rows_prepare() {
     return cudaSuccess;
 }
 
-template <typename T, int D, int DYN, int KIND, int OCC>
+template <typename T, int D, int DYN, int SCHEME, int KIND, int OCC>
 cudaError_t launch_rows_occ(const StageParams& p, const RowsCfg& c, cudaStream_t s) {
     dim3 grid, block;
     size_t smem;
     rows_shape<T, D, DYN>(p, c, grid, block, smem);
-    cudaError_t e = rows_prepare<T, D, DYN, KIND, OCC>();
+    cudaError_t e = rows_prepare<T, D, DYN, SCHEME, KIND, OCC>();
     if (e != cudaSuccess) return e;
-    rows_kernel<T, D, DYN, KIND, OCC><<<grid, block, smem, s>>>(p, c);
+    rows_kernel<T, D, DYN, SCHEME, KIND, OCC><<<grid, block, smem, s>>>(p, c);
     return cudaGetLastError();
 }
 
 // The variant for two blocks per SM exists for FP32 only.
-template <typename T, int D, int DYN, int KIND>
+template <typename T, int D, int DYN, int SCHEME, int KIND>
 cudaError_t launch_rows_kind(const StageParams& p, const RowsCfg& c, cudaStream_t s) {
     if constexpr (std::is_same<T, float>::value) {
-        if (c.occ == 2) return launch_rows_occ<T, D, DYN, KIND, 2>(p, c, s);
+        if (c.occ == 2) return launch_rows_occ<T, D, DYN, SCHEME, KIND, 2>(p, c, s);
     }
-    return launch_rows_occ<T, D, DYN, KIND, 1>(p, c, s);
+    return launch_rows_occ<T, D, DYN, SCHEME, KIND, 1>(p, c, s);
 }
 
-template <typename T, int D, int DYN>
-cudaError_t launch_rows_dyn(const StageParams& p, const RowsCfg& c, cudaStream_t s) {
+template <typename T, int D, int DYN, int SCHEME>
+cudaError_t launch_rows_scheme(const StageParams& p, const RowsCfg& c, cudaStream_t s) {
     switch (stage_kind(p)) {
-    case kKindTerm: return launch_rows_kind<T, D, DYN, kKindTerm>(p, c, s);
-    case kKindFirst: return launch_rows_kind<T, D, DYN, kKindFirst>(p, c, s);
-    default: return launch_rows_kind<T, D, DYN, kKindCombine>(p, c, s);
+    case kKindTerm: return launch_rows_kind<T, D, DYN, SCHEME, kKindTerm>(p, c, s);
+    case kKindFirst: return launch_rows_kind<T, D, DYN, SCHEME, kKindFirst>(p, c, s);
+    default: return launch_rows_kind<T, D, DYN, SCHEME, kKindCombine>(p, c, s);
     }
 }
+template <typename T, int D, int DYN>
+cudaError_t launch_rows_weno5(const StageParams& p, const RowsCfg& c, cudaStream_t s) {
+    return launch_rows_scheme<T, D, DYN, HJ_WENO5>(p, c, s);
+}
+template <typename T, int D, int DYN>
+cudaError_t launch_rows_eno2(const StageParams& p, const RowsCfg& c, cudaStream_t s) {
+    return launch_rows_scheme<T, D, DYN, HJ_ENO2>(p, c, s);
+}
 
-template <typename T, int D, int DYN, int OCC>
+template <typename T, int D, int DYN, int SCHEME, int OCC>
 int rows_bps_occ(const StageParams& p, const RowsCfg& c) {
     dim3 grid, block;
     size_t smem;
     rows_shape<T, D, DYN>(p, c, grid, block, smem);
     if ((int)block.x > RowsBounds<T, OCC>::kThreads) return 0;
-    if (rows_prepare<T, D, DYN, kKindCombine, OCC>() != cudaSuccess) return 0;
+    if (rows_prepare<T, D, DYN, SCHEME, kKindCombine, OCC>() != cudaSuccess) return 0;
     int bps = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, rows_kernel<T, D, DYN, kKindCombine, OCC>,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, rows_kernel<T, D, DYN, SCHEME, kKindCombine, OCC>,
                                                       (int)block.x, smem) != cudaSuccess)
         return 0;
     return bps;
@@ -507,12 +513,20 @@ int rows_bps_occ(const StageParams& p, const RowsCfg& c) {
 
 // Resident blocks per SM of the stage kernels of a configuration (the
 // combining stages, the largest of the three kinds); 0 if it cannot launch.
-template <typename T, int D, int DYN>
-int rows_bps_dyn(const StageParams& p, const RowsCfg& c) {
+template <typename T, int D, int DYN, int SCHEME>
+int rows_bps_scheme(const StageParams& p, const RowsCfg& c) {
     if constexpr (std::is_same<T, float>::value) {
-        if (c.occ == 2) return rows_bps_occ<T, D, DYN, 2>(p, c);
+        if (c.occ == 2) return rows_bps_occ<T, D, DYN, SCHEME, 2>(p, c);
     }
-    return rows_bps_occ<T, D, DYN, 1>(p, c);
+    return rows_bps_occ<T, D, DYN, SCHEME, 1>(p, c);
+}
+template <typename T, int D, int DYN>
+int rows_bps_weno5(const StageParams& p, const RowsCfg& c) {
+    return rows_bps_scheme<T, D, DYN, HJ_WENO5>(p, c);
+}
+template <typename T, int D, int DYN>
+int rows_bps_eno2(const StageParams& p, const RowsCfg& c) {
+    return rows_bps_scheme<T, D, DYN, HJ_ENO2>(p, c);
 }
 
 // Dispatch over the (dimension, dynamics) pairs the row kernel is built for.

@@ -26,6 +26,8 @@
 
 #include <cuda_runtime.h>
 
+#include "../../include/hj.h"
+
 namespace hj {
 
 __device__ __forceinline__ float rcp_approx(float x) {
@@ -133,6 +135,35 @@ __device__ __forceinline__ void weno_iface(double e1, double e2, double e3, doub
     } else {
         pm_j1 = denL > 0.0 ? phi2 + numL / denL : phi2;
         pp_j = denR > 0.0 ? psi2 - numR / denR : psi2;
+    }
+}
+
+// Second-order ENO (Sec. 3.2; Osher & Fedkiw 2003 Sec. 3.3) per interface.
+// Both one-sided derivatives at the interface between nodes j and j+1 (p+ of
+// j and p- of j+1) take the stencil that starts at j: the first difference
+// across the interface plus or minus half the smaller (in magnitude; ties to
+// the left) of the second differences centred at j and j+1. In raw
+// (undivided) units, from the values v0..v3 at nodes j-1 .. j+2:
+//   e = v2 - v1, dL = e - (v1 - v0), dR = (v3 - v2) - e,
+//   c = |dL| <= |dR| ? dL : dR,  p+_j = e - c/2,  p-_{j+1} = e + c/2.
+template <typename T>
+__device__ __forceinline__ void eno2_iface(T v0, T v1, T v2, T v3, T& pp_j, T& pm_j1) {
+    const T e = v2 - v1;
+    const T dL = e - (v1 - v0);
+    const T dR = (v3 - v2) - e;
+    const T c = (fabs(dL) <= fabs(dR)) ? dL : dR;
+    pp_j = e - T(0.5) * c;
+    pm_j1 = e + T(0.5) * c;
+}
+
+// The interface between nodes j and j+1 from the values at nodes j-2 .. j+3
+// (WENO5 reads all six, ENO2 the middle four).
+template <int SCHEME, typename T>
+__device__ __forceinline__ void iface_at(T v0, T v1, T v2, T v3, T v4, T v5, T floor_raw, T& pp_j, T& pm_j1) {
+    if constexpr (SCHEME == HJ_ENO2) {
+        eno2_iface(v1, v2, v3, v4, pp_j, pm_j1);
+    } else {
+        weno_iface(v1 - v0, v2 - v1, v3 - v2, v4 - v3, v5 - v4, floor_raw, pp_j, pm_j1);
     }
 }
 

@@ -315,13 +315,14 @@ def test_errors_are_reported_not_raised_on_device(ctx):
     (DI, (127, 29), ["1,1", "3,1", "4,1", "7,1", "8,1"]),
 ])
 @pytest.mark.parametrize("dtype", ["float64", "float32"])
-def test_row_kernel_is_independent_of_tiling(ctx, monkeypatch, dyn, shape, cfgs, dtype):
+@pytest.mark.parametrize("scheme", [5, 2])
+def test_row_kernel_is_independent_of_tiling(ctx, monkeypatch, dyn, shape, cfgs, dtype, scheme):
     from paper_2507_11542_gb300 import solver
     base = SPECS[dyn]
     spec = W.GridSpec(shape, base.lo, base.hi, base.periodic)
     V = _field(spec, 21)
-    m = lib_method(dynamics=dyn, brt=1)
-    dt = 0.8 / O.step_bound_inv(spec, oracle_method(dynamics=dyn))
+    m = lib_method(scheme=scheme, dynamics=dyn, brt=1)
+    dt = 0.8 / O.step_bound_inv(spec, oracle_method(scheme=scheme, dynamics=dyn))
     outs = []
     max_threads = 512 if dtype == "float64" else 1024
     for cfg in cfgs:
@@ -341,7 +342,7 @@ def test_row_kernel_is_independent_of_tiling(ctx, monkeypatch, dyn, shape, cfgs,
     monkeypatch.delenv("HJ_ROWS")
     assert rel_err(to_host(Vd, spec.n), outs[0]) <= (1e-13 if dtype == "float64" else 1e-5)
     if dtype == "float64":
-        ref = O.rk3_step(spec, oracle_method(dynamics=dyn, brt=1), V, dt)
+        ref = O.rk3_step(spec, oracle_method(scheme=scheme, dynamics=dyn, brt=1), V, dt)
         assert rel_err(outs[0], ref) <= TOL64
 
 
