@@ -518,7 +518,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--legs", default="f32,f64,e2e,batch,serve,large",
                     help="comma list of legs to run; f32 always runs, and a run without all of them "
-                         "(a profiling run: --legs f32 or f32,f64) prints timings instead of the JSON line")
+                         "(a profiling run: --legs f32, f32,f64 or f32,large) prints timings instead of the "
+                         "JSON line")
     ap.add_argument("--serve-requests", type=int, default=100)
     args = ap.parse_args()
     world, rank, local = dist_setup()
@@ -541,10 +542,12 @@ def main():
         r64 = bench_dtype(ctx, spec, V0, "float64", max(3, K // 4), 3, world, flush) if "f64" in legs else None
         if not full:
             # a partial run (profiling): the chosen device legs only, no JSON line
-            ctx.close()
             print("f32 leg: %.3f ms per step" % r32["ms_per_step"], flush=True)
             if r64:
                 print("f64 leg: %.3f ms per step" % r64["ms_per_step"], flush=True)
+            if "large" in legs:
+                print("large grids: %s" % json.dumps(bench_large(ctx, world, flush)), flush=True)
+            ctx.close()
             return
         e2e = bench_e2e(ctx, spec, V0, "float32", max(3, K // 4), 2, world)
         batch = bench_batch(ctx, rank=rank, world=world)
