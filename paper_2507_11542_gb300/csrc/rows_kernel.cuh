@@ -1,16 +1,17 @@
 // rows_kernel.cuh -- the fused RK stage kernel for WENO5 on 2-4 dimensional
 // grids, tiled for GB300:
 //
-//  * A thread block owns TY full rows (all n0 nodes along dimension 0) of one
-//    plane of dimensions (0, 1); threadIdx = (x, row), with n0 + 1 threads
-//    per row and usually TY + 1 thread rows. The plane with three halo rows
-//    above and below lives in shared memory.
-//  * WENO5 is evaluated per interface (one interface gives p+ of a node and
-//    p- of the next). Along dimension 0 thread x computes the interface
-//    between nodes x-1 and x (the extra thread x = n0 the row's last one);
-//    along dimension 1 thread row k the one between tile rows k-1 and k (the
-//    extra thread row the tile's last one). So each node pays for about one
-//    interface per dimension instead of two.
+//  * A thread block (1-D) owns TY full rows (all n0 nodes along dimension 0)
+//    of one plane of dimensions (0, 1): one thread per node, one per row end
+//    and, where the block has room, one per column for the tile's last
+//    dimension-1 interface, each role in its own warps. The plane with
+//    three halo rows above and below lives in shared memory.
+//  * The upwind scheme (WENO5 or ENO2) is evaluated per interface (one
+//    interface gives p+ of a node and p- of the next). Along dimension 0 the
+//    node thread x computes the interface between nodes x-1 and x (the row
+//    end the row's last one); along dimension 1 the node thread of row k the
+//    one between tile rows k-1 and k (the gap threads the tile's last one).
+//    So each node pays for about one interface per dimension instead of two.
 //  * For 3-D and 4-D grids the block streams along the last dimension through
 //    a chunk of planes: each thread keeps six values of its column in
 //    registers and carries the interface result p- to the next plane. Planes
