@@ -298,6 +298,37 @@ def test_errors_are_reported_not_raised_on_device(ctx):
     with pytest.raises(L.HJError) as e:
         solver.solve(ctx, spec, lib_method(dynamics=DI, cfl=1.5), to_dev(V0), [0.1])
     assert e.value.status == L.HJ_EINVAL
+    for bad_method in (lib_method(dynamics=DI, order=4), lib_method(dynamics=DI, scheme=4)):
+        with pytest.raises(L.HJError) as e:
+            solver.solve(ctx, spec, bad_method, to_dev(V0), [0.1])
+        assert e.value.status == L.HJ_EINVAL
+    m_bad = lib_method(dynamics=DI)
+    m_bad.alpha_mode = 2
+    with pytest.raises(L.HJError) as e:
+        solver.term(ctx, spec, m_bad, to_dev(V0))
+    assert e.value.status == L.HJ_EINVAL
+    # empty and malformed grids are rejected before any work
+    m = lib_method(dynamics=NORM, brt=0)
+    for g in (W.GridSpec((0, 5), (-1.0, -1.0), (1.0, 1.0)), W.GridSpec((1, 5), (-1.0, -1.0), (1.0, 1.0)),
+              W.GridSpec((5, 5), (1.0, -1.0), (-1.0, 1.0))):
+        grid = L.make_grid(g)
+        ydot = torch.zeros(8, dtype=torch.float64, device="cuda")
+        st = L.load().hj_term(ctx.handle, grid, m, L.HJ_F64, ydot.data_ptr(), ydot.data_ptr())
+        assert st == L.HJ_EINVAL, g
+    grid5 = L.make_grid(spec)
+    grid5.ndim = 5
+    assert L.load().hj_term(ctx.handle, grid5, m, L.HJ_F64, ydot.data_ptr(), ydot.data_ptr()) == L.HJ_EINVAL
+    # no slices
+    prob = L.hj_problem()
+    prob.grid = L.make_grid(spec)
+    prob.method = lib_method(dynamics=DI)
+    prob.dtype = L.HJ_F64
+    v0d = to_dev(V0)
+    prob.v0 = v0d.data_ptr()
+    prob.v0_on_device = 1
+    prob.n_slices = 0
+    out0 = torch.empty(v0d.numel(), dtype=torch.float64, device="cuda")
+    assert L.load().hj_solve(ctx.handle, prob, out0.data_ptr(), 1, None, None) == L.HJ_EINVAL
     # the context is still usable afterwards
     out, _, stats = solver.solve(ctx, spec, lib_method(dynamics=DI), to_dev(V0), [0.05])
     assert stats["steps"] > 0 and torch.isfinite(out).all()
@@ -407,3 +438,24 @@ def test_solve_orders_and_global_alpha_fp64(ctx, order, alpha_global, dyn, schem
     # the batched entry point solves such problems one by one, with the same result
     outs, _, _ = solver.solve_batch(ctx, [spec], [ml], [to_dev(V0)], [ts])
     np.testing.assert_array_equal(outs[0].cpu().numpy(), out.cpu().numpy())
+
+
+@pytest.mark.parametrize("dtype,n0", [("float64", 511), ("float32", 1023)])
+def test_row_kernel_widest_rows(ctx, monkeypatch, dtype, n0):
+    # the widest rows a row-kernel block holds (one node row of n0 nodes plus
+    # its row-end thread fill a 512- or 1024-thread block, no gap threads)
+    from paper_2507_11542_gb300 import solver
+    spec = W.GridSpec((n0, 9), (-1.0, -1.0), (1.0, 1.0))
+    V = _field(spec, 17)
+    m = lib_method(dynamics=DI, brt=1)
+    dt = 0.8 / O.step_bound_inv(spec, oracle_method(dynamics=DI))
+    Vd = to_dev(V, dtype)
+    solver.rk3_step(ctx, spec, m, Vd, dt)
+    got = to_host(Vd, spec.n)
+    monkeypatch.setenv("HJ_ROWS", "0")
+    Vo = to_dev(V, dtype)
+    solver.rk3_step(ctx, spec, m, Vo, dt)
+    monkeypatch.delenv("HJ_ROWS")
+    assert rel_err(got, to_host(Vo, spec.n)) <= (1e-13 if dtype == "float64" else 1e-5)
+    if dtype == "float64":
+        assert rel_err(got, O.rk3_step(spec, oracle_method(dynamics=DI), V, dt)) <= TOL64
