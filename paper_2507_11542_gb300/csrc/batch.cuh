@@ -15,7 +15,7 @@ template <> __device__ __forceinline__ double batch_dt<double>(const BatchInst& 
 template <> __device__ __forceinline__ float batch_dt<float>(const BatchInst& I) { return I.dt_f; }
 
 // KIND: kKindFirst for stage 1, kKindCombine for stages 2 and 3.
-template <typename T, int D, int DYN, int KIND>
+template <typename T, int D, int DYN, int SCHEME, int KIND>
 __global__ void __launch_bounds__(RowsLimits<T>::kMaxThreads)
     batch_kernel(const BatchTile* __restrict__ tiles, const BatchInst* __restrict__ insts, const int stage) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -48,44 +48,55 @@ __global__ void __launch_bounds__(RowsLimits<T>::kMaxThreads)
         R.cu = T(2.0 / 3.0);
         R.minv = I.brt == HJ_BRT_MINV;
     }
-    rows_tile<T, D, DYN, HJ_WENO5, KIND>(I.P, R, I.ty, (int)blockDim.x, I.tz, t.row_tile, t.i2, t.chunk,
-                                         (int)threadIdx.x, reinterpret_cast<T*>(smem_raw));
+    rows_tile<T, D, DYN, SCHEME, KIND>(I.P, R, I.ty, (int)blockDim.x, I.tz, t.row_tile, t.i2, t.chunk,
+                                       (int)threadIdx.x, reinterpret_cast<T*>(smem_raw));
 }
 
-template <typename T, int D, int DYN, int KIND>
+template <typename T, int D, int DYN, int SCHEME, int KIND>
 cudaError_t launch_batch_kind(const BatchTile* tiles, int ntiles, const BatchInst* insts, int stage, int threads,
                               size_t smem, cudaStream_t s) {
     static bool done = false;  // benign race: setting the attribute twice is harmless
     if (!done) {
-        cudaError_t e = cudaFuncSetAttribute(batch_kernel<T, D, DYN, KIND>,
+        cudaError_t e = cudaFuncSetAttribute(batch_kernel<T, D, DYN, SCHEME, KIND>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         if (e != cudaSuccess) return e;
         done = true;
     }
-    batch_kernel<T, D, DYN, KIND><<<ntiles, threads, smem, s>>>(tiles, insts, stage);
+    batch_kernel<T, D, DYN, SCHEME, KIND><<<ntiles, threads, smem, s>>>(tiles, insts, stage);
     return cudaGetLastError();
 }
 
+template <typename T, int D, int DYN, int SCHEME>
+cudaError_t launch_batch_scheme(const BatchTile* tiles, int ntiles, const BatchInst* insts, int stage, int threads,
+                                size_t smem, cudaStream_t s) {
+    return stage == 1
+               ? launch_batch_kind<T, D, DYN, SCHEME, kKindFirst>(tiles, ntiles, insts, stage, threads, smem, s)
+               : launch_batch_kind<T, D, DYN, SCHEME, kKindCombine>(tiles, ntiles, insts, stage, threads, smem, s);
+}
 template <typename T, int D, int DYN>
-cudaError_t launch_batch_dyn(const BatchTile* tiles, int ntiles, const BatchInst* insts, int stage, int threads,
-                             size_t smem, cudaStream_t s) {
-    return stage == 1 ? launch_batch_kind<T, D, DYN, kKindFirst>(tiles, ntiles, insts, stage, threads, smem, s)
-                      : launch_batch_kind<T, D, DYN, kKindCombine>(tiles, ntiles, insts, stage, threads, smem, s);
+cudaError_t launch_batch_weno5(const BatchTile* tiles, int ntiles, const BatchInst* insts, int stage, int threads,
+                               size_t smem, cudaStream_t s) {
+    return launch_batch_scheme<T, D, DYN, HJ_WENO5>(tiles, ntiles, insts, stage, threads, smem, s);
+}
+template <typename T, int D, int DYN>
+cudaError_t launch_batch_eno2(const BatchTile* tiles, int ntiles, const BatchInst* insts, int stage, int threads,
+                              size_t smem, cudaStream_t s) {
+    return launch_batch_scheme<T, D, DYN, HJ_ENO2>(tiles, ntiles, insts, stage, threads, smem, s);
 }
 
-#define HJ_BATCH_DISPATCH(T)                                                                                   \
+#define HJ_BATCH_DISPATCH(FN, T)                                                                                   \
     switch (ndim * 16 + dynamics) {                                                                            \
     case 2 * 16 + HJ_DYN_DOUBLE_INTEGRATOR:                                                                    \
-        return launch_batch_dyn<T, 2, HJ_DYN_DOUBLE_INTEGRATOR>(tiles, ntiles, insts, stage, threads, smem, s); \
-    case 2 * 16 + HJ_DYN_NORM: return launch_batch_dyn<T, 2, HJ_DYN_NORM>(tiles, ntiles, insts, stage, threads, smem, s); \
-    case 2 * 16 + HJ_DYN_ADVECT: return launch_batch_dyn<T, 2, HJ_DYN_ADVECT>(tiles, ntiles, insts, stage, threads, smem, s); \
-    case 2 * 16 + HJ_DYN_ROTATE: return launch_batch_dyn<T, 2, HJ_DYN_ROTATE>(tiles, ntiles, insts, stage, threads, smem, s); \
-    case 3 * 16 + HJ_DYN_AIR3D: return launch_batch_dyn<T, 3, HJ_DYN_AIR3D>(tiles, ntiles, insts, stage, threads, smem, s); \
-    case 3 * 16 + HJ_DYN_ROCKETS: return launch_batch_dyn<T, 3, HJ_DYN_ROCKETS>(tiles, ntiles, insts, stage, threads, smem, s); \
-    case 3 * 16 + HJ_DYN_NORM: return launch_batch_dyn<T, 3, HJ_DYN_NORM>(tiles, ntiles, insts, stage, threads, smem, s); \
-    case 3 * 16 + HJ_DYN_ADVECT: return launch_batch_dyn<T, 3, HJ_DYN_ADVECT>(tiles, ntiles, insts, stage, threads, smem, s); \
-    case 3 * 16 + HJ_DYN_ROTATE: return launch_batch_dyn<T, 3, HJ_DYN_ROTATE>(tiles, ntiles, insts, stage, threads, smem, s); \
-    case 4 * 16 + HJ_DYN_DUBINS4D: return launch_batch_dyn<T, 4, HJ_DYN_DUBINS4D>(tiles, ntiles, insts, stage, threads, smem, s); \
+        return FN<T, 2, HJ_DYN_DOUBLE_INTEGRATOR>(tiles, ntiles, insts, stage, threads, smem, s); \
+    case 2 * 16 + HJ_DYN_NORM: return FN<T, 2, HJ_DYN_NORM>(tiles, ntiles, insts, stage, threads, smem, s); \
+    case 2 * 16 + HJ_DYN_ADVECT: return FN<T, 2, HJ_DYN_ADVECT>(tiles, ntiles, insts, stage, threads, smem, s); \
+    case 2 * 16 + HJ_DYN_ROTATE: return FN<T, 2, HJ_DYN_ROTATE>(tiles, ntiles, insts, stage, threads, smem, s); \
+    case 3 * 16 + HJ_DYN_AIR3D: return FN<T, 3, HJ_DYN_AIR3D>(tiles, ntiles, insts, stage, threads, smem, s); \
+    case 3 * 16 + HJ_DYN_ROCKETS: return FN<T, 3, HJ_DYN_ROCKETS>(tiles, ntiles, insts, stage, threads, smem, s); \
+    case 3 * 16 + HJ_DYN_NORM: return FN<T, 3, HJ_DYN_NORM>(tiles, ntiles, insts, stage, threads, smem, s); \
+    case 3 * 16 + HJ_DYN_ADVECT: return FN<T, 3, HJ_DYN_ADVECT>(tiles, ntiles, insts, stage, threads, smem, s); \
+    case 3 * 16 + HJ_DYN_ROTATE: return FN<T, 3, HJ_DYN_ROTATE>(tiles, ntiles, insts, stage, threads, smem, s); \
+    case 4 * 16 + HJ_DYN_DUBINS4D: return FN<T, 4, HJ_DYN_DUBINS4D>(tiles, ntiles, insts, stage, threads, smem, s); \
     default: return cudaErrorInvalidValue;                                                                     \
     }
 

@@ -102,21 +102,45 @@ hj_status Engine::init(hj_ctx* ctx, cudaStream_t stream, int max_slots, size_t a
 
 bool Engine::eligible(const hj_problem* p) {
     const GridDev G = make_grid(&p->grid, p->method.extrap);
-    const bool rk3_node = (p->method.order == 0 || p->method.order == 3) && p->method.alpha_mode == HJ_ALPHA_NODE &&
-                          p->method.scheme == HJ_WENO5;
+    const bool rk3_node = (p->method.order == 0 || p->method.order == 3) && p->method.alpha_mode == HJ_ALPHA_NODE;
     return rk3_node && rows_eligible(G, p->method.scheme, p->method.dynamics, p->dtype) &&
            G.n[0] + 1 <= max_block_threads(p->dtype);
 }
 
-size_t Engine::footprint(const hj_problem* p, bool out_on_device) {
+// The arena layout of one instance, as offsets from the start of its block:
+// V, V1, V2, the angle tables (FP64, FP32), the host-output staging, and the
+// slice schedule (ends, end_slice, end_dt). footprint() is its total size.
+namespace {
+struct SlotLayout {
+    size_t v, v1, v2, td, tf, stage, ends, end_slice, end_dt, total;
+};
+SlotLayout slot_layout(const hj_problem* p, bool out_on_device) {
     const size_t es = elem_size(p->dtype);
-    const size_t arr = align_up((size_t)nodes_of(p->grid) * es);
-    size_t b = 3 * arr;
-    if (uses_angles(p->method.dynamics)) b += align_up(2 * (size_t)p->grid.n[2] * 12);
-    if (!out_on_device) b += align_up((size_t)p->n_slices * nodes_of(p->grid) * es);
-    b += 3 * align_up((size_t)p->n_slices * 8);  // ends, end_slice, end_dt
-    return b;
+    const size_t n = (size_t)nodes_of(p->grid);
+    const size_t arr = align_up(n * es);
+    SlotLayout L;
+    size_t o = 0;
+    L.v = o; o += arr;
+    L.v1 = o; o += arr;
+    L.v2 = o; o += arr;
+    L.td = L.tf = L.stage = 0;
+    if (uses_angles(p->method.dynamics)) {
+        L.td = o; o += align_up(2 * (size_t)p->grid.n[2] * 8);
+        L.tf = o; o += align_up(2 * (size_t)p->grid.n[2] * 4);
+    }
+    if (!out_on_device) {
+        L.stage = o;
+        o += align_up((size_t)p->n_slices * n * es);
+    }
+    L.ends = o; o += align_up((size_t)p->n_slices * 8);
+    L.end_slice = o; o += align_up((size_t)p->n_slices * 8);
+    L.end_dt = o; o += align_up((size_t)p->n_slices * 8);
+    L.total = o;
+    return L;
 }
+}  // namespace
+
+size_t Engine::footprint(const hj_problem* p, bool out_on_device) { return slot_layout(p, out_on_device).total; }
 
 int Engine::free_slot() const {
     for (int i = 0; i < max_slots_; ++i)
@@ -148,22 +172,18 @@ hj_status Engine::admit(const hj_problem* p, void* out, bool out_on_device, doub
     S.tag = tag;
     S.off = off;
     S.bytes = bytes;
-    const size_t arr = align_up((size_t)S.N * S.es);
-    size_t o = off;
-    S.o_v = o; o += arr;
-    S.o_v1 = o; o += arr;
-    S.o_v2 = o; o += arr;
+    const SlotLayout L = slot_layout(p, out_on_device);
+    S.o_v = off + L.v;
+    S.o_v1 = off + L.v1;
+    S.o_v2 = off + L.v2;
     if (S.angles) {
-        S.o_td = o; o += align_up(2 * (size_t)S.G.n[2] * 8);
-        S.o_tf = o; o += align_up(2 * (size_t)S.G.n[2] * 4);
+        S.o_td = off + L.td;
+        S.o_tf = off + L.tf;
     }
-    if (!out_on_device) {
-        S.o_stage = o;
-        o += align_up((size_t)p->n_slices * S.N * S.es);
-    }
-    S.o_ends = o; o += align_up((size_t)p->n_slices * 8);
-    S.o_end_slice = o; o += align_up((size_t)p->n_slices * 8);
-    S.o_end_dt = o; o += align_up((size_t)p->n_slices * 8);
+    if (!out_on_device) S.o_stage = off + L.stage;
+    S.o_ends = off + L.ends;
+    S.o_end_slice = off + L.end_slice;
+    S.o_end_dt = off + L.end_dt;
     unsigned char* A = arena_.base();
     HJ_CUDA(ctx_, cudaMemcpyAsync(A + S.o_v, p->v0, (size_t)S.N * S.es,
                                   p->v0_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, stream_));
@@ -283,14 +303,18 @@ hj_status Engine::activate(std::vector<int>* failed) {
         D.dt_f = (float)D.dt;
         // group
         const int dyn = S.prob.method.dynamics;
+        const int scheme = S.prob.method.scheme;
         int gi = -1;
         for (size_t k = 0; k < groups_.size(); ++k)
-            if (groups_[k].dtype == S.dtype && groups_[k].ndim == S.G.ndim && groups_[k].dyn == dyn) gi = (int)k;
+            if (groups_[k].dtype == S.dtype && groups_[k].ndim == S.G.ndim && groups_[k].dyn == dyn &&
+                groups_[k].scheme == scheme)
+                gi = (int)k;
         if (gi < 0) {
             Group g;
             g.dtype = S.dtype;
             g.ndim = S.G.ndim;
             g.dyn = dyn;
+            g.scheme = scheme;
             groups_.push_back(g);
             gi = (int)groups_.size() - 1;
         }
@@ -355,7 +379,7 @@ void append_tiles(const Slot& S, int si, std::vector<BatchTile>* out) {
 }  // namespace
 
 // The group's block size and planes per tile: measured once per (dtype,
-// dimension, dynamics) and context on the members at hand, then reused.
+// dimension, dynamics, scheme) and context on the members at hand, then reused.
 hj_status Engine::shape_group(Group& g, const std::vector<int>& members, const std::vector<int>& fresh) {
     int max_nx = 0;
     for (int m : members) max_nx = std::max(max_nx, slots[m].G.n[0]);
@@ -370,7 +394,7 @@ hj_status Engine::shape_group(Group& g, const std::vector<int>& members, const s
             h_insts_[m].tz = slots[m].tz;
         }
     };
-    const std::vector<long long> key = {g.dtype, g.ndim, g.dyn};
+    const std::vector<long long> key = {g.dtype, g.ndim, g.dyn, g.scheme};
     auto it = ctx_->batch_shape.find(key);
     if (it != ctx_->batch_shape.end() && it->second.first >= max_nx + 1) {
         apply(it->second.first, it->second.second);
@@ -407,9 +431,9 @@ hj_status Engine::shape_group(Group& g, const std::vector<int>& members, const s
             // stage 1 only writes V1, which the first real step rewrites
             auto launch = [&]() {
                 return g.dtype == HJ_F64 ? launch_batch_stage_f64(g.d_tiles, (int)g.tiles.size(), d_insts_, 1, g.ndim,
-                                                                  g.dyn, g.threads, g.smem, stream_)
+                                                                  g.dyn, g.scheme, g.threads, g.smem, stream_)
                                          : launch_batch_stage_f32(g.d_tiles, (int)g.tiles.size(), d_insts_, 1, g.ndim,
-                                                                  g.dyn, g.threads, g.smem, stream_);
+                                                                  g.dyn, g.scheme, g.threads, g.smem, stream_);
             };
             if (e == cudaSuccess) e = launch();
             float ms = 1e30f;
@@ -482,9 +506,9 @@ cudaError_t Engine::enqueue_step(cudaStream_t s, bool count) {
         for (const Group& g : groups_) {
             if (g.tiles.empty()) continue;
             cudaError_t e = g.dtype == HJ_F64 ? launch_batch_stage_f64(g.d_tiles, (int)g.tiles.size(), d_insts_, stage,
-                                                                       g.ndim, g.dyn, g.threads, g.smem, s)
+                                                                       g.ndim, g.dyn, g.scheme, g.threads, g.smem, s)
                                               : launch_batch_stage_f32(g.d_tiles, (int)g.tiles.size(), d_insts_, stage,
-                                                                       g.ndim, g.dyn, g.threads, g.smem, s);
+                                                                       g.ndim, g.dyn, g.scheme, g.threads, g.smem, s);
             if (e != cudaSuccess) return e;
             if (count) {
                 launches += 1;

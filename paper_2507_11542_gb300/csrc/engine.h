@@ -96,7 +96,7 @@ class Engine {
 
  private:
     struct Group {
-        int dtype = 0, ndim = 0, dyn = 0;
+        int dtype = 0, ndim = 0, dyn = 0, scheme = HJ_WENO5;
         int threads = 0, tz_target = 8;
         size_t smem = 0;
         std::vector<BatchTile> tiles;

@@ -184,9 +184,9 @@ struct BatchInst {
 };
 
 cudaError_t launch_batch_stage_f32(const BatchTile* tiles, int ntiles, const BatchInst* insts, int stage, int ndim,
-                                   int dynamics, int threads, size_t smem, cudaStream_t s);
+                                   int dynamics, int scheme, int threads, size_t smem, cudaStream_t s);
 cudaError_t launch_batch_stage_f64(const BatchTile* tiles, int ntiles, const BatchInst* insts, int stage, int ndim,
-                                   int dynamics, int threads, size_t smem, cudaStream_t s);
+                                   int dynamics, int scheme, int threads, size_t smem, cudaStream_t s);
 cudaError_t launch_batch_advance(BatchInst* insts, int n, cudaStream_t s);
 
 // max over nodes of sum_d alpha_d(x)/dx_d, as the FP64 bit pattern, atomically

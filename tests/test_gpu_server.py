@@ -108,9 +108,9 @@ def test_cancel_timeout_and_refusals(ctx):
         st, _, _, _ = srv.wait(long_t, 30000)
         assert st == L.HJ_ECANCELLED
         assert srv.cancel(long_t) == L.HJ_EINVAL       # forgotten after wait
-        # an ENO2 problem is not served by the batched kernel; a grid beyond the budget cannot fit
+        # a second-order-in-time problem is not served by the batched kernel; a grid beyond the budget cannot fit
         with pytest.raises(L.HJError) as e:
-            srv.submit(g, lib_method(scheme=2, dynamics=AIR3D), to_dev(V0), [0.1])
+            srv.submit(g, lib_method(scheme=2, dynamics=AIR3D, order=2), to_dev(V0), [0.1])
         assert e.value.status == L.HJ_EINVAL
         gb, Vb = W.air3d(161, 5.0)
         with pytest.raises(L.HJError) as e:
