@@ -375,8 +375,17 @@ std::vector<RowsCfg> rows_candidates(hj_ctx* ctx, const StageParams& P, int dtyp
 // HJ_TUNE=0 keeps the model's first choice without timing.
 hj_status rows_config(hj_ctx* ctx, const StageParams& P, int dtype, RowsCfg* out) {
     const GridDev& G = P.g;
-    // HJ_ROWS_CFG="ty,tz" or "ty,tz,occ" pins the shape (used to check that results do not depend on it)
+    std::vector<long long> key = {G.ndim, P.dynamics, P.scheme, dtype, G.n[0], G.n[1], G.n[2], G.n[3]};
+    // HJ_ROWS_CFG="ty,tz" or "ty,tz,occ" pins the shape (used to check that results do not depend on
+    // it); a pinned shape is validated once and cached like a tuned one
     if (const char* pin = std::getenv("HJ_ROWS_CFG")) {
+        std::vector<long long> pkey = key;
+        for (const char* c = pin; *c; ++c) pkey.push_back(-1 - (long long)(unsigned char)*c);
+        auto hit = ctx->rows_cache.find(pkey);
+        if (hit != ctx->rows_cache.end()) {
+            *out = hit->second;
+            return HJ_OK;
+        }
         int ty = 0, tz = 0, occ = 1;
         const int got = std::sscanf(pin, "%d,%d,%d", &ty, &tz, &occ);
         if (got >= 2 && ty >= 1 && tz >= 1 && ty <= G.n[1] && (occ == 1 || occ == 2) &&
@@ -384,11 +393,13 @@ hj_status rows_config(hj_ctx* ctx, const StageParams& P, int dtype, RowsCfg* out
             *out = make_rows_cfg(G, ty, tz, dtype);
             out->occ = occ;
             if (occ == 2 && (dtype == HJ_F64 || out->nt > kRowsOcc2Threads)) out->occ = 0;
-            if (out->occ && out->nchunks <= 65535 && rows_bps(P, *out, dtype) > 0) return HJ_OK;
+            if (out->occ && out->nchunks <= 65535 && rows_bps(P, *out, dtype) > 0) {
+                ctx->rows_cache[pkey] = *out;
+                return HJ_OK;
+            }
         }
         return fail(ctx, HJ_EINVAL, "HJ_ROWS_CFG=%s does not fit this grid", pin);
     }
-    std::vector<long long> key = {G.ndim, P.dynamics, P.scheme, dtype, G.n[0], G.n[1], G.n[2], G.n[3]};
     auto it = ctx->rows_cache.find(key);
     if (it != ctx->rows_cache.end()) {
         *out = it->second;
