@@ -15,11 +15,12 @@ cudaError_t launch_batch_stage_f32(const BatchTile* tiles, int ntiles, const Bat
 // After stage 3 of a step: count the step, and set up the next one. Every
 // step uses dt_full except the one that completes a slice, which is clipped
 // to land on the slice time (Listing 6) and also writes the slice output.
-__global__ void batch_advance_kernel(BatchInst* insts, int n) {
+// Only instances of lane min_lane and above took this step.
+__global__ void batch_advance_kernel(BatchInst* insts, int n, int min_lane) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     BatchInst& I = insts[i];
-    if (I.k >= I.steps_total) return;
+    if (I.k >= I.steps_total || I.lane < min_lane) return;
     const int k = ++I.k;
     I.slice_out = nullptr;
     if (k < I.steps_total) {
@@ -34,8 +35,8 @@ __global__ void batch_advance_kernel(BatchInst* insts, int n) {
     }
 }
 
-cudaError_t launch_batch_advance(BatchInst* insts, int n, cudaStream_t s) {
-    batch_advance_kernel<<<(n + 127) / 128, 128, 0, s>>>(insts, n);
+cudaError_t launch_batch_advance(BatchInst* insts, int n, int min_lane, cudaStream_t s) {
+    batch_advance_kernel<<<(n + 127) / 128, 128, 0, s>>>(insts, n, min_lane);
     return cudaGetLastError();
 }
 

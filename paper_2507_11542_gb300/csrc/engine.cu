@@ -68,9 +68,16 @@ void Arena::release(size_t off, size_t bytes) {
 // ---------------------------------------------------------------------------
 Engine::~Engine() { shutdown(); }
 
+void Engine::drop_graphs() {
+    for (int l = 0; l < kLanes; ++l) {
+        if (exec_[l]) cudaGraphExecDestroy(exec_[l]);
+        exec_[l] = nullptr;
+        exec_K_[l] = 0;
+    }
+}
+
 void Engine::shutdown() {
-    if (exec_) cudaGraphExecDestroy(exec_);
-    exec_ = nullptr;
+    drop_graphs();
     for (Group& g : groups_) cudaFree(g.d_tiles);
     groups_.clear();
     if (cap_stream_) cudaStreamDestroy(cap_stream_);
@@ -84,9 +91,10 @@ void Engine::shutdown() {
     slots.clear();
 }
 
-hj_status Engine::init(hj_ctx* ctx, cudaStream_t stream, int max_slots, size_t arena_bytes) {
+hj_status Engine::init(hj_ctx* ctx, cudaStream_t stream, int max_slots, size_t arena_bytes, bool multirate) {
     ctx_ = ctx;
     stream_ = stream;
+    multirate_ = multirate;
     max_slots_ = std::max(1, max_slots);
     HJ_CUDA(ctx, cudaMalloc(&arena_mem_, std::max<size_t>(arena_bytes, kAlign)));
     arena_.reset(static_cast<unsigned char*>(arena_mem_), std::max<size_t>(arena_bytes, kAlign));
@@ -301,6 +309,8 @@ hj_status Engine::activate(std::vector<int>* failed) {
             D.cursor = 1;
         }
         D.dt_f = (float)D.dt;
+        S.lane = !multirate_ ? 0 : (S.N > kLaneNodes[0] ? 0 : (S.N > kLaneNodes[1] ? 1 : 2));
+        D.lane = S.lane;
         // group
         const int dyn = S.prob.method.dynamics;
         const int scheme = S.prob.method.scheme;
@@ -464,23 +474,28 @@ hj_status Engine::shape_group(Group& g, const std::vector<int>& members, const s
 }
 
 hj_status Engine::rebuild_tiles() {
-    if (exec_) {
+    if (exec_[0] || exec_[1] || exec_[2]) {
         HJ_CUDA(ctx_, cudaStreamSynchronize(stream_));
-        cudaGraphExecDestroy(exec_);
-        exec_ = nullptr;
+        drop_graphs();
     }
     tiles_total_ = 0;
     for (size_t gi = 0; gi < groups_.size(); ++gi) {
         Group& g = groups_[gi];
         g.tiles.clear();
-        // largest instances first: their many tiles start early, small ones fill the tail
+        // by lane (the tiles of lanes >= l are a suffix), then largest instances
+        // first: their many tiles start early, small ones fill the tail
         std::vector<int> order;
         for (int i = 0; i < max_slots_; ++i)
             if (slots[i].used && slots[i].active && slots[i].group == (int)gi) order.push_back(i);
-        std::sort(order.begin(), order.end(), [&](int a, int b) { return slots[a].N > slots[b].N; });
+        std::sort(order.begin(), order.end(), [&](int a, int b) {
+            return slots[a].lane != slots[b].lane ? slots[a].lane < slots[b].lane : slots[a].N > slots[b].N;
+        });
         g.smem = 0;
+        for (int l = 0; l < kLanes; ++l) g.lane_off[l] = 0;
         for (int i : order) {
             append_tiles(slots[i], i, &g.tiles);
+            // tiles of lanes above this instance's start after it
+            for (int l = slots[i].lane + 1; l < kLanes; ++l) g.lane_off[l] = g.tiles.size();
             g.smem = std::max(g.smem, rows_smem(slots[i].G.n[0], slots[i].ty, slots[i].es));
         }
         tiles_total_ += (long long)g.tiles.size();
@@ -501,14 +516,17 @@ hj_status Engine::rebuild_tiles() {
     return HJ_OK;
 }
 
-cudaError_t Engine::enqueue_step(cudaStream_t s, bool count) {
+// One RK3 step of the instances of lane `lane` and above.
+cudaError_t Engine::enqueue_step(cudaStream_t s, bool count, int lane) {
     for (int stage = 1; stage <= 3; ++stage)
         for (const Group& g : groups_) {
-            if (g.tiles.empty()) continue;
-            cudaError_t e = g.dtype == HJ_F64 ? launch_batch_stage_f64(g.d_tiles, (int)g.tiles.size(), d_insts_, stage,
-                                                                       g.ndim, g.dyn, g.scheme, g.threads, g.smem, s)
-                                              : launch_batch_stage_f32(g.d_tiles, (int)g.tiles.size(), d_insts_, stage,
-                                                                       g.ndim, g.dyn, g.scheme, g.threads, g.smem, s);
+            const size_t off = g.lane_off[lane];
+            if (g.tiles.size() <= off) continue;
+            const int nt = (int)(g.tiles.size() - off);
+            cudaError_t e = g.dtype == HJ_F64 ? launch_batch_stage_f64(g.d_tiles + off, nt, d_insts_, stage, g.ndim,
+                                                                       g.dyn, g.scheme, g.threads, g.smem, s)
+                                              : launch_batch_stage_f32(g.d_tiles + off, nt, d_insts_, stage, g.ndim,
+                                                                       g.dyn, g.scheme, g.threads, g.smem, s);
             if (e != cudaSuccess) return e;
             if (count) {
                 launches += 1;
@@ -519,7 +537,7 @@ cudaError_t Engine::enqueue_step(cudaStream_t s, bool count) {
         launches += 1;
         ctx_->launches += 1;
     }
-    return launch_batch_advance(d_insts_, max_slots_, s);
+    return launch_batch_advance(d_insts_, max_slots_, lane, s);
 }
 
 long long Engine::dead_tiles() const {
@@ -552,37 +570,46 @@ hj_status Engine::run(int K) {
         if (st) return st;
     }
     cudaError_t e = cudaSuccess;
-    if (K >= 2) {
-        if (!exec_ || exec_K_ != K) {
-            if (exec_) {
-                cudaStreamSynchronize(stream_);
-                cudaGraphExecDestroy(exec_);
-                exec_ = nullptr;
+    // lane l takes (kLaneMult[l] - kLaneMult[l-1]) * K steps after the K steps of every lane
+    for (int l = 0; l < (multirate_ ? kLanes : 1) && e == cudaSuccess; ++l) {
+        bool any = false;
+        long long per_step = 1;
+        for (const Group& g : groups_)
+            if (g.tiles.size() > g.lane_off[l]) {
+                any = true;
+                per_step += 3;
             }
-            cudaGraph_t graph = nullptr;
-            e = cudaStreamBeginCapture(cap_stream_, cudaStreamCaptureModeThreadLocal);
-            for (int k = 0; k < K && e == cudaSuccess; ++k) e = enqueue_step(cap_stream_, false);
-            cudaError_t e2 = cudaStreamEndCapture(cap_stream_, &graph);
-            if (e == cudaSuccess) e = e2;
-            if (e == cudaSuccess) e = cudaGraphInstantiate(&exec_, graph, 0);
-            if (graph) cudaGraphDestroy(graph);
-            exec_K_ = K;
+        if (!any) continue;
+        const int Kl = l == 0 ? K : (kLaneMult[l] - kLaneMult[l - 1]) * K;
+        if (Kl >= 2) {
+            if (!exec_[l] || exec_K_[l] != Kl) {
+                if (exec_[l]) {
+                    cudaStreamSynchronize(stream_);
+                    cudaGraphExecDestroy(exec_[l]);
+                    exec_[l] = nullptr;
+                }
+                cudaGraph_t graph = nullptr;
+                e = cudaStreamBeginCapture(cap_stream_, cudaStreamCaptureModeThreadLocal);
+                for (int k = 0; k < Kl && e == cudaSuccess; ++k) e = enqueue_step(cap_stream_, false, l);
+                cudaError_t e2 = cudaStreamEndCapture(cap_stream_, &graph);
+                if (e == cudaSuccess) e = e2;
+                if (e == cudaSuccess) e = cudaGraphInstantiate(&exec_[l], graph, 0);
+                if (graph) cudaGraphDestroy(graph);
+                exec_K_[l] = Kl;
+            }
+            if (e == cudaSuccess) e = cudaGraphLaunch(exec_[l], stream_);
+            if (e == cudaSuccess) {
+                launches += per_step * Kl;
+                ctx_->launches += per_step * Kl;
+            }
+        } else {
+            for (int k = 0; k < Kl && e == cudaSuccess; ++k) e = enqueue_step(stream_, true, l);
         }
-        if (e == cudaSuccess) e = cudaGraphLaunch(exec_, stream_);
-        if (e == cudaSuccess) {
-            long long per_step = 1;
-            for (const Group& g : groups_)
-                if (!g.tiles.empty()) per_step += 3;
-            launches += per_step * K;
-            ctx_->launches += per_step * K;
-        }
-    } else {
-        e = enqueue_step(stream_, true);
     }
     if (e != cudaSuccess) return cuda_fail(ctx_, e, "batched step launch");
     for (int i = 0; i < max_slots_; ++i) {
         Slot& S = slots[i];
-        if (S.used && S.active) S.k_host = std::min(S.steps_total, S.k_host + K);
+        if (S.used && S.active) S.k_host = std::min(S.steps_total, S.k_host + (long long)K * kLaneMult[S.lane]);
     }
     // tiles of finished instances idle; rebuild once they are a quarter of the list
     if (4 * dead_tiles() >= tiles_total_ && tiles_total_ > 0) tiles_dirty_ = true;

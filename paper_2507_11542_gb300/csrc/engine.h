@@ -46,6 +46,7 @@ struct Slot {
     long long N = 0;
     bool angles = false;
     int group = -1;
+    int lane = 0;                    // rate class (Engine::init with lanes)
     int ty = 1, tz = 1;
     Schedule S;
     double sbi = 0.0;
@@ -63,7 +64,10 @@ class Engine {
  public:
     ~Engine();
     // Allocates the arena (arena_bytes), descriptor table and reduction words.
-    hj_status init(hj_ctx* ctx, cudaStream_t stream, int max_slots, size_t arena_bytes);
+    // With multirate, instances are sorted by size into rate lanes: per K
+    // steps of the largest, smaller ones take kLaneMult[lane] * K (a server's
+    // small requests do not wait for the pace of its largest ones).
+    hj_status init(hj_ctx* ctx, cudaStream_t stream, int max_slots, size_t arena_bytes, bool multirate = false);
     void shutdown();
 
     // Whether the batched row kernel serves this problem.
@@ -95,17 +99,23 @@ class Engine {
     long long launches = 0;
 
  private:
+    static constexpr int kLanes = 3;
+    static constexpr int kLaneMult[kLanes] = {1, 4, 16};
+    // lane of an instance of N nodes: 0 above kLaneNodes[0], 1 above kLaneNodes[1], else 2
+    static constexpr long long kLaneNodes[2] = {1LL << 22, 1LL << 20};
+
     struct Group {
         int dtype = 0, ndim = 0, dyn = 0, scheme = HJ_WENO5;
         int threads = 0, tz_target = 8;
         size_t smem = 0;
-        std::vector<BatchTile> tiles;
+        std::vector<BatchTile> tiles;     // instances by lane, then by size (largest first)
+        size_t lane_off[kLanes] = {0, 0, 0};  // first tile of an instance of lane >= l
         BatchTile* d_tiles = nullptr;
         size_t tile_cap = 0;
     };
     hj_status shape_group(Group& g, const std::vector<int>& members, const std::vector<int>& fresh);
     hj_status rebuild_tiles();
-    cudaError_t enqueue_step(cudaStream_t s, bool count);
+    cudaError_t enqueue_step(cudaStream_t s, bool count, int lane);
     long long dead_tiles() const;
 
     hj_ctx* ctx_ = nullptr;
@@ -120,8 +130,10 @@ class Engine {
     std::vector<Group> groups_;
     bool tiles_dirty_ = true;
     long long tiles_total_ = 0;
-    cudaGraphExec_t exec_ = nullptr;
-    int exec_K_ = 0;
+    bool multirate_ = false;
+    cudaGraphExec_t exec_[kLanes] = {nullptr, nullptr, nullptr};  // the step blocks of each lane
+    int exec_K_[kLanes] = {0, 0, 0};
+    void drop_graphs();
     std::vector<int> pending_;
 };
 

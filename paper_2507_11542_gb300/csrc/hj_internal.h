@@ -181,13 +181,15 @@ struct BatchInst {
     void* out;                // slice outputs: n_slices x nodes elements
     long long nodes;
     int elem;                 // element size in bytes
+    int lane;                 // rate class: advanced by the step graphs of lanes 0 .. lane
 };
 
 cudaError_t launch_batch_stage_f32(const BatchTile* tiles, int ntiles, const BatchInst* insts, int stage, int ndim,
                                    int dynamics, int scheme, int threads, size_t smem, cudaStream_t s);
 cudaError_t launch_batch_stage_f64(const BatchTile* tiles, int ntiles, const BatchInst* insts, int stage, int ndim,
                                    int dynamics, int scheme, int threads, size_t smem, cudaStream_t s);
-cudaError_t launch_batch_advance(BatchInst* insts, int n, cudaStream_t s);
+// Advances the instances of lane min_lane and above (BatchInst::lane).
+cudaError_t launch_batch_advance(BatchInst* insts, int n, int min_lane, cudaStream_t s);
 
 // max over nodes of sum_d alpha_d(x)/dx_d, as the FP64 bit pattern, atomically
 // max-ed into *acc (which the caller zeroes first).

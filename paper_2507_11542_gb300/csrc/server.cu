@@ -210,7 +210,7 @@ hj_status hj_server_create(hj_ctx* ctx, size_t hbm_budget, int32_t max_slots, hj
         return fail(ctx, HJ_ECUDA, "server stream");
     }
     hj_status st = hj_ctx_create(ctx->device, s->stream, &s->ctx);
-    if (st == HJ_OK) st = s->eng.init(s->ctx, s->stream, max_slots, hbm_budget);
+    if (st == HJ_OK) st = s->eng.init(s->ctx, s->stream, max_slots, hbm_budget, /*multirate=*/true);
     if (st != HJ_OK) {
         const std::string msg = s->ctx ? hj_ctx_last_error(s->ctx) : "";
         s->eng.shutdown();

@@ -69,6 +69,34 @@ def test_served_results_equal_solo_solves(ctx, dtype, tol):
         assert stats["elapsed_ms"] > 0
 
 
+def test_rate_lanes_let_small_requests_finish_first(ctx):
+    # Instances above 4M nodes step once per server step, those above 1M four
+    # times, smaller ones sixteen times: submitted together, a small request
+    # retires long before a large one, and every result still equals the
+    # problem solved alone.
+    from paper_2507_11542_gb300 import _lib as L, solver
+    reqs = []
+    g, V0 = W.air3d(161, 5.0)  # 4.17M nodes: lane 0
+    reqs.append((g, lib_method(dynamics=AIR3D), to_dev(V0, "float32"), [0.1, 0.3]))
+    g, V0 = W.air3d(101, 4.0)  # 1.03M nodes: lane 1
+    reqs.append((g, lib_method(dynamics=AIR3D), to_dev(V0, "float32"), [0.3]))
+    g, V0 = W.double_integrator(81, 0.5)  # 6561 nodes: lane 2
+    reqs.append((g, lib_method(dynamics=DI), to_dev(V0, "float32"), [0.25, 0.5]))
+    with solver.Server(ctx, hbm_budget=1 << 30, max_slots=4) as srv:
+        tickets = [srv.submit(g, m, v0, ts) for g, m, v0, ts in reqs]
+        results = [srv.wait(t, 120000) for t in tickets]
+    lat = []
+    for (g, m, v0, ts), (st, out, times, stats) in zip(reqs, results):
+        assert st == L.HJ_OK
+        alone, t_alone, st_alone = solver.solve(ctx, g, m, v0, ts)
+        assert stats["steps"] == st_alone["steps"]
+        np.testing.assert_array_equal(times, t_alone)
+        for s in range(len(ts)):
+            assert rel_err(to_host(out[s], g.n), to_host(alone[s], g.n)) <= 2e-6
+        lat.append(stats["elapsed_ms"])
+    assert lat[2] < lat[1] < lat[0], lat
+
+
 def test_admission_keeps_within_the_budget(ctx):
     # each 2-D request needs three grids of 81x81 doubles plus bookkeeping
     # (about 160 KiB); a 400 KiB budget admits two at a time
