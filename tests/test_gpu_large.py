@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 from paper_2507_11542_gb300 import workloads as W
-from helpers import DUBINS, NORM, lib_method
+from helpers import DUBINS, NORM, lib_method, oracle_method, window_spec
 
 pytestmark = pytest.mark.gpu
 
@@ -127,3 +127,45 @@ def test_dubins_81_fp32_zero_set_matches_fp64(ctx):
         assert disp < 0.1
         # FP32 rounding over ~140 steps, largest next to the speed boundaries (measured 3e-3 at tau = 2)
         assert dv < 1e-2
+
+
+def test_grid_beyond_32_bit_indices_sampled(ctx):
+    # 1000 x 1000 x 2148 nodes (more than 2^31): beyond the row kernel's 32-bit
+    # flat indices, so the step runs on the one-node-per-thread kernel with
+    # 64-bit indices. V0 is built on the device (8.6 GB per FP32 array); after
+    # one RK3 step, sampled nodes (corners, faces, interior) are compared with
+    # the oracle's step on the window around each.
+    import torch
+    from oracle import oracle as O
+    from paper_2507_11542_gb300 import _lib as L, solver
+    spec = W.GridSpec((1000, 1000, 2148), (-1.0,) * 3, (1.0,) * 3)
+    n0, n1, n2 = spec.n
+    assert n0 * n1 * n2 > 2 ** 31
+    shapes = [dict(kind=L.HJ_SHAPE_SPHERE, op=L.HJ_SHAPE_UNION, dims=(0, 1, 2), center=(0.1, -0.05, 0.0),
+                   radius=0.5)]
+    V = solver.implicit_surface(ctx, spec, shapes, "float32")
+    m_l = lib_method(dynamics=NORM, brt=0)
+    m_o = oracle_method(dynamics=NORM, brt=0)
+    dt = 0.8 / solver.step_bound(ctx, spec, m_l)
+    rng = np.random.default_rng(11)
+    nodes = [(0, 0, 0), (n0 - 1, n1 - 1, n2 - 1), (n0 // 2, n1 // 2, n2 // 2), (1, n1 - 2, n2 - 2),
+             (450, 500, 1074), (0, 517, 2147)]
+    nodes += [tuple(int(rng.integers(0, m)) for m in spec.n) for _ in range(4)]
+
+    def gather(ws_idx):
+        flat = (ws_idx[0][:, None, None] + n0 * (ws_idx[1][None, :, None] + n1 * ws_idx[2][None, None, :]))
+        return torch.take(V, torch.from_numpy(flat.astype(np.int64)).to(V.device)).cpu().numpy()
+
+    windows = []
+    for node in nodes:
+        ws, idx, cw = window_spec(spec, node)
+        windows.append((ws, cw, np.asfortranarray(gather(idx).astype(np.float64))))
+    solver.rk3_step(ctx, spec, m_l, V, dt)
+    flat_nodes = torch.tensor([i + n0 * (j + n1 * k) for i, j, k in nodes], dtype=torch.int64, device=V.device)
+    got = torch.take(V, flat_nodes).cpu().numpy()
+    scale = max(float(np.max(np.abs(w[2]))) for w in windows)
+    for (ws, cw, w0), g_val, node in zip(windows, got, nodes):
+        want = O.rk3_step(ws, m_o, w0, dt)[cw]
+        assert abs(float(g_val) - want) <= 2e-6 * scale, (node, float(g_val), want)
+    del V
+    torch.cuda.empty_cache()
