@@ -520,7 +520,7 @@ def main():
                     help="comma list of legs to run; f32 always runs, and a run without all of them "
                          "(a profiling run: --legs f32, f32,f64 or f32,large) prints timings instead of the "
                          "JSON line")
-    ap.add_argument("--serve-requests", type=int, default=100)
+    ap.add_argument("--serve-requests", type=int, default=1000)
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
