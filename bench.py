@@ -518,7 +518,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--legs", default="f32,f64,e2e,batch,serve,large",
                     help="comma list of legs to run; f32 always runs, and a run without all of them "
-                         "(a profiling run: --legs f32, f32,f64 or f32,large) prints timings instead of the "
+                         "(a profiling run: --legs f32, f32,f64, f32,large or f32,batch) prints timings instead of the "
                          "JSON line")
     ap.add_argument("--serve-requests", type=int, default=1000)
     args = ap.parse_args()
@@ -547,6 +547,8 @@ def main():
                 print("f64 leg: %.3f ms per step" % r64["ms_per_step"], flush=True)
             if "large" in legs:
                 print("large grids: %s" % json.dumps(bench_large(ctx, world, flush)), flush=True)
+            if "batch" in legs:
+                print("batched: %s" % json.dumps(bench_batch(ctx, rank=rank, world=world)), flush=True)
             ctx.close()
             return
         e2e = bench_e2e(ctx, spec, V0, "float32", max(3, K // 4), 2, world)
