@@ -4,7 +4,8 @@ Each case integrates the oracle through several RK3 steps and compares with
 a solution known independently of the scheme: exact translation and rotation
 of the level-set equation, the Hopf-Lax solution of an expanding sphere, the
 swept-disk solution of the Dubins car without controls, the double-integrator
-reachable set by brute force over bang-bang controls, and the mirror symmetry
+reachable set by brute force over bang-bang controls and against its
+minimum-time isochrons, and the mirror symmetry
 and refinement convergence of the air3D game.
 """
 import math
@@ -175,3 +176,32 @@ def test_air3d_converges_under_refinement():
     d1 = np.mean(np.abs(sols[0] - sols[1][::2, ::2, ::2]))
     d2 = np.mean(np.abs(sols[1] - sols[2][::2, ::2, ::2]))
     assert d2 < d1 / 2.5, (d1, d2)  # measured: 0.0445 -> 0.0122
+
+
+def _di_min_time(x1, x2):
+    """Minimum time to the origin of x1' = x2, x2' = u, |u| <= 1 (bang-bang
+    with one switch on the curve x1 = -x2|x2|/2)."""
+    above = x1 + 0.5 * x2 * np.abs(x2) > 0
+    return np.where(above, x2 + 2.0 * np.sqrt(np.maximum(x1 + 0.5 * x2 * x2, 0.0)),
+                    -x2 + 2.0 * np.sqrt(np.maximum(-x1 + 0.5 * x2 * x2, 0.0)))
+
+
+def test_double_integrator_brt_lies_between_min_time_isochrons():
+    # A small disk target (r = 0.05): every state that reaches the origin by
+    # tau reaches the disk, and a state that reaches the disk by tau reaches
+    # the origin by tau + (the longest minimum time from the disk). So the
+    # zero sublevel set lies between the isochrons T = tau and
+    # T = tau + T_disk; 0.1 of margin on each side absorbs the scheme's
+    # smearing of the front (a few cells).
+    r, tau = 0.05, 0.6
+    g, V0 = W.double_integrator(101, r)
+    m = O.method(scheme=O.WENO5, dynamics=O.DYN_DOUBLE_INTEGRATOR, params=(1.0,), brt=O.BRT_MIN0)
+    S, _, _ = O.solve(g, m, V0, [tau])
+    X1, X2 = np.meshgrid(g.axis(0), g.axis(1), indexing="ij")
+    T = _di_min_time(X1, X2)
+    a = np.linspace(0.0, 2.0 * np.pi, 721)
+    t_disk = float(np.max(_di_min_time(r * np.cos(a), r * np.sin(a))))
+    inner, outer = T <= tau - 0.1, T >= tau + t_disk + 0.1
+    assert inner.sum() > 50 and outer.sum() > 50
+    assert np.all(S[0][inner] < 0.0)
+    assert np.all(S[0][outer] > 0.0)
