@@ -467,6 +467,54 @@ def bench_serve(ctx, n_req: int, seed: int = 7, load: float = 0.8, budget_gb: fl
             "kernel_launches": launches}
 
 
+def zero_set_displacement_cells(V, Vref):
+    """Zero-level-set displacement in cells, measured on grid edges: where both
+    fields change sign along an edge, |s - s_ref| of the linearly interpolated
+    crossing points; where only one does, the distance from that crossing to
+    the nearer end of the edge (a lower bound of the move). Max over edges."""
+    worst = 0.0
+    pos, pos_r = V > 0, Vref > 0
+    for d in range(V.ndim):
+        a = [slice(None)] * V.ndim
+        b = [slice(None)] * V.ndim
+        a[d], b[d] = slice(0, V.shape[d] - 1), slice(1, V.shape[d])
+        a, b = tuple(a), tuple(b)
+        c, cr = pos[a] != pos[b], pos_r[a] != pos_r[b]
+        with np.errstate(divide="ignore", invalid="ignore"):
+            s = np.nan_to_num(V[a] / (V[a] - V[b]))
+            sr = np.nan_to_num(Vref[a] / (Vref[a] - Vref[b]))
+        both, only = c & cr, c ^ cr
+        if both.any():
+            worst = max(worst, float(np.max(np.abs(s - sr)[both])))
+        if only.any():
+            t = np.where(c, s, sr)[only]
+            worst = max(worst, float(np.max(np.minimum(t, 1.0 - t))))
+    return worst
+
+
+def bench_fp32_error(ctx, spec, V0):
+    """The FP32 path's error on the bench workload over its whole horizon: the
+    11 slices to tau = 2.8 in FP32 against the same solve in FP64 (which the
+    parity tests hold within 1e-12 of the oracle)."""
+    import torch
+    from paper_2507_11542_gb300 import solver, workloads as W
+    m = solver.method(dynamics=2, params=(5.0, 5.0, 1.0, 1.0), brt=1)
+    ts = W.slice_times(2.8)
+    flat = torch.from_numpy(np.ascontiguousarray(V0.ravel(order="F"))).cuda()
+    s32, _, st = solver.solve(ctx, spec, m, flat.float(), ts)
+    s64, _, _ = solver.solve(ctx, spec, m, flat.double(), ts)
+    worst_rel, worst_cells = 0.0, 0.0
+    for k in range(1, len(ts)):
+        a = s32[k].double().cpu().numpy().reshape(spec.n, order="F")
+        b = s64[k].cpu().numpy().reshape(spec.n, order="F")
+        worst_rel = max(worst_rel, float(np.max(np.abs(a - b)) / np.max(np.abs(b))))
+        worst_cells = max(worst_cells, zero_set_displacement_cells(a, b))
+    return {"workload": "air3D 101^3, 11 slices to tau = 2.8 (%d RK3 steps), FP32 against the FP64 solve"
+                        % st["steps"],
+            "max_abs_err_rel": worst_rel, "zero_set_displacement_cells": worst_cells,
+            "bar_cells": 0.1}
+
+
 def cpu_oracle_rate(spec, V0, steps: int):
     """The FP64 oracle, single-threaded, on the full 101^3 grid for `steps` RK3 steps."""
     from oracle import oracle as O
@@ -598,6 +646,7 @@ def main():
         serve = bench_serve(ctx, args.serve_requests) if world == 1 else None
         large = bench_large(ctx, world, flush)
         rockets = bench_rockets(ctx) if world == 1 else None
+        fp32_error = bench_fp32_error(ctx, spec, V0) if rank == 0 else None
     value = world * K * N_CELLS / (r32["total_ms"] / 1e3)
     hbm, hbm_kind = measured_hbm_gbs()
     launch_s = r32["launch_ms_mean"] / 1e3
@@ -641,6 +690,8 @@ def main():
     line["large_grids"] = large
     if rockets:
         line["rockets"] = rockets
+    if fp32_error:
+        line["fp32_error"] = fp32_error
     if rank == 0 and not args.no_cpu_baseline:
         rate1, el1 = cpu_oracle_rate(spec, V0, args.cpu_steps)
         procs = host_cores()
