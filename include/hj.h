@@ -206,7 +206,7 @@ hj_status hj_solve(hj_ctx* ctx, const hj_problem* problem, void* out_slices, int
  * writes its slices to out_slices[i] (device memory if out_on_device[i], else
  * host memory), its slice times to out_times[i] (may be NULL, or out_times
  * itself NULL) and its statistics to stats[i] (stats may be NULL).
- * WENO5 and ENO2 instances of the row kernel's (dimension, dynamics) pairs
+ * Instances (any scheme) of the row kernel's (dimension, dynamics) pairs
  * with n0 < 1024 (FP32) or n0 < 512 (FP64), the three-stage scheme and
  * per-node dissipation advance together: one launch per RK stage and
  * (element type, dimension, dynamics, scheme) group covers every tile of
@@ -253,7 +253,7 @@ hj_status hj_server_create(hj_ctx* ctx, size_t hbm_budget, int32_t max_slots, hj
  * memory if out_on_device) and out_times (host, n_slices doubles, may be
  * NULL) must stay valid until hj_server_wait returns for the ticket.
  * Errors: HJ_EINVAL (malformed, or not served by the batched row kernel:
- * WENO5 or ENO2, the three-stage scheme, per-node dissipation, the
+ * the three-stage scheme, per-node dissipation, the
  * dimension/dynamics pairs of hj_solve_batch), HJ_ENOMEM (footprint
  * larger than the whole budget), HJ_ECANCELLED (server stopping). */
 hj_status hj_server_submit(hj_server* srv, const hj_problem* problem, void* out_slices, int32_t out_on_device,

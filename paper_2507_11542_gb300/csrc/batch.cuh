@@ -84,6 +84,17 @@ cudaError_t launch_batch_eno2(const BatchTile* tiles, int ntiles, const BatchIns
     return launch_batch_scheme<T, D, DYN, HJ_ENO2>(tiles, ntiles, insts, stage, threads, smem, s);
 }
 
+template <typename T, int D, int DYN>
+cudaError_t launch_batch_eno1(const BatchTile* tiles, int ntiles, const BatchInst* insts, int stage, int threads,
+                              size_t smem, cudaStream_t s) {
+    return launch_batch_scheme<T, D, DYN, HJ_ENO1>(tiles, ntiles, insts, stage, threads, smem, s);
+}
+template <typename T, int D, int DYN>
+cudaError_t launch_batch_eno3(const BatchTile* tiles, int ntiles, const BatchInst* insts, int stage, int threads,
+                              size_t smem, cudaStream_t s) {
+    return launch_batch_scheme<T, D, DYN, HJ_ENO3>(tiles, ntiles, insts, stage, threads, smem, s);
+}
+
 #define HJ_BATCH_DISPATCH(FN, T)                                                                                   \
     switch (ndim * 16 + dynamics) {                                                                            \
     case 2 * 16 + HJ_DYN_DOUBLE_INTEGRATOR:                                                                    \

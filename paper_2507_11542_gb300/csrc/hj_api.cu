@@ -286,7 +286,9 @@ StageParams stage_params(hj_ctx* ctx, const GridDev& G, const hj_method* m, int 
 
 
 bool rows_eligible(const GridDev& G, int scheme, int dynamics, int dtype) {
-    if ((scheme != HJ_WENO5 && scheme != HJ_ENO2) || !rows_supported(G.ndim, dynamics)) return false;
+    if ((scheme != HJ_WENO5 && scheme != HJ_ENO1 && scheme != HJ_ENO2 && scheme != HJ_ENO3) ||
+        !rows_supported(G.ndim, dynamics))
+        return false;
     if (const char* env = std::getenv("HJ_ROWS"))  // HJ_ROWS=0: always the one-node-per-thread kernel
         if (env[0] == '0') return false;
     for (int d = 0; d < G.ndim; ++d)

@@ -6,7 +6,7 @@
 //    and, where the block has room, one per column for the tile's last
 //    dimension-1 interface, each role in its own warps. The plane with
 //    three halo rows above and below lives in shared memory.
-//  * The upwind scheme (WENO5 or ENO2) is evaluated per interface (one
+//  * The upwind scheme (WENO5, ENO1/2/3) is evaluated per interface (one
 //    interface gives p+ of a node and p- of the next). Along dimension 0 the
 //    node thread x computes the interface between nodes x-1 and x (the row
 //    end the row's last one); along dimension 1 the node thread of row k the
@@ -497,6 +497,14 @@ template <typename T, int D, int DYN>
 cudaError_t launch_rows_eno2(const StageParams& p, const RowsCfg& c, cudaStream_t s) {
     return launch_rows_scheme<T, D, DYN, HJ_ENO2>(p, c, s);
 }
+template <typename T, int D, int DYN>
+cudaError_t launch_rows_eno1(const StageParams& p, const RowsCfg& c, cudaStream_t s) {
+    return launch_rows_scheme<T, D, DYN, HJ_ENO1>(p, c, s);
+}
+template <typename T, int D, int DYN>
+cudaError_t launch_rows_eno3(const StageParams& p, const RowsCfg& c, cudaStream_t s) {
+    return launch_rows_scheme<T, D, DYN, HJ_ENO3>(p, c, s);
+}
 
 template <typename T, int D, int DYN, int SCHEME, int OCC>
 int rows_bps_occ(const StageParams& p, const RowsCfg& c) {
@@ -528,6 +536,14 @@ int rows_bps_weno5(const StageParams& p, const RowsCfg& c) {
 template <typename T, int D, int DYN>
 int rows_bps_eno2(const StageParams& p, const RowsCfg& c) {
     return rows_bps_scheme<T, D, DYN, HJ_ENO2>(p, c);
+}
+template <typename T, int D, int DYN>
+int rows_bps_eno1(const StageParams& p, const RowsCfg& c) {
+    return rows_bps_scheme<T, D, DYN, HJ_ENO1>(p, c);
+}
+template <typename T, int D, int DYN>
+int rows_bps_eno3(const StageParams& p, const RowsCfg& c) {
+    return rows_bps_scheme<T, D, DYN, HJ_ENO3>(p, c);
 }
 
 // Dispatch over the (dimension, dynamics) pairs the row kernel is built for.

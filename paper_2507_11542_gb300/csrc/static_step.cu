@@ -202,7 +202,7 @@ extern "C" hj_status hj_rk3_step_static(void* cuda_stream, int32_t device, const
     if (cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return HJ_ECUDA;
     RowsCfg cfg;
     P.scheme = method->scheme;
-    const bool rows = (method->scheme == HJ_WENO5 || method->scheme == HJ_ENO2) && pick_rows(P, dtype, sm_count, &cfg);
+    const bool rows = pick_rows(P, dtype, sm_count, &cfg);  // every scheme has a row-kernel variant
 
     // stage 1: w1 = v + dt L(v); stage 2: w2 = 3/4 v + 1/4 (w1 + dt L(w1));
     // stage 3: v = 1/3 v + 2/3 (w2 + dt L(w2)) [then min(., v) for the min-V rule]

@@ -156,12 +156,42 @@ __device__ __forceinline__ void eno2_iface(T v0, T v1, T v2, T v3, T& pp_j, T& p
     pm_j1 = e + T(0.5) * c;
 }
 
+// Third-order ENO (Sec. 3.2; Osher & Fedkiw 2003 Sec. 3.3) per interface.
+// p+ of node j and p- of node j+1 both start from k = j, so they take the
+// same second-difference choice (c; k* = j-1 on the left, else j) and the
+// same third-difference choice (c*, the smaller of the two differences next
+// to k*; ties to the left); only the polynomial coefficients differ. In raw
+// units, from e_m = v_{m+1} - v_m, second differences d2_m = e_m - e_{m-1}
+// and third differences d3 = d2_{m+1} - d2_m (the divided differences are
+// e/dx, d2/(2 dx^2), d3/(6 dx^3)):
+//   p+_j     = e_j - c/2 + c* (left ? -1 : 2)/6
+//   p-_{j+1} = e_j + c/2 + c* (left ? 2 : -1)/6
+// from the values v0..v5 at nodes j-2 .. j+3.
+template <typename T>
+__device__ __forceinline__ void eno3_iface(T v0, T v1, T v2, T v3, T v4, T v5, T& pp_j, T& pm_j1) {
+    const T e0 = v1 - v0, e1 = v2 - v1, e2 = v3 - v2, e3 = v4 - v3, e4 = v5 - v4;
+    const T dm = e1 - e0, d0 = e2 - e1, d1 = e3 - e2, d2 = e4 - e3;  // second differences at j-1, j, j+1, j+2
+    const bool left = fabs(d0) <= fabs(d1);
+    const T c = left ? d0 : d1;
+    const T a = left ? d0 - dm : d1 - d0;  // third differences next to k*
+    const T b = left ? d1 - d0 : d2 - d1;
+    const T cs = (fabs(a) <= fabs(b)) ? a : b;
+    const T third = cs * T(1.0 / 6.0);
+    pp_j = e2 - T(0.5) * c + (left ? -third : T(2) * third);
+    pm_j1 = e2 + T(0.5) * c + (left ? T(2) * third : -third);
+}
+
 // The interface between nodes j and j+1 from the values at nodes j-2 .. j+3
-// (WENO5 reads all six, ENO2 the middle four).
+// (WENO5 and ENO3 read all six, ENO2 the middle four, ENO1 the middle two:
+// first order takes the difference across the interface for both sides).
 template <int SCHEME, typename T>
 __device__ __forceinline__ void iface_at(T v0, T v1, T v2, T v3, T v4, T v5, T floor_raw, T& pp_j, T& pm_j1) {
-    if constexpr (SCHEME == HJ_ENO2) {
+    if constexpr (SCHEME == HJ_ENO1) {
+        pp_j = pm_j1 = v3 - v2;
+    } else if constexpr (SCHEME == HJ_ENO2) {
         eno2_iface(v1, v2, v3, v4, pp_j, pm_j1);
+    } else if constexpr (SCHEME == HJ_ENO3) {
+        eno3_iface(v0, v1, v2, v3, v4, v5, pp_j, pm_j1);
     } else {
         weno_iface(v1 - v0, v2 - v1, v3 - v2, v4 - v3, v5 - v4, floor_raw, pp_j, pm_j1);
     }

@@ -51,6 +51,11 @@ def _mixed(dtype):
     cases.append((g, lib_method(dynamics=NORM, brt=0), W.sphere(g, (0.0,) * 3, 0.25), [0.1, 0.3], NORM))
     g = W.GridSpec((25, 27), (-1.0, -1.0), (1.0, 1.0))
     cases.append((g, lib_method(dynamics=DI, brt=2), W.sphere(g, (0.1, 0.0), 0.4), [0.25], DI))
+    # third- and first-order ENO instances (groups of their own)
+    g, V0 = W.air3d(27, 4.5)
+    cases.append((g, lib_method(scheme=3, dynamics=AIR3D), V0, [0.3, 0.6], AIR3D))
+    g, V0 = W.double_integrator(35, 0.5)
+    cases.append((g, lib_method(scheme=1, dynamics=DI), V0, [0.4], DI))
     return cases
 
 
@@ -71,7 +76,7 @@ def test_batch_equals_each_solve_alone(ctx, dtype):
 
 def test_batch_fp64_matches_oracle(ctx):
     from paper_2507_11542_gb300 import solver
-    cases = _mixed("float64")[:9]
+    cases = _mixed("float64")
     outs, times, stats = solver.solve_batch(ctx, [c[0] for c in cases], [c[1] for c in cases],
                                             [to_dev(c[2]) for c in cases], [c[3] for c in cases])
     for k, (spec, m, V0, ts, dyn) in enumerate(cases):

@@ -79,7 +79,7 @@ def test_upwind_parity_fp32(ctx, scheme):
 
 
 @pytest.mark.parametrize("dyn", [DI, AIR3D, DUBINS, NORM, ADVECT, ROTATE, ROCKETS])
-@pytest.mark.parametrize("scheme", [2, 5])
+@pytest.mark.parametrize("scheme", [1, 2, 3, 5])
 @pytest.mark.parametrize("brt", [0, 1])
 def test_term_parity_fp64(ctx, dyn, scheme, brt):
     from paper_2507_11542_gb300 import solver
@@ -346,7 +346,7 @@ def test_errors_are_reported_not_raised_on_device(ctx):
     (DI, (127, 29), ["1,1", "3,1", "4,1", "7,1", "8,1"]),
 ])
 @pytest.mark.parametrize("dtype", ["float64", "float32"])
-@pytest.mark.parametrize("scheme", [5, 2])
+@pytest.mark.parametrize("scheme", [5, 3, 2, 1])
 def test_row_kernel_is_independent_of_tiling(ctx, monkeypatch, dyn, shape, cfgs, dtype, scheme):
     from paper_2507_11542_gb300 import solver
     base = SPECS[dyn]
