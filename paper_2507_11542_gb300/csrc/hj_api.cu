@@ -323,7 +323,9 @@ cudaError_t rows_launch(hj_ctx* ctx, const StageParams& P0, const RowsCfg& c, in
 
 // Candidate shapes ranked by a simple cost model: whole waves of resident
 // blocks times the work of a block (warps x planes, plus one plane of
-// prologue per chunk and the halo rows per plane).
+// prologue per chunk and the halo rows per plane). The sixteen best blocks
+// with row-end threads and the eight best of n0*ty threads (the last node row
+// taking the row ends) are timed.
 std::vector<RowsCfg> rows_candidates(hj_ctx* ctx, const StageParams& P, int dtype) {
     const GridDev& G = P.g;
     const int nx = G.n[0], ny = G.n[1];
@@ -332,9 +334,9 @@ std::vector<RowsCfg> rows_candidates(hj_ctx* ctx, const StageParams& P, int dtyp
     const size_t es = dtype == HJ_F64 ? 8 : 4;
     static const int tys[] = {1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 12, 16, 24, 32};
     static const int tzs[] = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64, 128, 256};
-    std::vector<std::pair<double, RowsCfg>> scored;
+    std::vector<std::pair<double, RowsCfg>> scored, scored_merged;
     for (int ty : tys) {
-        if (ty > ny || (nx + 1) * ty > rows_max_threads(dtype == HJ_F64)) continue;
+        if (ty > ny || ty > nx || nx * ty > rows_max_threads(dtype == HJ_F64)) continue;
         if (rows_smem(nx, ty, es) > 200 * 1024) continue;
         std::vector<int> zs;
         if (D >= 3) {
@@ -344,9 +346,12 @@ std::vector<RowsCfg> rows_candidates(hj_ctx* ctx, const StageParams& P, int dtyp
         } else {
             zs.push_back(1);
         }
-        for (int k = 0; k < 2 * (int)zs.size(); ++k) {
-            const int tz = zs[k / 2];
+        for (int k = 0; k < 4 * (int)zs.size(); ++k) {
+            const int tz = zs[k / 4];
+            const bool merged = (k % 4) >= 2;  // a block of n0*ty threads: the last node row takes the row ends
+            if (!merged && (nx + 1) * ty > rows_max_threads(dtype == HJ_F64)) continue;
             RowsCfg c = make_rows_cfg(G, ty, tz, dtype);
+            if (merged) c.nt = nx * ty;
             if (k % 2 == 1) {  // the FP32 variant for two blocks per SM
                 if (dtype == HJ_F64 || c.nt > kRowsOcc2Threads) continue;
                 c.occ = 2;
@@ -361,13 +366,17 @@ std::vector<RowsCfg> rows_candidates(hj_ctx* ctx, const StageParams& P, int dtyp
             const double rows_valid = std::min(ty, ny);
             const double plane = warps * (1.0 + 0.1 * (6.0 + ty - rows_valid) / ty);
             const double planes = D >= 3 ? (double)std::min(tz, ns) + 1.0 : 1.0;
-            scored.push_back({waves * std::min((double)bps, blocks) * plane * planes, c});
+            (merged ? scored_merged : scored).push_back({waves * std::min((double)bps, blocks) * plane * planes, c});
         }
     }
-    std::sort(scored.begin(), scored.end(),
-              [](const std::pair<double, RowsCfg>& a, const std::pair<double, RowsCfg>& b) { return a.first < b.first; });
+    const auto by_cost = [](const std::pair<double, RowsCfg>& a, const std::pair<double, RowsCfg>& b) {
+        return a.first < b.first;
+    };
+    std::sort(scored.begin(), scored.end(), by_cost);
+    std::sort(scored_merged.begin(), scored_merged.end(), by_cost);
     std::vector<RowsCfg> out;
     for (size_t k = 0; k < scored.size() && k < 16; ++k) out.push_back(scored[k].second);
+    for (size_t k = 0; k < scored_merged.size() && k < 8; ++k) out.push_back(scored_merged[k].second);
     return out;
 }
 
@@ -378,8 +387,9 @@ std::vector<RowsCfg> rows_candidates(hj_ctx* ctx, const StageParams& P, int dtyp
 hj_status rows_config(hj_ctx* ctx, const StageParams& P, int dtype, RowsCfg* out) {
     const GridDev& G = P.g;
     std::vector<long long> key = {G.ndim, P.dynamics, P.scheme, dtype, G.n[0], G.n[1], G.n[2], G.n[3]};
-    // HJ_ROWS_CFG="ty,tz" or "ty,tz,occ" pins the shape (used to check that results do not depend on
-    // it); a pinned shape is validated once and cached like a tuned one
+    // HJ_ROWS_CFG="ty,tz", "ty,tz,occ" or "ty,tz,occ,merged" pins the shape (used to check that
+    // results do not depend on it; merged = 1: a block of n0*ty threads, without row-end threads); a
+    // pinned shape is validated once and cached like a tuned one
     if (const char* pin = std::getenv("HJ_ROWS_CFG")) {
         std::vector<long long> pkey = key;
         for (const char* c = pin; *c; ++c) pkey.push_back(-1 - (long long)(unsigned char)*c);
@@ -388,11 +398,12 @@ hj_status rows_config(hj_ctx* ctx, const StageParams& P, int dtype, RowsCfg* out
             *out = hit->second;
             return HJ_OK;
         }
-        int ty = 0, tz = 0, occ = 1;
-        const int got = std::sscanf(pin, "%d,%d,%d", &ty, &tz, &occ);
-        if (got >= 2 && ty >= 1 && tz >= 1 && ty <= G.n[1] && (occ == 1 || occ == 2) &&
-            (G.n[0] + 1) * ty <= rows_max_threads(dtype == HJ_F64)) {
+        int ty = 0, tz = 0, occ = 1, merged = 0;
+        const int got = std::sscanf(pin, "%d,%d,%d,%d", &ty, &tz, &occ, &merged);
+        if (got >= 2 && ty >= 1 && tz >= 1 && ty <= G.n[1] && (occ == 1 || occ == 2) && (merged == 0 || merged == 1) &&
+            (G.n[0] + 1 - merged) * ty <= rows_max_threads(dtype == HJ_F64) && ty <= G.n[0]) {
             *out = make_rows_cfg(G, ty, tz, dtype);
+            if (merged) out->nt = G.n[0] * ty;
             out->occ = occ;
             if (occ == 2 && (dtype == HJ_F64 || out->nt > kRowsOcc2Threads)) out->occ = 0;
             if (out->occ && out->nchunks <= 65535 && rows_bps(P, *out, dtype) > 0) {

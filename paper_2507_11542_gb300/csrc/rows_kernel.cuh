@@ -113,6 +113,8 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 //   t <  n0*TY+TY+n0    gap thread of column x (present when the block has
 //                       room: NT >= n0*TY + TY + n0);
 //   others              barriers only.
+// A block of exactly n0*TY threads has no row-end threads: node thread x of
+// the last node row takes the end of row x as well (rows of n0 >= TY nodes).
 //
 // Interfaces along dimensions 0 and 1 are each evaluated once per plane and
 // shared through shared memory:
@@ -186,7 +188,15 @@ __device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T
     else if (is_gap) gk = rows_valid;
     else if (!gaps && is_node && r == rows_valid) gk = rows_valid;  // an idle row of a ragged tile
     const bool do_ylast = !gaps && rows_valid == TY && is_node && r == 0;  // full tile, no gap threads
-    const bool spare = is_end && r < rows_valid;  // the row end of node row r
+    // The row-end role of a tile row er: the row's last dimension-0 interface,
+    // its ghost sources and ghost cells. Row-end threads take it, or, in a
+    // block of exactly n0*TY threads (no row-end threads), node thread x of the
+    // last node row takes the end of row x: that row's threads evaluate one
+    // interface fewer than row 0's, which also takes the tile's last gap.
+    const bool merged = NT < n_end;
+    const bool spare = merged ? (is_node && r == TY - 1 && x < rows_valid) : (is_end && r < rows_valid);
+    const int er = merged ? x : r;
+    const int ey = y0 + er;
 
     const int i2 = (D == 4) ? i2_in : 0;
     const int chunk = (D >= 3) ? chunk_in : 0;
@@ -267,16 +277,16 @@ __device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T
         }
         for (int sidx = t + NT; sidx < n_halo; sidx += NT) halo_slot(sidx, fp, b);  // small blocks, ragged tiles
         if (spare) {
-            const T* rowg = u + plane0 + fp + y * nx;
+            const T* rowg = u + plane0 + fp + ey * nx;
             if (per0) {
-                T* rows = b + (r + 3) * W;
+                T* rows = b + (er + 3) * W;
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
                     cp_async_elem(rows + k, rowg + nx - 3 + k);
                     cp_async_elem(rows + nx + 3 + k, rowg + k);
                 }
             } else {
-                T* e = b + o_ends + 4 * r;
+                T* e = b + o_ends + 4 * er;
                 cp_async_elem(e + 0, rowg);
                 cp_async_elem(e + 1, rowg + 1);
                 cp_async_elem(e + 2, rowg + nx - 1);
@@ -287,8 +297,8 @@ __device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T
     // Row end, after its copies into b have landed: the extrapolated x-ghost cells of its row.
     auto finish_ghosts = [&](T* b) {
         if (spare && !per0) {
-            const T* e = b + o_ends + 4 * r;
-            T* rows = b + (r + 3) * W;
+            const T* e = b + o_ends + 4 * er;
+            T* rows = b + (er + 3) * W;
             const T e0 = e[0], e1 = e[1], f0 = e[2], f1 = e[3];
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
@@ -348,6 +358,13 @@ __device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T
             T ppj;
             iface_at<SCHEME>(a[0], a[1], a[2], a[3], a[4], a[5], floor_raw, ppj, pmx);
             bz[s_pxp] = ppj;
+        }
+        // merged blocks: the last interface of row er (between node n0-1 and the ghost n0)
+        if (merged && spare) {
+            const T* a = bz + (er + 3) * W + nx;
+            T ppj, unused;
+            iface_at<SCHEME>(a[0], a[1], a[2], a[3], a[4], a[5], floor_raw, ppj, unused);
+            bz[o_pxp + er * (nx + 1) + nx] = ppj;
         }
         // y-interface of gap gk (between tile rows gk-1 and gk) of column x
         if (gk >= 0) {

@@ -339,11 +339,12 @@ def test_errors_are_reported_not_raised_on_device(ctx):
 # ---------------------------------------------------------------------------
 
 @pytest.mark.parametrize("dyn,shape,cfgs", [
-    (AIR3D, (37, 29, 23), ["1,1", "2,5", "4,23", "7,3", "13,8"]),
-    (DUBINS, (13, 11, 9, 7), ["1,1", "3,2", "11,7"]),
-    (DI, (37, 29), ["1,1", "5,1", "13,1"]),
+    # "ty,tz,1,1": blocks of n0*ty threads, whose last node row takes the row ends
+    (AIR3D, (37, 29, 23), ["1,1", "2,5", "4,23", "7,3", "13,8", "1,4,1,1", "2,5,1,1", "13,8,1,1"]),
+    (DUBINS, (13, 11, 9, 7), ["1,1", "3,2", "11,7", "3,2,1,1", "11,7,1,1"]),
+    (DI, (37, 29), ["1,1", "5,1", "13,1", "5,1,1,1"]),
     # rows of 128 threads: 4 node rows leave no room for an extra thread row in FP64 blocks (512), 8 in FP32 (1024)
-    (DI, (127, 29), ["1,1", "3,1", "4,1", "7,1", "8,1"]),
+    (DI, (127, 29), ["1,1", "3,1", "4,1", "7,1", "8,1", "8,1,1,1"]),
 ])
 @pytest.mark.parametrize("dtype", ["float64", "float32"])
 @pytest.mark.parametrize("scheme", [5, 3, 2, 1])
