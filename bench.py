@@ -51,7 +51,7 @@ WORDS_PER_NODE_STEP = 8
 # workload, from the ncu capture summarised in profiles/rows_kernel_f32_air3d101.md
 # (the 4.1 MB arrays stay in L2, so DRAM traffic is below the algorithmic bytes);
 # executed flops per node from that capture's instruction counts (interfaces shared).
-NCU_TRAFFIC_BYTES_F32 = 8.30e6
+NCU_TRAFFIC_BYTES_F32 = 8.29e6
 NCU_EXECUTED_FLOPS_PER_NODE_F32 = 330
 # GB300 unit counts: 152 SMs, 128 FP32 lanes and 2 FP64 lanes per SM, FMA = 2 flops, max SM clock 2070 MHz
 SM_COUNT, SM_MAX_MHZ = 152, 2070.0
