@@ -76,3 +76,20 @@ def test_static_step_rejects_what_does_not_fit(ctx):
     for other in (lib_method(dynamics=DI, brt=1, order=2), lib_method(dynamics=DI, brt=1, alpha_global=True)):
         assert L.hj_rk3_step_static(ctx.stream.cuda_stream, 0, L.make_grid(ok), other, L.HJ_F64, v, 0.01) == \
             L.HJ_EINVAL
+
+
+@pytest.mark.parametrize("scheme", [1, 2, 3])
+def test_static_step_runs_every_scheme(ctx, scheme):
+    # the ENO schemes also run on the row kernel inside the no-allocation step
+    import torch
+    from paper_2507_11542_gb300 import _lib as L, solver
+    dyn, spec = CASES[0][0], CASES[0][1]
+    V0 = W.sphere(spec, (0.3,) * 2, 1.0, dims=(0, 1)) + 0.1 * W.random_field(spec, 4)
+    m = lib_method(scheme=scheme, dynamics=dyn, brt=1)
+    dt = 0.8 / solver.step_bound(ctx, spec, m)
+    b = to_dev(V0, "float64")
+    st = L.hj_rk3_step_static(ctx.stream.cuda_stream, 0, L.make_grid(spec), m, L.HJ_F64, b, dt)
+    assert st == L.HJ_OK
+    torch.cuda.synchronize()
+    ref = O.rk3_step(spec, oracle_method(scheme=scheme, dynamics=dyn, brt=1), V0, dt)
+    assert rel_err(to_host(b, spec.n), ref) <= 1e-12
