@@ -281,7 +281,7 @@ StageParams stage_params(hj_ctx* ctx, const GridDev& G, const hj_method* m, int 
 }
 
 // ---------------------------------------------------------------------------
-// Row-tiled WENO5 kernel: eligibility, launch-shape tuning, dispatch
+// Row-tiled stage kernel: eligibility, launch-shape tuning, dispatch
 // ---------------------------------------------------------------------------
 
 

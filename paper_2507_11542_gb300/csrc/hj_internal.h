@@ -46,7 +46,7 @@ struct StageParams {
     int brt_min0;     // clamp ydot at zero (BRT min(0, H))
     int minv_after;   // out = min(out, Vn)
     int mode;         // StageMode
-    int scheme;       // HJ_WENO5 or HJ_ENO2 (row kernel); the one-node kernel takes it as an argument
+    int scheme;       // HJ_ENO1/2/3 or HJ_WENO5 (row kernel); the one-node kernel takes it as an argument
     double dt;
     double cv, cu;    // stage combination coefficients
     const void* u;    // stencil input
@@ -101,10 +101,10 @@ struct UpwindParams {
     double weno_floor;
 };
 
-// Launch configuration of the row-tiled WENO5 stage kernel (rows_kernel.cuh).
+// Launch configuration of the row-tiled stage kernel (rows_kernel.cuh).
 struct RowsCfg {
     int ty;         // node rows per tile
-    int nt;         // threads per block (1-D): rows_block_threads(n0, ty, ...)
+    int nt;         // threads per block (1-D): rows_block_threads(n0, ty, ...), or n0*ty (no row-end threads)
     int tz;         // planes per chunk along the streamed (last) dimension
     int nchunks;    // chunks along the streamed dimension
     int row_tiles;  // ceil(n1 / ty)
@@ -140,8 +140,8 @@ cudaError_t launch_stage_f32(const StageParams& p, int scheme, cudaStream_t s);
 cudaError_t launch_upwind_f64(const UpwindParams& p, int scheme, cudaStream_t s);
 cudaError_t launch_upwind_f32(const UpwindParams& p, int scheme, cudaStream_t s);
 
-// Row-tiled WENO5 stage kernel: defined for D = 2 (double integrator, norm,
-// advection, rotation), D = 3 (air3D, norm, advection, rotation), D = 4 (Dubins4D).
+// Row-tiled stage kernel (every scheme): defined for D = 2 (double integrator, norm,
+// advection, rotation), D = 3 (air3D, rockets, norm, advection, rotation), D = 4 (Dubins4D).
 bool rows_supported(int ndim, int dynamics);
 cudaError_t launch_rows_f64(const StageParams& p, const RowsCfg& c, cudaStream_t s);
 cudaError_t launch_rows_f32(const StageParams& p, const RowsCfg& c, cudaStream_t s);

@@ -1,4 +1,4 @@
-// rows_kernel.cuh -- the fused RK stage kernel for WENO5 on 2-4 dimensional
+// rows_kernel.cuh -- the fused RK stage kernel (WENO5, ENO1/2/3) on 2-4 dimensional
 // grids, tiled for GB300:
 //
 //  * A thread block (1-D) owns TY full rows (all n0 nodes along dimension 0)
