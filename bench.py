@@ -677,7 +677,9 @@ def main():
                  "roofline": {"bound": "alu", "achieved": FLOPS_PER_NODE_STAGE * N_CELLS / launch64_s / 1e12,
                               "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                               "frac": FLOPS_PER_NODE_STAGE * N_CELLS / launch64_s / 1e12 / FP64_PEAK_TFLOPS,
-                              "peak_source": "152 SMs x 2 FP64 lanes x 2 x 2070 MHz"}},
+                              "peak_source": "152 SMs x 2 FP64 lanes x 2 x 2070 MHz",
+                              "hbm_achieved_gbs": words_per_launch * 8 * N_CELLS / launch64_s / 1e9,
+                              "hbm_frac": words_per_launch * 8 * N_CELLS / launch64_s / 1e9 / hbm}},
         "e2e": {k: e2e[k] for k in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step")},
         "gpu_launches": r32["launches"],
         "clocks": clk.summary(),
