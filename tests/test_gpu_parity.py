@@ -146,7 +146,8 @@ def test_solve_air3d_full_horizon_fp64(ctx):
 
 
 def test_solve_dubins_full_horizon_fp64_host_io(ctx):
-    spec, V0 = W.dubins4d(15)
+    # the reduced 4-D configuration: 31^4 over the whole horizon (54 steps; the oracle takes about a minute)
+    spec, V0 = W.dubins4d(31)
     ts = W.slice_times(2.0, 3)
     got, ref, stats, steps_o, times, times_o = _solve_both(ctx, spec, V0, DUBINS, ts, host_io=True)
     assert stats["steps"] == steps_o
