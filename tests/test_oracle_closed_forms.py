@@ -205,3 +205,16 @@ def test_double_integrator_brt_lies_between_min_time_isochrons():
     assert inner.sum() > 50 and outer.sum() > 50
     assert np.all(S[0][inner] < 0.0)
     assert np.all(S[0][outer] > 0.0)
+
+
+@pytest.mark.parametrize("dyn,params", [(O.DYN_ADVECT, (0.7, -0.4)), (O.DYN_NORM, (1.0,))])
+def test_periodic_shift_invariance(dyn, params):
+    # On a grid periodic in every dimension, with dynamics that do not depend
+    # on x, solving a shifted V0 gives the shifted solution, node for node.
+    g = W.GridSpec((24, 20), (0.0, 0.0), (1.0, 1.0), (0, 1))
+    V0 = W.random_field(g, 13)
+    m = O.method(scheme=O.WENO5, dynamics=dyn, params=params, brt=O.BRT_MIN0)
+    S, _, _ = O.solve(g, m, V0, [0.2])
+    shift = (5, -3)
+    Ss, _, _ = O.solve(g, m, np.asfortranarray(np.roll(V0, shift, axis=(0, 1))), [0.2])
+    np.testing.assert_array_equal(Ss[0], np.roll(S[0], shift, axis=(0, 1)))
