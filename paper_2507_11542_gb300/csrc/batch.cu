@@ -24,6 +24,7 @@ void clear_engine(Engine* eng) {
 
 extern "C" hj_status hj_solve_batch(hj_ctx* ctx, int32_t n, const hj_problem* problems, void* const* out_slices,
                                     const int32_t* out_on_device, double* const* out_times, hj_stats* stats) {
+    NvtxRange range("hj_solve_batch");
     if (!ctx) return HJ_EINVAL;
     const auto t0 = std::chrono::steady_clock::now();
     if (n < 0 || (n > 0 && (!problems || !out_slices || !out_on_device)))

@@ -219,6 +219,7 @@ hj_status Engine::admit(const hj_problem* p, void* out, bool out_on_device, doub
 }
 
 hj_status Engine::activate(std::vector<int>* failed) {
+    NvtxRange range("activate instances");
     if (failed) failed->clear();
     if (pending_.empty()) return HJ_OK;
     std::vector<unsigned long long> words(2 * (size_t)max_slots_);
@@ -564,6 +565,7 @@ void Engine::done_slots(std::vector<int>* out) const {
 }
 
 hj_status Engine::run(int K) {
+    NvtxRange range("batched steps");
     if (K <= 0 || !any_active()) return HJ_OK;
     if (tiles_dirty_) {
         hj_status st = rebuild_tiles();

@@ -735,6 +735,7 @@ hj_status hj_step_bound(hj_ctx* ctx, const hj_grid* grid, const hj_method* metho
 
 hj_status hj_rk3_step(hj_ctx* ctx, const hj_grid* grid, const hj_method* method, int32_t dtype, void* v,
                       double dt) {
+    hj::NvtxRange range("hj_rk3_step");
     if (!ctx) return HJ_EINVAL;
     hj_status st = check_grid(ctx, grid);
     if (st) return st;
@@ -782,6 +783,7 @@ hj_status hj_rk3_stage(hj_ctx* ctx, const hj_grid* grid, const hj_method* method
 
 hj_status hj_solve(hj_ctx* ctx, const hj_problem* pr, void* out_slices, int32_t out_on_device, double* out_times,
                    hj_stats* stats) {
+    hj::NvtxRange range("hj_solve");
     if (!ctx) return HJ_EINVAL;
     const auto t0 = std::chrono::steady_clock::now();
     if (!pr) return fail(ctx, HJ_EINVAL, "problem is NULL");

@@ -4,10 +4,21 @@
 
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 namespace hj {
 
 constexpr int kMaxDim = 4;
+
+// A named NVTX range for the lifetime of the object: solves, steps, batched
+// graph replays and server admissions show up as ranges in a profiler's
+// timeline (header-only NVTX: inert unless a tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Largest block of the row-tiled kernels: FP32 blocks may hold 1024 threads
 // (<= 64 registers each), FP64 blocks 512 (<= 128 registers), since the FP64

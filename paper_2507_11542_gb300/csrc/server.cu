@@ -103,6 +103,7 @@ void engine_loop(hj_server* s) {
                 continue;
             }
         }
+        NvtxRange tick_range("server tick");  // admission, activation, steps and retirement of one tick
         hj_status st = HJ_OK;
         // cancellations of requests on the device take effect here, between blocks of steps
         for (uint64_t t : cancel_running) {
