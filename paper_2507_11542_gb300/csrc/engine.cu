@@ -433,8 +433,13 @@ hj_status Engine::shape_group(Group& g, const std::vector<int>& members, const s
             if (g.tiles.size() > g.tile_cap) {
                 cudaStreamSynchronize(stream_);
                 cudaFree(g.d_tiles);
+                g.d_tiles = nullptr;
                 g.tile_cap = g.tiles.size() * 2;
                 e = cudaMalloc(&g.d_tiles, g.tile_cap * sizeof(BatchTile));
+                if (e != cudaSuccess) {
+                    g.d_tiles = nullptr;
+                    g.tile_cap = 0;
+                }
             }
             if (e == cudaSuccess)
                 e = cudaMemcpyAsync(g.d_tiles, g.tiles.data(), g.tiles.size() * sizeof(BatchTile), cudaMemcpyHostToDevice,

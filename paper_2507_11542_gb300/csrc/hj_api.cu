@@ -34,6 +34,9 @@ hj_status fail(hj_ctx* ctx, hj_status st, const char* fmt, ...) {
 }
 
 hj_status cuda_fail(hj_ctx* ctx, cudaError_t e, const char* what) {
+    // A failed allocation is not sticky, but the runtime also records it as the
+    // thread's last error: clear it, or the next launch check would report it.
+    if (e == cudaErrorMemoryAllocation) (void)cudaGetLastError();
     return fail(ctx, e == cudaErrorMemoryAllocation ? HJ_ENOMEM : HJ_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
@@ -651,6 +654,7 @@ hj_status hj_ctx_create(int32_t device, void* cuda_stream, hj_ctx** out) {
         return HJ_ECUDA;
     }
     if (cudaMalloc(&ctx->aux, 256) != cudaSuccess) {
+        (void)cudaGetLastError();  // not sticky: leave no recorded error behind
         delete ctx;
         return HJ_ENOMEM;
     }

@@ -461,3 +461,22 @@ def test_row_kernel_widest_rows(ctx, monkeypatch, dtype, n0):
     assert rel_err(got, to_host(Vo, spec.n)) <= (1e-13 if dtype == "float64" else 1e-5)
     if dtype == "float64":
         assert rel_err(got, O.rk3_step(spec, oracle_method(dynamics=DI), V, dt)) <= TOL64
+
+
+def test_allocation_failure_is_reported_and_the_context_stays_usable(ctx):
+    # A grid whose stage buffers exceed the GPU's memory (4e10 FP64 nodes, 320 GB
+    # each): the solve fails with HJ_ENOMEM while allocating, before it reads v0,
+    # and the same context then solves a small problem normally.
+    import torch
+    from paper_2507_11542_gb300 import _lib as L, solver
+    big = W.GridSpec((4000, 4000, 2500), (-1.0,) * 3, (1.0,) * 3)
+    assert torch.cuda.get_device_properties(0).total_memory < 8 * 4000 * 4000 * 2500
+    tiny = torch.zeros(16, dtype=torch.float64, device="cuda")
+    prob, keep = L.make_problem(big, lib_method(dynamics=NORM, brt=0), L.HJ_F64, tiny.data_ptr(), True,
+                                np.array([0.1]))
+    with pytest.raises(L.HJError) as e:
+        L.hj_solve(ctx.handle, prob, tiny.data_ptr(), True, None)
+    assert e.value.status == L.HJ_ENOMEM
+    spec, V0 = W.double_integrator(21)
+    got, ref, stats, steps_o, _, _ = _solve_both(ctx, spec, V0, DI, [0.0, 0.1])
+    assert rel_err(got[-1], ref[-1]) <= TOL64
