@@ -122,7 +122,12 @@ typedef struct hj_problem {
     const void* v0;            /* initial value function, prod(n) elements */
     int32_t v0_on_device;      /* 1: v0 is device memory, 0: host memory */
     int32_t n_slices;          /* >= 1 output times */
-    const double* slice_times; /* host array, non-decreasing, >= 0 */
+    const double* slice_times; /* host array, non-decreasing, >= t0 */
+    double t0;                 /* time of v0: 0 for a fresh solve. To resume a solve from one of
+                                * its slices (a checkpoint), pass that slice as v0, the time the
+                                * solve reported for it (out_times) as t0 and the later slice
+                                * times: the steps that follow are those of the uninterrupted
+                                * solve, bit for bit. */
 } hj_problem;
 
 typedef struct hj_stats {

@@ -56,7 +56,7 @@ class hj_method(ctypes.Structure):
 class hj_problem(ctypes.Structure):
     _fields_ = [("grid", hj_grid), ("method", hj_method), ("dtype", ctypes.c_int32), ("v0", ctypes.c_void_p),
                 ("v0_on_device", ctypes.c_int32), ("n_slices", ctypes.c_int32),
-                ("slice_times", ctypes.POINTER(ctypes.c_double))]
+                ("slice_times", ctypes.POINTER(ctypes.c_double)), ("t0", ctypes.c_double)]
 
 
 class hj_stats(ctypes.Structure):
@@ -324,7 +324,8 @@ def hj_server_destroy(srv) -> None:
     load().hj_server_destroy(_vp(srv))
 
 
-def make_problem(spec, method: hj_method, dtype: int, v0_ptr: int, v0_on_device: bool, slice_times: np.ndarray):
+def make_problem(spec, method: hj_method, dtype: int, v0_ptr: int, v0_on_device: bool, slice_times: np.ndarray,
+                 t0: float = 0.0):
     """Returns (problem, keepalive) -- keep the second value alive while the problem is in use."""
     ts = np.ascontiguousarray(slice_times, dtype=np.float64)
     p = hj_problem()
@@ -335,6 +336,7 @@ def make_problem(spec, method: hj_method, dtype: int, v0_ptr: int, v0_on_device:
     p.v0_on_device = int(bool(v0_on_device))
     p.n_slices = ts.size
     p.slice_times = ts.ctypes.data_as(_P(ctypes.c_double))
+    p.t0 = float(t0)
     return p, ts
 
 

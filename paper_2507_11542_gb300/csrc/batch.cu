@@ -34,7 +34,7 @@ extern "C" hj_status hj_solve_batch(hj_ctx* ctx, int32_t n, const hj_problem* pr
         const hj_problem* pr = &problems[i];
         hj_status st;
         if ((st = check_grid(ctx, &pr->grid)) || (st = check_method(ctx, &pr->grid, &pr->method)) ||
-            (st = check_solver_settings(ctx, &pr->method)) || (st = check_slices(ctx, pr->n_slices, pr->slice_times))) {
+            (st = check_solver_settings(ctx, &pr->method)) || (st = check_slices(ctx, pr->n_slices, pr->slice_times, pr->t0))) {
             const std::string msg = ctx->last_error;
             return fail(ctx, st, "problem %d: %s", i, msg.c_str());
         }

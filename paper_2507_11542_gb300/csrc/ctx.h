@@ -65,7 +65,7 @@ size_t elem_size(int dtype);
 hj_status check_grid(hj_ctx* ctx, const hj_grid* g);
 hj_status check_method(hj_ctx* ctx, const hj_grid* g, const hj_method* m);
 hj_status check_solver_settings(hj_ctx* ctx, const hj_method* m);
-hj_status check_slices(hj_ctx* ctx, int n_slices, const double* slice_times);
+hj_status check_slices(hj_ctx* ctx, int n_slices, const double* slice_times, double t0);
 GridDev make_grid(const hj_grid* g, int extrap);
 double weno_floor(const GridDev& g, int dtype);
 hj_status ensure(hj_ctx* ctx, void** p, size_t* cap, size_t bytes);
@@ -83,6 +83,7 @@ struct Schedule {
     std::vector<long long> slice_steps;
     std::vector<double> slice_t;
 };
-void plan_schedule(const hj_method* m, double step_bound_inv, int n_slices, const double* slice_times, Schedule* s);
+void plan_schedule(const hj_method* m, double step_bound_inv, int n_slices, const double* slice_times, double t0,
+                   Schedule* s);
 
 }  // namespace hj

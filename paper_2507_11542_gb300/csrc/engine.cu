@@ -241,7 +241,7 @@ hj_status Engine::activate(std::vector<int>* failed) {
             continue;
         }
         std::memcpy(&S.sbi, &words[2 * si], sizeof(double));
-        plan_schedule(&S.prob.method, S.sbi, S.prob.n_slices, S.prob.slice_times, &S.S);
+        plan_schedule(&S.prob.method, S.sbi, S.prob.n_slices, S.prob.slice_times, S.prob.t0, &S.S);
         S.steps_total = (long long)S.S.dts.size();
         S.k_host = 0;
         // distinct positive slice step counts, the slice written there, and that step's dt

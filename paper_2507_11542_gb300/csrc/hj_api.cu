@@ -202,11 +202,12 @@ void angle_table(const hj_grid* g, std::vector<double>* out) {
     }
 }
 
-hj_status check_slices(hj_ctx* ctx, int n_slices, const double* slice_times) {
+hj_status check_slices(hj_ctx* ctx, int n_slices, const double* slice_times, double t0) {
     if (n_slices < 1 || !slice_times) return fail(ctx, HJ_EINVAL, "need at least one slice time");
+    if (!(t0 >= 0.0) || !std::isfinite(t0)) return fail(ctx, HJ_EINVAL, "t0 must be finite and >= 0");
     for (int s = 0; s < n_slices; ++s) {
         const double ts = slice_times[s];
-        if (!(ts >= 0.0) || !std::isfinite(ts)) return fail(ctx, HJ_EINVAL, "slice time %d invalid", s);
+        if (!(ts >= t0) || !std::isfinite(ts)) return fail(ctx, HJ_EINVAL, "slice time %d invalid (before t0?)", s);
         if (s > 0 && ts < slice_times[s - 1]) return fail(ctx, HJ_EINVAL, "slice times must not decrease");
     }
     return HJ_OK;
@@ -215,13 +216,14 @@ hj_status check_slices(hj_ctx* ctx, int n_slices, const double* slice_times) {
 // Listing 6: dt = min(t_f - t, maxStep, cfl * stepBound), stepBound = 1/stepBoundInv,
 // while t_f - t >= eps t_f; alpha depends on x only, so stepBound is the same at
 // every step and the whole schedule is known before the first step.
-void plan_schedule(const hj_method* m, double sbi, int n_slices, const double* slice_times, Schedule* S) {
+void plan_schedule(const hj_method* m, double sbi, int n_slices, const double* slice_times, double t0,
+                   Schedule* S) {
     S->dts.clear();
     S->slice_steps.assign(n_slices, 0);
-    S->slice_t.assign(n_slices, 0.0);
+    S->slice_t.assign(n_slices, t0);
     const double step_bound_v = 1.0 / sbi;
     const double eps = 100.0 * DBL_EPSILON;
-    double t = 0.0;
+    double t = t0;
     for (int s = 0; s < n_slices; ++s) {
         const double ts = slice_times[s];
         while (ts > t && ts - t >= eps * ts) {
@@ -798,7 +800,7 @@ hj_status hj_solve(hj_ctx* ctx, const hj_problem* pr, void* out_slices, int32_t 
     const size_t es = elem_size(pr->dtype);
     if (!es) return fail(ctx, HJ_EINVAL, "unknown dtype %d", pr->dtype);
     if (!pr->v0 || !out_slices) return fail(ctx, HJ_EINVAL, "NULL v0 or output");
-    if ((st = check_slices(ctx, pr->n_slices, pr->slice_times))) return st;
+    if ((st = check_slices(ctx, pr->n_slices, pr->slice_times, pr->t0))) return st;
     DeviceGuard guard(ctx->device);
     const GridDev G = make_grid(&pr->grid, pr->method.extrap);
     const size_t bytes = (size_t)G.total * es;
@@ -816,7 +818,7 @@ hj_status hj_solve(hj_ctx* ctx, const hj_problem* pr, void* out_slices, int32_t 
     StageParams P;
     if ((st = method_params(ctx, &pr->grid, G, &pr->method, pr->dtype, &P))) return st;
     Schedule S;
-    plan_schedule(&pr->method, sbi, pr->n_slices, pr->slice_times, &S);
+    plan_schedule(&pr->method, sbi, pr->n_slices, pr->slice_times, pr->t0, &S);
     const cudaMemcpyKind out_kind = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     size_t k = 0;
     for (int s = 0; s < pr->n_slices; ++s) {

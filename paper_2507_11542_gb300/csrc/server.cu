@@ -230,7 +230,7 @@ hj_status hj_server_submit(hj_server* s, const hj_problem* p, void* out_slices, 
     if (!s || !p || !ticket || !out_slices || !p->v0) return HJ_EINVAL;
     *ticket = 0;
     if (check_grid(nullptr, &p->grid) || check_method(nullptr, &p->grid, &p->method) ||
-        check_solver_settings(nullptr, &p->method) || check_slices(nullptr, p->n_slices, p->slice_times) ||
+        check_solver_settings(nullptr, &p->method) || check_slices(nullptr, p->n_slices, p->slice_times, p->t0) ||
         !elem_size(p->dtype))
         return HJ_EINVAL;
     if (!Engine::eligible(p)) return HJ_EINVAL;

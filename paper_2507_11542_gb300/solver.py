@@ -88,11 +88,13 @@ def rk3_stage(ctx: Context, spec, m: L.hj_method, stage: int, u, vn, out, dt: fl
     return out
 
 
-def solve(ctx: Context, spec, m: L.hj_method, V0, slice_times, out=None):
+def solve(ctx: Context, spec, m: L.hj_method, V0, slice_times, out=None, t0: float = 0.0):
     """Integrate V0 through the slice times.
 
     V0: flat CUDA tensor, or a host tensor (pinned memory recommended).
     out: optional tensor [n_slices, prod(n)] of V0's dtype (device or host).
+    t0: the time of V0; to resume from a slice of an earlier solve, pass that
+    slice and its reported time (the continuation equals the uninterrupted solve).
     Returns (out, times_reached, stats_dict).
     """
     import torch
@@ -104,18 +106,19 @@ def solve(ctx: Context, spec, m: L.hj_method, V0, slice_times, out=None):
         out = torch.empty((ts.size, N), dtype=V0.dtype, device=V0.device)
     if out.dtype != V0.dtype or out.numel() != ts.size * N or not out.is_contiguous():
         raise ValueError("out must be a contiguous [n_slices, prod(n)] tensor of V0's dtype")
-    prob, keep = L.make_problem(spec, m, L.dtype_code(V0.dtype), int(V0.data_ptr()), V0.is_cuda, ts)
+    prob, keep = L.make_problem(spec, m, L.dtype_code(V0.dtype), int(V0.data_ptr()), V0.is_cuda, ts, t0)
     times = np.zeros(ts.size)
     stats = L.hj_solve(ctx.handle, prob, int(out.data_ptr()), out.is_cuda, times)
     del keep
     return out, times, stats.as_dict()
 
 
-def solve_batch(ctx: Context, specs, methods, V0s, slice_times, outs=None):
+def solve_batch(ctx: Context, specs, methods, V0s, slice_times, outs=None, t0s=None):
     """Many independent solves in one call (hj_solve_batch).
 
     specs, methods, V0s (flat tensors, device or host), slice_times: one entry
-    per problem. outs: optional list of [n_slices, prod(n)] tensors.
+    per problem. outs: optional list of [n_slices, prod(n)] tensors. t0s:
+    optional list of the times of the V0s (see solve).
     Returns (outs, times_list, stats_list)."""
     import torch
     n = len(specs)
@@ -125,11 +128,12 @@ def solve_batch(ctx: Context, specs, methods, V0s, slice_times, outs=None):
     if outs is None:
         outs = [torch.empty((len(ts), V0.numel()), dtype=V0.dtype, device=V0.device)
                 for V0, ts in zip(V0s, slice_times)]
-    for spec, m, V0, ts, out in zip(specs, methods, V0s, slice_times, outs):
+    t0s = [0.0] * n if t0s is None else list(t0s)
+    for spec, m, V0, ts, out, t0 in zip(specs, methods, V0s, slice_times, outs, t0s):
         N = int(np.prod(spec.n))
         if V0.numel() != N or not V0.is_contiguous() or out.numel() != len(ts) * N or out.dtype != V0.dtype:
             raise ValueError("V0/out do not match the grid")
-        p, k = L.make_problem(spec, m, L.dtype_code(V0.dtype), int(V0.data_ptr()), V0.is_cuda, ts)
+        p, k = L.make_problem(spec, m, L.dtype_code(V0.dtype), int(V0.data_ptr()), V0.is_cuda, ts, t0)
         probs.append(p)
         keep.append(k)
         times.append(np.zeros(len(ts)))
@@ -147,12 +151,12 @@ class Server:
         self.handle = L.hj_server_create(ctx.handle, hbm_budget, max_slots)
         self._live = {}
 
-    def submit(self, spec, m: L.hj_method, V0, slice_times, out=None):
+    def submit(self, spec, m: L.hj_method, V0, slice_times, out=None, t0: float = 0.0):
         import torch
         ts = np.ascontiguousarray(slice_times, dtype=np.float64)
         if out is None:
             out = torch.empty((ts.size, V0.numel()), dtype=V0.dtype, device=V0.device)
-        prob, keep = L.make_problem(spec, m, L.dtype_code(V0.dtype), int(V0.data_ptr()), V0.is_cuda, ts)
+        prob, keep = L.make_problem(spec, m, L.dtype_code(V0.dtype), int(V0.data_ptr()), V0.is_cuda, ts, t0)
         times = np.zeros(ts.size)
         ticket = L.hj_server_submit(self.handle, prob, int(out.data_ptr()), out.is_cuda, times)
         self._live[ticket] = (V0, out, times, keep)

@@ -152,3 +152,19 @@ def test_batch_mix_workload_fp32_zero_sets(ctx, monkeypatch):
             assert edge < 0.1, (k, edge)
             checked += 1
     assert checked >= len(mix) // 2
+
+
+def test_batch_resumes_from_slices(ctx):
+    # the batched engine honours each problem's t0 like hj_solve
+    import torch
+    from paper_2507_11542_gb300 import solver
+    cases = _mixed("float64")[:4]
+    specs, methods = [c[0] for c in cases], [c[1] for c in cases]
+    full, t_full, _ = solver.solve_batch(ctx, specs, methods, [to_dev(c[2]) for c in cases],
+                                         [[0.2, 0.5] for _ in cases])
+    part, t_part, _ = solver.solve_batch(ctx, specs, methods, [to_dev(c[2]) for c in cases], [[0.2] for _ in cases])
+    rest, t_rest, _ = solver.solve_batch(ctx, specs, methods, [p[0].clone() for p in part], [[0.5] for _ in cases],
+                                         t0s=[float(t[0]) for t in t_part])
+    for k in range(len(cases)):
+        assert torch.equal(rest[k][0], full[k][1]), k
+        assert t_rest[k][0] == t_full[k][1]

@@ -502,3 +502,22 @@ def test_allocation_failure_is_reported_and_the_context_stays_usable(ctx):
     spec, V0 = W.double_integrator(21)
     got, ref, stats, steps_o, _, _ = _solve_both(ctx, spec, V0, DI, [0.0, 0.1])
     assert rel_err(got[-1], ref[-1]) <= TOL64
+
+
+@pytest.mark.parametrize("dtype", ["float64", "float32"])
+def test_resume_from_a_slice_equals_the_uninterrupted_solve(ctx, dtype):
+    # checkpoint / resume: a slice and its reported time restart the solve;
+    # the continuation takes the same steps, so the results are bit for bit equal
+    import torch
+    from paper_2507_11542_gb300 import _lib as L, solver
+    spec, V0 = W.air3d(27, 4.5)
+    m = lib_method(dynamics=AIR3D)
+    full, t_full, st_full = solver.solve(ctx, spec, m, to_dev(V0, dtype), [0.25, 0.6, 1.0])
+    part, t_part, st_part = solver.solve(ctx, spec, m, to_dev(V0, dtype), [0.25])
+    rest, t_rest, st_rest = solver.solve(ctx, spec, m, part[0].clone(), [0.6, 1.0], t0=float(t_part[0]))
+    assert torch.equal(rest[0], full[1]) and torch.equal(rest[1], full[2])
+    np.testing.assert_array_equal(t_rest, t_full[1:])
+    assert st_part["steps"] + st_rest["steps"] == st_full["steps"]
+    with pytest.raises(L.HJError) as e:  # a slice before t0
+        solver.solve(ctx, spec, m, part[0].clone(), [0.2], t0=0.25)
+    assert e.value.status == L.HJ_EINVAL
