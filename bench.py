@@ -694,7 +694,7 @@ def main():
         line["rockets"] = rockets
     if fp32_error:
         line["fp32_error"] = fp32_error
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:  # the host baseline is taken at N = 1 only
         rate1, el1 = cpu_oracle_rate(spec, V0, args.cpu_steps)
         procs = host_cores()
         rate, el = cpu_oracle_rate_all_cores(1, max(2, args.cpu_steps // 4), procs)
