@@ -646,7 +646,7 @@ def main():
         serve = bench_serve(ctx, args.serve_requests) if world == 1 else None
         large = bench_large(ctx, world, flush)
         rockets = bench_rockets(ctx) if world == 1 else None
-        fp32_error = bench_fp32_error(ctx, spec, V0) if rank == 0 else None
+        fp32_error = bench_fp32_error(ctx, spec, V0) if world == 1 else None
     value = world * K * N_CELLS / (r32["total_ms"] / 1e3)
     hbm, hbm_kind = measured_hbm_gbs()
     launch_s = r32["launch_ms_mean"] / 1e3
