@@ -138,3 +138,12 @@ def test_two_gloo_ranks_step_one_grid_by_halo_exchange():
         assert p.exitcode == 0
     assert bound == pytest.approx(bound_whole, rel=1e-14)
     assert err <= 1e-13
+
+
+def test_plan_splits_the_last_dimension_of_a_4d_grid():
+    g = W.GridSpec((7, 6, 5, 12), (0.0,) * 4, (1.0, 1.0, 2.0 * math.pi, 2.0), (2,))
+    plan = SL.plan(g, 4)
+    assert [(s.z0, s.z1) for s in plan] == [(0, 3), (3, 6), (6, 9), (9, 12)]
+    for s in plan:
+        assert s.spec.n[:3] == g.n[:3] and s.spec.periodic == (2,)  # theta stays periodic, v is split
+        assert s.below == (0 if s.z0 == 0 else 3) and s.above == (0 if s.z1 == 12 else 3)
