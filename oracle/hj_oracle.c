@@ -25,6 +25,12 @@
  *  R7 (Sec. 6.1): the backward reachable tube inequality is applied as
  *     V_tau = min(0, Hg_LF) at every stage (ORC_BRT_MIN0), or as
  *     V <- min(V_new, V_old) after each full step (ORC_BRT_MINV).
+ *  R12 (Sec. 4, alpha = max |H_p| "over" an unstated set of gradients; the
+ *     rockets listing passes dL, dR to its dissipation routine): with
+ *     alpha_box, alpha_d at a node is the maximum of |dHg/dp_d| over the box
+ *     of gradients spanned by that node's p- and p+ (local in x and p). The
+ *     CFL bound keeps the R5 value, the maximum over every p, which bounds
+ *     the box maximum from above.
  */
 #include "hj_oracle.h"
 
@@ -328,6 +334,101 @@ int orc_alpha(const orc_method* m, int ndim, const double* x, double* alpha) {
     }
 }
 
+/* Range [*mn, *mx] of c * p over p in [lo, hi]. */
+static void scaled_range(double c, double lo, double hi, double* mn, double* mx) {
+    double a = c * lo, b = c * hi;
+    *mn = a < b ? a : b;
+    *mx = a < b ? b : a;
+}
+
+/* max |d + k sigma| over the signs sigma the box allows (plus: +1 allowed,
+ * minus: -1 allowed). */
+static double max_over_signs(double d, double k, int plus, int minus) {
+    double best = 0.0;
+    if (plus && fabs(d + k) > best) best = fabs(d + k);
+    if (minus && fabs(d - k) > best) best = fabs(d - k);
+    return best;
+}
+
+/* R12: the maximum of |dHg/dp_d| over the box lo <= p <= hi.
+ * Linear parts of Hg contribute a constant derivative. A term c |l . p|
+ * contributes c sigma l_d, sigma = sign(l . p); the box allows sigma = +1 if
+ * max over the box of l . p >= 0 and sigma = -1 if its min <= 0 (both where
+ * the box reaches the kink). A derivative that involves two such terms takes
+ * its largest value when both signs can be equal at one point of the box,
+ * which is checked on the box directly. */
+int orc_alpha_box(const orc_method* m, int ndim, const double* x, const double* lo, const double* hi,
+                  double* alpha) {
+    const double* q = m->params;
+    switch (m->dynamics) {
+    case ORC_DYN_NORM: {
+        /* Hg = -c |p|: |dHg/dp_d| = c |p_d| / |p|, largest at the largest |p_d|
+         * and the smallest |p_j| (j != d) the box holds; at p = 0 (a box that
+         * is the single point 0 along d and holds 0 along the others) the
+         * generalized gradient is the ball of radius c. */
+        for (int d = 0; d < ndim; ++d) {
+            double big = fabs(lo[d]) > fabs(hi[d]) ? fabs(lo[d]) : fabs(hi[d]);
+            double others = 0.0;
+            for (int j = 0; j < ndim; ++j) {
+                if (j == d) continue;
+                double small = (lo[j] <= 0.0 && hi[j] >= 0.0) ? 0.0 : (fabs(lo[j]) < fabs(hi[j]) ? fabs(lo[j]) : fabs(hi[j]));
+                others += small * small;
+            }
+            if (big == 0.0) alpha[d] = (others == 0.0) ? q[0] : 0.0;
+            else alpha[d] = q[0] * big / sqrt(big * big + others);
+        }
+        return 0;
+    }
+    case ORC_DYN_AIR3D: {
+        /* Hg = p0 f0 + p1 f1 + amax |s| - bmax |p2|, s = p0 y - p1 x - p2:
+         * dHg/dp0 = f0 + amax y sign(s), dHg/dp1 = f1 - amax x sign(s),
+         * dHg/dp2 = -amax sign(s) - bmax sign(p2). */
+        if (ndim != 3) return ORC_EINVAL;
+        double va = q[0], vb = q[1], amax = q[2], bmax = q[3];
+        double f0 = -va + vb * cos(x[2]), f1 = vb * sin(x[2]);
+        double a0, b0, a1, b1;
+        scaled_range(x[1], lo[0], hi[0], &a0, &b0); /* range of p0 y */
+        scaled_range(x[0], lo[1], hi[1], &a1, &b1); /* range of p1 x */
+        double smax = b0 - a1 - lo[2], smin = a0 - b1 - hi[2];
+        int plus = smax >= 0.0, minus = smin <= 0.0;
+        alpha[0] = max_over_signs(f0, amax * x[1], plus, minus);
+        alpha[1] = max_over_signs(f1, -amax * x[0], plus, minus);
+        /* equal signs of s and p2: s >= 0 with p2 in [max(lo2, 0), hi2], or
+         * s <= 0 with p2 in [lo2, min(hi2, 0)] */
+        double top = lo[2] > 0.0 ? lo[2] : 0.0, bot = hi[2] < 0.0 ? hi[2] : 0.0;
+        int same = (top <= hi[2] && b0 - a1 - top >= 0.0) || (lo[2] <= bot && a0 - b1 - bot <= 0.0);
+        alpha[2] = same ? amax + bmax : fabs(amax - bmax);
+        return 0;
+    }
+    case ORC_DYN_ROCKETS: {
+        /* Hg = p0 f0 + p1 f1 + ue |s1| - up |s2|, s1 = p0 x - p2, s2 = p1 x + p2:
+         * dHg/dp0 = f0 + ue x sign(s1), dHg/dp1 = f1 - up x sign(s2),
+         * dHg/dp2 = -ue sign(s1) - up sign(s2). */
+        if (ndim != 3) return ORC_EINVAL;
+        double a = q[0], g = q[1], ue = q[2], up = q[3];
+        double f0 = a * cos(x[2]), f1 = a * sin(x[2]) + a - g;
+        double a0, b0, a1, b1;
+        scaled_range(x[0], lo[0], hi[0], &a0, &b0); /* range of p0 x */
+        scaled_range(x[0], lo[1], hi[1], &a1, &b1); /* range of p1 x */
+        alpha[0] = max_over_signs(f0, ue * x[0], b0 - lo[2] >= 0.0, a0 - hi[2] <= 0.0);
+        alpha[1] = max_over_signs(f1, -up * x[0], b1 + hi[2] >= 0.0, a1 + lo[2] <= 0.0);
+        /* equal signs: s1, s2 >= 0 needs p2 in [max(lo2, -b1), min(hi2, b0)];
+         * s1, s2 <= 0 needs p2 in [max(lo2, a0), min(hi2, -a1)] */
+        double l1 = lo[2] > -b1 ? lo[2] : -b1, h1 = hi[2] < b0 ? hi[2] : b0;
+        double l2 = lo[2] > a0 ? lo[2] : a0, h2 = hi[2] < -a1 ? hi[2] : -a1;
+        int same = (l1 <= h1) || (l2 <= h2);
+        alpha[2] = same ? ue + up : fabs(ue - up);
+        return 0;
+    }
+    default:
+        /* double integrator, Dubins car, advection, rotation: |dHg/dp_d| does
+         * not depend on p (a |p_d| term has derivative of magnitude bound on
+         * either side of its kink), so the box maximum is the maximum over
+         * every p (R5). */
+        return orc_alpha(m, ndim, x, alpha);
+    }
+}
+
 static void node_coords(const orc_grid* g, int64_t idx, double* x) {
     for (int d = 0; d < g->ndim; ++d) {
         int64_t i = idx % g->n[d];
@@ -355,8 +456,9 @@ int orc_alpha_max(const orc_grid* g, const orc_method* m, double* alpha_max) {
 
 /* Lax-Friedrichs term (Sec. 4, Listing 5) in time-to-go form:
  *   ydot = Hg(x, (p- + p+)/2) + sum_d alpha_d (p+_d - p-_d)/2
- * with alpha_d = alpha_d(x) (local, R5) or its maximum over the grid
- * (global), followed by the BRT clamp min(0, ydot) in ORC_BRT_MIN0 mode (R7). */
+ * with alpha_d = alpha_d(x) (local, R5), its maximum over the grid (global),
+ * or the maximum over the node's box of gradients (R12), followed by the BRT
+ * clamp min(0, ydot) in ORC_BRT_MIN0 mode (R7). */
 int orc_term(const orc_grid* g, const orc_method* m, const double* V, double* ydot) {
     if (!grid_ok(g) || !m || !V || !ydot) return ORC_EINVAL;
     int64_t total = orc_num_nodes(g);
@@ -376,7 +478,16 @@ int orc_term(const orc_grid* g, const orc_method* m, const double* V, double* yd
         node_coords(g, idx, x);
         for (int d = 0; d < D; ++d) pbar[d] = (pm[d][idx] + pp[d][idx]) / 2.0;
         rc = orc_hamiltonian(m, D, x, pbar, &hg);
-        if (rc == 0) rc = orc_alpha(m, D, x, alpha);
+        if (rc == 0 && m->alpha_box) {
+            double lo[4], hi[4];
+            for (int d = 0; d < D; ++d) {
+                lo[d] = pm[d][idx] < pp[d][idx] ? pm[d][idx] : pp[d][idx];
+                hi[d] = pm[d][idx] < pp[d][idx] ? pp[d][idx] : pm[d][idx];
+            }
+            rc = orc_alpha_box(m, D, x, lo, hi, alpha);
+        } else if (rc == 0) {
+            rc = orc_alpha(m, D, x, alpha);
+        }
         if (rc != 0) break;
         if (m->alpha_global)
             for (int d = 0; d < D; ++d) alpha[d] = amax[d];

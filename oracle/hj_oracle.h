@@ -65,6 +65,7 @@ typedef struct {
     double max_step;     /* upper bound on dt (use +inf for none) */
     int order;           /* TVD-RK order of a time step: 1, 2 or 3 (0 means 3) */
     int alpha_global;    /* 1: global Lax-Friedrichs, alpha_d = max over the grid of alpha_d(x) */
+    int alpha_box;       /* 1: alpha_d = max of |dHg/dp_d| over the node's box of gradients (R12) */
 } orc_method;
 
 int64_t orc_num_nodes(const orc_grid* g);
@@ -90,6 +91,12 @@ double orc_weno5(const double v[5], int ideal);
  * alpha_d(x) = max over controls and p of |dHg/dp_d| (Sec. 4). */
 int orc_hamiltonian(const orc_method* m, int ndim, const double* x, const double* p, double* hg);
 int orc_alpha(const orc_method* m, int ndim, const double* x, double* alpha);
+/* alpha_d = max of |dHg/dp_d| over the box of gradients p with lo[j] <= p_j <=
+ * hi[j] for every j (R12), at the node with coordinates x. Where Hg has a kink
+ * (|.| of a linear form) the derivative's one-sided values on both sides count
+ * for a box that reaches the kink; at p = 0 the norm Hamiltonian counts c. */
+int orc_alpha_box(const orc_method* m, int ndim, const double* x, const double* lo, const double* hi,
+                  double* alpha);
 
 /* ydot = [min(0, .)] (Hg(x, (p- + p+)/2) + sum_d alpha_d (p+_d - p-_d)/2) at every node. */
 int orc_term(const orc_grid* g, const orc_method* m, const double* V, double* ydot);

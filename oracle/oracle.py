@@ -22,6 +22,12 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "hj_oracle.c")
 HDR = os.path.join(HERE, "hj_oracle.h")
 LIB = os.path.join(HERE, "liboracle.so")
+# The same source compiled with floating-point contraction: every a*b + c the
+# compiler fuses rounds once instead of twice (on Arm; on targets without a
+# fused multiply-add instruction it is the same code). The distance between
+# the two builds is the oracle's own sensitivity to rounding order, the yard
+# stick of the parity tests on ill-conditioned solves.
+LIB_FMA = os.path.join(HERE, "liboracle_fma.so")
 
 ENO1, ENO2, ENO3, WENO5 = 1, 2, 3, 5
 DYN_DOUBLE_INTEGRATOR, DYN_AIR3D, DYN_DUBINS4D, DYN_NORM, DYN_ADVECT, DYN_ROTATE, DYN_ROCKETS = 1, 2, 3, 4, 5, 6, 7
@@ -32,16 +38,19 @@ _lock = threading.Lock()
 _lib = None
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (plain C99, no FMA contraction, no fast-math)."""
-    stale = (not os.path.exists(LIB)
-             or os.path.getmtime(LIB) < max(os.path.getmtime(SRC), os.path.getmtime(HDR)))
+def build(force: bool = False, fma: bool = False) -> str:
+    """Compile the oracle with gcc (plain C99, no FMA contraction, no
+    fast-math); fma=True compiles the contracted variant (LIB_FMA)."""
+    path = LIB_FMA if fma else LIB
+    stale = (not os.path.exists(path)
+             or os.path.getmtime(path) < max(os.path.getmtime(SRC), os.path.getmtime(HDR)))
     if force or stale:
-        tmp = LIB + ".%d.tmp" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off",
+        tmp = path + ".%d.tmp" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared",
+                               "-ffp-contract=fast" if fma else "-ffp-contract=off",
                                "-fno-fast-math", "-o", tmp, SRC, "-lm"])
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, path)
+    return path
 
 
 class _Grid(ctypes.Structure):
@@ -53,7 +62,7 @@ class _Method(ctypes.Structure):
     _fields_ = [("scheme", ctypes.c_int), ("dynamics", ctypes.c_int), ("params", ctypes.c_double * 8),
                 ("brt", ctypes.c_int), ("extrap", ctypes.c_int), ("weno_ideal", ctypes.c_int),
                 ("cfl", ctypes.c_double), ("max_step", ctypes.c_double), ("order", ctypes.c_int),
-                ("alpha_global", ctypes.c_int)]
+                ("alpha_global", ctypes.c_int), ("alpha_box", ctypes.c_int)]
 
 
 _DP = ctypes.POINTER(ctypes.c_double)
@@ -75,6 +84,7 @@ def lib():
             L.orc_weno5.argtypes = [_DP, ctypes.c_int]
             L.orc_hamiltonian.argtypes = [P(_Method), ctypes.c_int, _DP, _DP, _DP]
             L.orc_alpha.argtypes = [P(_Method), ctypes.c_int, _DP, _DP]
+            L.orc_alpha_box.argtypes = [P(_Method), ctypes.c_int, _DP, _DP, _DP, _DP]
             L.orc_term.argtypes = [P(_Grid), P(_Method), _DP, _DP]
             L.orc_step_bound_inv.argtypes = [P(_Grid), P(_Method), _DP]
             L.orc_rk3_step.argtypes = [P(_Grid), P(_Method), ctypes.c_double, _DP]
@@ -103,7 +113,7 @@ def _grid(g) -> _Grid:
 
 def method(scheme=WENO5, dynamics=DYN_DOUBLE_INTEGRATOR, params=(), brt=BRT_MIN0,
            extrap=EXTRAP_AWAY_FROM_ZERO, weno_ideal=False, cfl=0.8, max_step=float("inf"), order=3,
-           alpha_global=False) -> _Method:
+           alpha_global=False, alpha_box=False) -> _Method:
     M = _Method()
     M.scheme = scheme
     M.dynamics = dynamics
@@ -116,6 +126,7 @@ def method(scheme=WENO5, dynamics=DYN_DOUBLE_INTEGRATOR, params=(), brt=BRT_MIN0
     M.max_step = float(max_step)
     M.order = int(order)
     M.alpha_global = 1 if alpha_global else 0
+    M.alpha_box = 1 if alpha_box else 0
     return M
 
 
@@ -179,6 +190,16 @@ def alpha(m: _Method, x) -> np.ndarray:
     return out
 
 
+def alpha_box(m: _Method, x, lo, hi) -> np.ndarray:
+    """max of |dHg/dp_d| over the box lo <= p <= hi at coordinates x (R12)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    lo = np.ascontiguousarray(lo, dtype=np.float64)
+    hi = np.ascontiguousarray(hi, dtype=np.float64)
+    out = np.zeros(x.size)
+    _check(lib().orc_alpha_box(ctypes.byref(m), x.size, _ptr(x), _ptr(lo), _ptr(hi), _ptr(out)), "alpha_box")
+    return out
+
+
 def upwind(g, m: _Method, V, dim: int):
     V = _f64(V, g.n)
     pm = np.empty(V.shape, order="F")
@@ -220,15 +241,32 @@ def alpha_max(g, m: _Method) -> np.ndarray:
     return out[:len(g.n)]
 
 
-def solve(g, m: _Method, V0, slice_times):
-    """Returns (slices[n_slices, *n] , steps, times_reached)."""
+_lib_fma = None
+
+
+def _solve_lib(fma: bool):
+    global _lib_fma
+    if not fma:
+        return lib()
+    with _lock:
+        if _lib_fma is None:
+            L = ctypes.CDLL(build(fma=True))
+            L.orc_solve.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(_Method), _DP, ctypes.c_int, _DP, _DP,
+                                    ctypes.POINTER(ctypes.c_int64), _DP]
+            _lib_fma = L
+    return _lib_fma
+
+
+def solve(g, m: _Method, V0, slice_times, fma: bool = False):
+    """Returns (slices[n_slices, *n] , steps, times_reached); fma=True runs the
+    contracted build (LIB_FMA)."""
     V0 = _f64(V0, g.n)
     ts = np.ascontiguousarray(slice_times, dtype=np.float64)
     total = int(np.prod(g.n))
     out = np.empty(ts.size * total)
     steps = ctypes.c_int64(0)
     times = np.empty(ts.size)
-    _check(lib().orc_solve(ctypes.byref(_grid(g)), ctypes.byref(m), _ptr(V0), ts.size, _ptr(ts), _ptr(out),
-                           ctypes.byref(steps), _ptr(times)), "solve")
+    _check(_solve_lib(fma).orc_solve(ctypes.byref(_grid(g)), ctypes.byref(m), _ptr(V0), ts.size, _ptr(ts),
+                                     _ptr(out), ctypes.byref(steps), _ptr(times)), "solve")
     slices = [out[k * total:(k + 1) * total].reshape(tuple(g.n), order="F") for k in range(ts.size)]
     return np.stack(slices), int(steps.value), times

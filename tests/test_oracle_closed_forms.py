@@ -67,13 +67,14 @@ def test_rotation_full_turn_returns_the_initial_surface():
     assert errs[1] < errs[0] and errs[1] < 0.25 * (2.0 / 80), errs
 
 
-@pytest.mark.parametrize("D,N", [(2, 41), (2, 81), (3, 33)])
-def test_expanding_sphere_hopf_lax(D, N):
-    # v_t + |grad v| = 0 with V0 = |x| - r0 has V = max(|x| - tau, 0) - r0
+@pytest.mark.parametrize("D,N,box", [(2, 41, False), (2, 81, False), (3, 33, False), (2, 81, True), (3, 33, True)])
+def test_expanding_sphere_hopf_lax(D, N, box):
+    # v_t + |grad v| = 0 with V0 = |x| - r0 has V = max(|x| - tau, 0) - r0;
+    # box: dissipation local in p (R12), the same closed form
     r0, tau = 0.25, 0.5
     g = W.GridSpec((N,) * D, (-1.0,) * D, (1.0,) * D)
     V0 = W.sphere(g, (0.0,) * D, r0)
-    m = O.method(scheme=O.WENO5, dynamics=O.DYN_NORM, params=(1.0,), brt=O.BRT_NONE)
+    m = O.method(scheme=O.WENO5, dynamics=O.DYN_NORM, params=(1.0,), brt=O.BRT_NONE, alpha_box=box)
     S, _, _ = O.solve(g, m, V0, [tau])
     R = np.sqrt(sum(X ** 2 for X in g.mesh()))
     exact = np.maximum(R - tau, 0.0) - r0

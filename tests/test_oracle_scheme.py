@@ -317,3 +317,184 @@ def test_invalid_arguments_are_rejected():
         O.solve(g, O.method(dynamics=O.DYN_ADVECT, params=(1.0,)), np.zeros(10), [0.2, 0.1])
     with pytest.raises(ValueError):
         O.upwind_line(np.zeros(10), 0.1, scheme=4)
+
+
+# ---------------------------------------------------------------------------
+# Lax-Friedrichs dissipation local in p (R12): alpha_d = max of |dHg/dp_d|
+# over the box of gradients spanned by a node's p- and p+.
+# ---------------------------------------------------------------------------
+
+def _game_dynamics(dyn, params, x):
+    """f(x, a, b) on the control grid for the two-player games (a maximises,
+    b minimises), shape (41, 41, 3)."""
+    if dyn == O.DYN_AIR3D:
+        va, vb, amax, bmax = params
+        X, Y, psi = x
+        A, B = np.meshgrid(amax * U, bmax * U, indexing="ij")
+        return np.stack([-va + vb * math.cos(psi) + A * Y, vb * math.sin(psi) - A * X, B - A], axis=-1)
+    a, g, uemax, upmax = params
+    X, Z, th = x
+    UE, UP = np.meshgrid(uemax * U, upmax * U, indexing="ij")
+    return np.stack([a * math.cos(th) + UE * X, a * math.sin(th) + a - g + UP * X, UP - UE], axis=-1)
+
+
+def _generalized_slopes(F, p, tol=1e-9):
+    """max over the optimal control pairs at p of |f_d|: the extreme points of
+    the generalized gradient of Hg(p) = max_a min_b p . f(a, b) (envelope
+    theorem; tied optima give every one-sided slope)."""
+    P = F @ p
+    inner = P.min(axis=1)
+    val = inner.max()
+    best = np.zeros(F.shape[-1])
+    for i in np.nonzero(inner >= val - tol)[0]:
+        for j in np.nonzero(P[i] <= inner[i] + tol)[0]:
+            best = np.maximum(best, np.abs(F[i, j]))
+    return best
+
+
+def _box_vertices(lo, hi, planes):
+    """Vertices of the arrangement of the box faces and the switching planes
+    n . p = 0 inside the box: every cell of constant optimal controls that
+    meets the box has one of them in its closure."""
+    import itertools
+    D = len(lo)
+    rows = []
+    for d in range(D):
+        e = np.zeros(D)
+        e[d] = 1.0
+        rows += [(e, lo[d]), (e, hi[d])]
+    rows += [(np.asarray(n, dtype=float), 0.0) for n in planes]
+    out = []
+    for combo in itertools.combinations(rows, D):
+        M = np.array([r[0] for r in combo])
+        if abs(np.linalg.det(M)) < 1e-12:
+            continue
+        p = np.linalg.solve(M, np.array([r[1] for r in combo]))
+        if np.all(p >= np.asarray(lo) - 1e-12) and np.all(p <= np.asarray(hi) + 1e-12):
+            out.append(np.clip(p, lo, hi))
+    return out
+
+
+def _switching_planes(dyn, params, x):
+    # p . f is affine in each control; it switches where the control's
+    # coefficient p . (f(u = 1) - f(u = 0)) vanishes
+    F = _game_dynamics(dyn, (params[0], params[1], 1.0, 1.0), x)
+    i0, i1 = len(U) // 2, len(U) - 1   # U[20] = 0, U[40] = 1
+    return [F[i1, i0] - F[i0, i0], F[i0, i1] - F[i0, i0]]
+
+
+def _random_box(rng, D, scale):
+    kind = rng.integers(0, 4)
+    c = rng.normal(size=D) * scale
+    w = np.abs(rng.normal(size=D)) * scale * (0.05 if kind == 0 else 0.6)
+    if kind == 3:
+        w[rng.integers(0, D)] = 0.0      # flat along one dimension
+    return c - w, c + w
+
+
+@pytest.mark.parametrize("dyn,params", [(O.DYN_AIR3D, (5.0, 5.0, 1.0, 1.0)), (O.DYN_AIR3D, (3.0, 4.0, 0.7, 1.3)),
+                                        (O.DYN_ROCKETS, (1.0, 32.0, 1.0, 1.0)), (O.DYN_ROCKETS, (1.5, 9.8, 0.7, 1.2))])
+def test_box_alpha_of_the_games_is_the_largest_slope_over_the_box(dyn, params):
+    rng = np.random.default_rng(31)
+    m = O.method(dynamics=dyn, params=params)
+    for trial in range(40):
+        x = np.array([rng.uniform(-6, 6), rng.uniform(-6, 6), rng.uniform(-3, 3)])
+        lo, hi = _random_box(rng, 3, 1.0)
+        F = _game_dynamics(dyn, params, x)
+        brute = np.zeros(3)
+        for p in _box_vertices(lo, hi, _switching_planes(dyn, params, x)):
+            brute = np.maximum(brute, _generalized_slopes(F, p))
+        got = O.alpha_box(m, x, lo, hi)
+        np.testing.assert_allclose(got, brute, rtol=0, atol=1e-9, err_msg=str((trial, x, lo, hi)))
+        # never above the maximum over every p (the CFL bound stays valid)
+        assert np.all(got <= O.alpha(m, x) + 1e-12)
+    # a box holding a neighbourhood of p = 0 meets every switching pattern
+    x = np.array([1.3, -2.2, 0.7])
+    np.testing.assert_allclose(O.alpha_box(m, x, -np.ones(3), np.ones(3)), O.alpha(m, x), rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("D", [2, 3])
+def test_box_alpha_of_the_norm_is_the_largest_slope_over_the_box(D):
+    # Hg = -c |p|: dHg/dp = -c p / |p| (the ball of radius c at p = 0); over a
+    # box the largest |p_d| / |p| sits at the largest |p_d| and the smallest
+    # |p_j| the box holds, which are box ends or 0: all on the sample grid
+    import itertools
+    c = 1.7
+    m = O.method(dynamics=O.DYN_NORM, params=(c,))
+    rng = np.random.default_rng(32)
+    for trial in range(40):
+        lo, hi = _random_box(rng, D, 1.0)
+        axes = [sorted(set(list(np.linspace(l, h, 5)) + ([0.0] if l < 0.0 < h else []))) for l, h in zip(lo, hi)]
+        brute = np.zeros(D)
+        for p in itertools.product(*axes):
+            p = np.array(p)
+            r = np.sqrt(np.sum(p * p))
+            brute = np.maximum(brute, c * np.abs(p) / r if r > 0 else np.full(D, c))
+        got = O.alpha_box(m, np.zeros(D), lo, hi)
+        np.testing.assert_allclose(got, brute, rtol=1e-13, atol=1e-15, err_msg=str((trial, lo, hi)))
+    # a box that is one point p: the slope of -c|p| there
+    p = np.array([0.3, -0.4, 1.2])[:D]
+    np.testing.assert_allclose(O.alpha_box(m, np.zeros(D), p, p), c * np.abs(p) / np.linalg.norm(p), rtol=1e-15)
+    # the point p = 0: the generalized gradient is the ball of radius c
+    np.testing.assert_array_equal(O.alpha_box(m, np.zeros(D), np.zeros(D), np.zeros(D)), np.full(D, c))
+
+
+@pytest.mark.parametrize("dyn,params,D", [(O.DYN_DOUBLE_INTEGRATOR, (1.0,), 2), (O.DYN_DUBINS4D, (1.0, 0.5), 4),
+                                          (O.DYN_ADVECT, (0.7, -1.3, 0.4), 3), (O.DYN_ROTATE, (1.3,), 2)])
+def test_box_alpha_equals_the_node_alpha_where_slopes_do_not_depend_on_p(dyn, params, D):
+    # |dHg/dp_d| is the same on both sides of every |p_d| kink of these
+    # Hamiltonians, so the box maximum is the maximum over every p; checked
+    # against slopes of the brute-force control optimum at box corners
+    import itertools
+    rng = np.random.default_rng(33)
+    m = O.method(dynamics=dyn, params=params)
+    for _ in range(10):
+        x = rng.uniform(-3, 3, size=D)
+        lo, hi = _random_box(rng, D, 1.0)
+        got = O.alpha_box(m, x, lo, hi)
+        np.testing.assert_array_equal(got, O.alpha(m, x))
+        if dyn in (O.DYN_DOUBLE_INTEGRATOR, O.DYN_DUBINS4D):
+            h = 1e-7
+            for corner in itertools.product(*zip(lo, hi)):
+                p = np.array(corner) + 0.01   # off the kinks
+                for d in range(D):
+                    e = np.zeros(D)
+                    e[d] = h
+                    slope = (_brute_hg(dyn, params, x, p + e) - _brute_hg(dyn, params, x, p - e)) / (2 * h)
+                    assert abs(slope) <= got[d] + 1e-6
+
+
+def test_box_lax_friedrichs_term():
+    # 1-D norm: |dHg/dp| = c on both sides of 0, so the box term is the node term
+    g = Line(40)
+    rng = np.random.default_rng(34)
+    V = rng.normal(size=40)
+    node = O.method(scheme=O.WENO5, dynamics=O.DYN_NORM, params=(1.2,), brt=O.BRT_NONE)
+    box = O.method(scheme=O.WENO5, dynamics=O.DYN_NORM, params=(1.2,), brt=O.BRT_NONE, alpha_box=True)
+    np.testing.assert_array_equal(O.term(g, box, V), O.term(g, node, V))
+    # 2-D norm: at each node the term takes the box maximum of the node's own p-, p+
+    g2 = W.GridSpec((17, 13), (-1.0, -1.0), (1.0, 1.0))
+    V2 = np.asfortranarray(rng.normal(size=g2.n))
+    node2 = O.method(scheme=O.ENO2, dynamics=O.DYN_NORM, params=(1.2,), brt=O.BRT_NONE)
+    box2 = O.method(scheme=O.ENO2, dynamics=O.DYN_NORM, params=(1.2,), brt=O.BRT_NONE, alpha_box=True)
+    pm = [O.upwind(g2, node2, V2, d)[0] for d in range(2)]
+    pp = [O.upwind(g2, node2, V2, d)[1] for d in range(2)]
+    yb, yn = O.term(g2, box2, V2), O.term(g2, node2, V2)
+    for idx in [(0, 0), (5, 7), (16, 12), (9, 3)]:
+        lo = [min(pm[d][idx], pp[d][idx]) for d in range(2)]
+        hi = [max(pm[d][idx], pp[d][idx]) for d in range(2)]
+        a = O.alpha_box(box2, [0.0, 0.0], lo, hi)
+        half = [(pp[d][idx] - pm[d][idx]) / 2 for d in range(2)]
+        assert yb[idx] - yn[idx] == pytest.approx(sum((a[d] - 1.2) * half[d] for d in range(2)), abs=1e-12)
+
+
+def test_contracted_build_is_the_same_scheme():
+    # the oracle compiled with contraction (the parity tests' measure of its
+    # own rounding sensitivity) solves a well-conditioned problem alike
+    spec, V0 = W.double_integrator(31)
+    m = O.method(scheme=O.WENO5, dynamics=O.DYN_DOUBLE_INTEGRATOR, params=(1.0,), brt=O.BRT_MIN0)
+    a, steps_a, ta = O.solve(spec, m, V0, [0.25, 0.5])
+    b, steps_b, tb = O.solve(spec, m, V0, [0.25, 0.5], fma=True)
+    assert steps_a == steps_b
+    np.testing.assert_array_equal(ta, tb)
+    assert np.max(np.abs(a - b)) <= 1e-13 * np.max(np.abs(a))
