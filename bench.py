@@ -8,14 +8,19 @@ min(0, H). One step = one full RK3 step (one hj_rk3_step call: three fused stage
 kernels) over the whole grid; the metric is cell-updates/s (one node advanced
 one RK3 step).
 
-  value  : FP32 device-resident throughput, L2 flushed between timed steps
-  fp64   : the same in FP64
-  e2e    : hj_solve through the C ABI with pinned host buffers: V0 uploaded,
-           the first time slice (tau = 0.28) integrated, V downloaded, per step
+  value  : FP64 (the paper's precision) device-resident throughput, L2 flushed
+           between timed steps; roofline against the measured DFMA ceiling
+  fp32   : the same in FP32, with its error against the FP64 solve over the
+           whole horizon; roofline against the measured FFMA ceiling
+  e2e    : FP64 hj_solve through the C ABI with pinned host buffers: V0
+           uploaded, the first time slice (tau = 0.28) integrated, V
+           downloaded, per step
   batched / served : the 64-instance mix in one batched solve; Poisson-arriving
-           requests through the server
-  large_grids : the expanding sphere on 512^3 (FP32) and the Dubins car on
-           81^4 (FP32, FP64), device-resident steps, with their HBM fraction
+           requests through the server; FP32 with each result's error against
+           FP64 stated
+  large_grids : the expanding sphere on 512^3 (FP32: WENO5, ENO1, ENO2) and the
+           Dubins car on 81^4 (FP32, FP64), device-resident steps, with their
+           HBM fraction
   cpu_baseline / --impl reference : the FP64 CPU oracle on the host cores
 
 Run: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
@@ -47,17 +52,44 @@ E2E_TAU = 0.28
 # stage input and V^n and write one array: 3 words).
 FLOPS_PER_NODE_STAGE = 475
 WORDS_PER_NODE_STEP = 8
-# DRAM bytes (read + write) of one stage-2 launch of the FP32 row kernel on this
-# workload, from the ncu capture summarised in profiles/rows_kernel_f32_air3d101.md
-# (the 4.1 MB arrays stay in L2, so DRAM traffic is below the algorithmic bytes);
-# executed flops per node from that capture's instruction counts (interfaces shared).
-NCU_TRAFFIC_BYTES_F32 = 8.29e6
-NCU_EXECUTED_FLOPS_PER_NODE_F32 = 330
-# GB300 unit counts: 152 SMs, 128 FP32 lanes and 2 FP64 lanes per SM, FMA = 2 flops, max SM clock 2070 MHz
-SM_COUNT, SM_MAX_MHZ = 152, 2070.0
-FP32_PEAK_TFLOPS = SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
-FP64_PEAK_TFLOPS = SM_COUNT * 2 * 2 * SM_MAX_MHZ * 1e6 / 1e12
+# DRAM bytes (read + write) of one stage-2 launch of the row kernel on this
+# workload, from the ncu captures committed under profiles/ (the 101^3 arrays
+# stay in L2, so DRAM traffic is below the algorithmic bytes); None where the
+# kernel changed after the capture.
+NCU_TRAFFIC_BYTES = {"float64": None, "float32": None}
+# FP32 / FP64 lanes per SM on GB300 (FMA = 2 flops): the unit-count peak given
+# beside the measured one
+LANES_PER_SM = {"float32": 128, "float64": 2}
+SM_MAX_MHZ = 2070.0
 L2_FLUSH_BYTES = 256 << 20
+
+
+def sm_count(device: int = 0) -> int:
+    import torch
+    return int(torch.cuda.get_device_properties(device).multi_processor_count)
+
+
+def alu_peaks(device: int):
+    """Measured FFMA and DFMA ceilings of this GPU (TFLOP/s): the best of five
+    launches of the FMA-throughput probe (libhj_peak.so), beside the peaks
+    from unit counts at the maximum SM clock."""
+    import ctypes
+    from paper_2507_11542_gb300 import build
+    lib = ctypes.CDLL(build.build_peak())
+    lib.hj_alu_peak.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                ctypes.POINTER(ctypes.c_double)]
+    out = {}
+    sms = sm_count(device)
+    for name, code in (("float32", 1), ("float64", 2)):
+        tf, ms = ctypes.c_double(0), ctypes.c_double(0)
+        rc = lib.hj_alu_peak(device, code, 5, ctypes.byref(tf), ctypes.byref(ms))
+        if rc != 0:
+            raise RuntimeError("FMA-throughput probe failed (%d)" % rc)
+        out[name] = {"measured_tflops": tf.value, "probe_ms": ms.value,
+                     "unit_count_tflops": sms * LANES_PER_SM[name] * 2 * SM_MAX_MHZ * 1e6 / 1e12,
+                     "unit_count_source": "%d SMs x %d lanes x 2 flops x %.0f MHz"
+                                          % (sms, LANES_PER_SM[name], SM_MAX_MHZ)}
+    return out
 
 
 def measured_hbm_gbs():
@@ -343,7 +375,10 @@ def bench_large(ctx, world, flush):
     from paper_2507_11542_gb300 import solver, workloads as W
     hbm, _ = measured_hbm_gbs()
     out = {}
-    cases = [("sphere512_f32", W.expanding_sphere(512), solver.method(dynamics=4, params=(1.0,), brt=0), "float32", 10),
+    sphere = W.expanding_sphere(512)
+    cases = [("sphere512_f32", sphere, solver.method(dynamics=4, params=(1.0,), brt=0), "float32", 10),
+             ("sphere512_f32_eno1", sphere, solver.method(scheme=1, dynamics=4, params=(1.0,), brt=0), "float32", 10),
+             ("sphere512_f32_eno2", sphere, solver.method(scheme=2, dynamics=4, params=(1.0,), brt=0), "float32", 10),
              ("dubins81_f32", W.dubins4d(81), solver.method(dynamics=3, params=(1.0, 0.5), brt=1), "float32", 6),
              ("dubins81_f64", W.dubins4d(81), solver.method(dynamics=3, params=(1.0, 0.5), brt=1), "float64", 3)]
     out["surface512_f32"] = bench_surface(ctx, hbm)
@@ -353,7 +388,8 @@ def bench_large(ctx, world, flush):
         rate = world * n / (r["ms_per_step"] / 1e3)
         gbs = 8 * (4 if dtype == "float32" else 8) * n / (r["ms_per_step"] / 1e3) / 1e9
         out[name] = {"value": rate, "unit": "cell-updates/s", "ms_per_step": r["ms_per_step"], "steps": K,
-                     "cells": n, "hbm_achieved_gbs": gbs, "hbm_frac": gbs / hbm}
+                     "cells": n, "hbm_achieved_gbs": gbs, "hbm_frac": gbs / hbm,
+                     "stage_launch_ms_mean": r["launch_ms_mean"]}
     return out
 
 
@@ -405,14 +441,57 @@ def bench_batch(ctx, fp64_subset: int = 8, rank: int = 0, world: int = 1):
         cells64 += st["cell_updates"]
     torch.cuda.synchronize()
     el64 = time.perf_counter() - t0
+    # each FP32 result against the same instance solved in FP64 (one batched FP64 solve)
+    a64, am64, av64, at64 = _mix_problems(mix, "float64")
+    ref, _, _ = solver.solve_batch(ctx, a64, am64, av64, at64)
+    errs = [fp32_instance_error(outs[k][-1], ref[k][-1], specs[k], "%s %s" % (mix[k][0], "x".join(map(str, specs[k].n))))
+            for k in range(len(mix))]
     return {"workload": "64 solves: 32 double integrator n~U{51..201}, 32 air3D n~U{41..121}, seed 42, FP32"
                         + (", sharded over %d ranks" % world if world > 1 else ""),
             "value": rate, "unit": "cell-updates/s", "seconds": el_batch, "kernel_launches": launches,
             "serial_fp32": cells / el_serial, "serial_fp64": cells64 / el64,
-            "serial_fp64_sample": "%d of the 64 instances, one hj_solve each" % len(sub)}
+            "serial_fp64_sample": "%d of the 64 instances, one hj_solve each" % len(sub),
+            "fp32_error": error_summary(errs, "every instance at its horizon, FP32 against its FP64 solve")}
 
 
-def bench_serve(ctx, n_req: int, seed: int = 7, load: float = 0.8, budget_gb: float = 64.0):
+def fp32_instance_error(a, b, spec, name):
+    """One FP32 result against the FP64 solve of the same problem: max|dV| /
+    max|V| and the zero-level-set displacement in cells (edge crossings), and
+    whether the FP64 zero set meets an extrapolated edge (where the R3 ghost
+    rule's sign(v0) can differ between precisions)."""
+    A = a.double().cpu().numpy().reshape(spec.n, order="F")
+    B = b.double().cpu().numpy().reshape(spec.n, order="F")
+    return {"instance": name, "max_abs_err_rel": float(np.max(np.abs(A - B)) / max(np.max(np.abs(B)), 1e-300)),
+            "zero_set_displacement_cells": zero_set_displacement_cells(A, B),
+            "zero_set_meets_extrapolated_edge": meets_extrapolated_edge(B, spec)}
+
+
+def meets_extrapolated_edge(V, spec) -> bool:
+    for d in range(V.ndim):
+        if d in spec.periodic:
+            continue
+        for idx in (0, V.shape[d] - 1):
+            face = np.take(V, idx, axis=d)
+            if (face > 0).any() and (face <= 0).any():
+                return True
+    return False
+
+
+def error_summary(errs, what):
+    cells = [e["zero_set_displacement_cells"] for e in errs]
+    over = [e for e in errs if e["zero_set_displacement_cells"] >= 0.1]
+    return {"what": what, "instances": len(errs), "bar_cells": 0.1,
+            "zero_set_displacement_cells_max": max(cells), "zero_set_displacement_cells_median": float(np.median(cells)),
+            "max_abs_err_rel_max": max(e["max_abs_err_rel"] for e in errs),
+            "over_bar": len(over),
+            "over_bar_instances": [{"instance": e["instance"], "cells": e["zero_set_displacement_cells"],
+                                    "reason": ("zero set meets an extrapolated edge: the away-from-zero ghost rule "
+                                               "takes sign(v0) at the edge node, which FP32 and FP64 can disagree on"
+                                               if e["zero_set_meets_extrapolated_edge"] else "none identified")}
+                                   for e in over]}
+
+
+def bench_serve(ctx, n_req: int, seed: int = 7, load: float = 0.8, budget_gb: float = 64.0, err_samples: int = 16):
     """Poisson arrivals of reachability requests (types uniform over double
     integrator, air3D, Dubins4D; 2-D n~U{51..301}, 3-D n~U{41..161}, 4-D
     n~U{31..81}; horizon ~U[0.5, 3]; FP32) at `load` times the capacity
@@ -453,18 +532,52 @@ def bench_serve(ctx, n_req: int, seed: int = 7, load: float = 0.8, budget_gb: fl
             while time.perf_counter() < next_t:
                 time.sleep(min(0.001, max(0.0, next_t - time.perf_counter())))
             tickets.append(srv.submit(specs[k], methods[k], v0s[k], tss[k]))
-        for t in tickets:
+        sampled = set(range(0, n_req, max(1, n_req // err_samples)))
+        kept = {}
+        queued = []
+        for k, t in enumerate(tickets):
             st, out, times, stats = srv.wait(t)
             lat.append(stats["elapsed_ms"])
+            queued.append(stats["queued_ms"])
             cells += stats["cell_updates"]
+            if k in sampled:
+                kept[k] = out[-1]
         el = time.perf_counter() - t0
         launches = srv.counters()["kernel_launches"]
-    lat = np.array(lat)
+    lat, queued = np.array(lat), np.array(queued)
+    kinds = np.array([m[0] for m in mix])
+    by_class = {}
+    for kind, label in (("di", "2-D double integrator"), ("air3d", "3-D air3D"), ("dubins", "4-D Dubins car")):
+        sel = kinds == kind
+        if sel.any():
+            by_class[label] = {"requests": int(sel.sum()), "p50_ms": float(np.percentile(lat[sel], 50)),
+                               "p99_ms": float(np.percentile(lat[sel], 99)),
+                               "queued_p50_ms": float(np.percentile(queued[sel], 50)),
+                               "queued_p99_ms": float(np.percentile(queued[sel], 99))}
+    worst = np.argsort(lat)[-max(1, n_req // 100):]   # the requests at or above p99
+    # sampled results against the same requests solved in FP64 (one batched FP64 solve)
+    ks = sorted(kept)
+    s64, m64, v64, t64 = _mix_problems([mix[k] for k in ks], "float64")
+    ref, _, _ = solver.solve_batch(ctx, s64, m64, v64, t64)
+    errs = [fp32_instance_error(kept[k], ref[i][-1], specs[k], "request %d (%s %s)" % (k, mix[k][0],
+                                                                                    "x".join(map(str, specs[k].n))))
+            for i, k in enumerate(ks)]
     return {"workload": "%d requests, seed %d, Poisson arrivals at %.2f req/s (%.1fx of capacity %.2f req/s), FP32, "
                         "HBM budget %.0f GB" % (n_req, seed, rate, load, n_req / cap_s, budget_gb),
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "value": cells / el, "unit": "cell-updates/s", "capacity_req_per_s": n_req / cap_s,
-            "kernel_launches": launches}
+            "kernel_launches": launches,
+            "latency_split": {"queued_p50_ms": float(np.percentile(queued, 50)),
+                              "queued_p99_ms": float(np.percentile(queued, 99)),
+                              "on_device_p50_ms": float(np.percentile(lat - queued, 50)),
+                              "on_device_p99_ms": float(np.percentile(lat - queued, 99)),
+                              "what": "queued: submission to admission; on device: admission to retirement"},
+            "by_class": by_class,
+            "slowest_1pct": {"classes": {str(c): int(np.sum(kinds[worst] == c)) for c in set(kinds[worst])},
+                             "queued_ms_median": float(np.median(queued[worst])),
+                             "latency_ms_median": float(np.median(lat[worst]))},
+            "fp32_error": error_summary(errs, "%d sampled requests (every %d-th), FP32 against the same request "
+                                              "solved in FP64" % (len(ks), max(1, n_req // err_samples)))}
 
 
 def zero_set_displacement_cells(V, Vref):
@@ -606,10 +719,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-steps", type=int, default=24, help="oracle steps for the cpu_baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--legs", default="f32,f64,e2e,batch,serve,large",
-                    help="comma list of legs to run; f32 always runs, and a run without all of them "
-                         "(a profiling run: --legs f32, f32,f64, f32,large or f32,batch) prints timings instead of the "
-                         "JSON line")
+    ap.add_argument("--legs", default="f64,f32,e2e,batch,serve,large",
+                    help="comma list of legs to run; f64 always runs, and a run without all of them "
+                         "(a profiling run: --legs f64, f64,f32, f64,large or f64,batch) prints timings instead of "
+                         "the JSON line")
     ap.add_argument("--serve-requests", type=int, default=1000)
     args = ap.parse_args()
     world, rank, local = dist_setup()
@@ -626,65 +739,72 @@ def main():
     ctx = solver.Context(local)
     K, W_ = args.steps, max(args.warmup, 3)
     legs = set(args.legs.split(","))
-    full = {"f64", "e2e", "batch", "serve", "large"} <= legs
+    full = {"f32", "e2e", "batch", "serve", "large"} <= legs
     with ClockSampler(local) as clk:
-        r32 = bench_dtype(ctx, spec, V0, "float32", K, W_, world, flush)
-        r64 = bench_dtype(ctx, spec, V0, "float64", max(3, K // 4), 3, world, flush) if "f64" in legs else None
+        r64 = bench_dtype(ctx, spec, V0, "float64", K, W_, world, flush)
+        r32 = bench_dtype(ctx, spec, V0, "float32", K, W_, world, flush) if "f32" in legs else None
         if not full:
             # a partial run (profiling): the chosen device legs only, no JSON line
-            print("f32 leg: %.3f ms per step" % r32["ms_per_step"], flush=True)
-            if r64:
-                print("f64 leg: %.3f ms per step" % r64["ms_per_step"], flush=True)
+            print("f64 leg: %.3f ms per step" % r64["ms_per_step"], flush=True)
+            if r32:
+                print("f32 leg: %.3f ms per step" % r32["ms_per_step"], flush=True)
             if "large" in legs:
                 print("large grids: %s" % json.dumps(bench_large(ctx, world, flush)), flush=True)
             if "batch" in legs:
                 print("batched: %s" % json.dumps(bench_batch(ctx, rank=rank, world=world)), flush=True)
+            if "serve" in legs:
+                print("served: %s" % json.dumps(bench_serve(ctx, args.serve_requests)), flush=True)
             ctx.close()
             return
-        e2e = bench_e2e(ctx, spec, V0, "float32", max(3, K // 4), 2, world)
+        e2e = bench_e2e(ctx, spec, V0, "float64", max(3, K // 4), 2, world)
         batch = bench_batch(ctx, rank=rank, world=world)
         serve = bench_serve(ctx, args.serve_requests) if world == 1 else None
         large = bench_large(ctx, world, flush)
         rockets = bench_rockets(ctx) if world == 1 else None
         fp32_error = bench_fp32_error(ctx, spec, V0) if world == 1 else None
-    value = world * K * N_CELLS / (r32["total_ms"] / 1e3)
+    peaks = alu_peaks(local)
     hbm, hbm_kind = measured_hbm_gbs()
-    launch_s = r32["launch_ms_mean"] / 1e3
-    achieved_tflops = FLOPS_PER_NODE_STAGE * N_CELLS / launch_s / 1e12
-    words_per_launch = WORDS_PER_NODE_STEP / 3.0
-    achieved_gbs = words_per_launch * 4 * N_CELLS / launch_s / 1e9
-    launch64_s = r64["launch_ms_mean"] / 1e3
+    value = world * K * N_CELLS / (r64["total_ms"] / 1e3)
+
+    def roofline(r, dtype):
+        launch_s = r["launch_ms_mean"] / 1e3
+        tflops = FLOPS_PER_NODE_STAGE * N_CELLS / launch_s / 1e12
+        es = 8 if dtype == "float64" else 4
+        gbs = WORDS_PER_NODE_STEP / 3.0 * es * N_CELLS / launch_s / 1e9
+        pk = peaks[dtype]
+        return {"bound": "alu", "achieved": tflops, "peak": pk["measured_tflops"], "unit": "TFLOP/s",
+                "frac": tflops / pk["measured_tflops"], "traffic": NCU_TRAFFIC_BYTES[dtype],
+                "peak_source": "measured in this run: %s throughput probe (libhj_peak.so), best of 5 launches"
+                               % ("DFMA" if dtype == "float64" else "FFMA"),
+                "peak_unit_counts": pk["unit_count_tflops"], "peak_unit_counts_source": pk["unit_count_source"],
+                "frac_of_unit_counts": tflops / pk["unit_count_tflops"],
+                "flops_per_node": FLOPS_PER_NODE_STAGE,
+                "flops_note": "two-sided WENO5 per dimension as the method states it (the kernel evaluates each "
+                              "interface once for its two nodes); achieved = flops x 1,030,301 nodes / mean "
+                              "stage-launch time (CUDA events on the launching stream)",
+                "kernel": "rows_kernel<%s,3,AIR3D,WENO5> (fused stage)" % ("double" if dtype == "float64" else "float"),
+                "launch_ms_mean": r["launch_ms_mean"],
+                "hbm_achieved_gbs": gbs, "hbm_peak_gbs": hbm, "hbm_peak_source": hbm_kind, "hbm_frac": gbs / hbm}
+
     line = {
         "metric": "cell-updates/s (air3D 101^3 WENO5 TVD-RK3 step)",
         "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": K, "warmup": W_,
-        "ms_per_step": r32["ms_per_step"], "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "air3d-101^3 WENO5 LF TVD-RK3 CFL0.8 BRT-min0", "cells": N_CELLS,
+        "ms_per_step": r64["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "air3d-101^3 WENO5 LF TVD-RK3 CFL0.8 BRT-min0 FP64", "cells": N_CELLS,
                    "l2": "flushed (256 MiB write) before every timed step",
                    "time": "FP64 t, dt and CFL bound", "parallelism": "replicas" if world > 1 else "single"},
-        "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved_tflops / FP32_PEAK_TFLOPS, "traffic": NCU_TRAFFIC_BYTES_F32,
-                     "flops_per_node": FLOPS_PER_NODE_STAGE,
-                     "flops_note": "two-sided WENO5 per dimension as the method states it; the kernel shares each "
-                                   "interface between its two nodes and executes about %d"
-                                   % NCU_EXECUTED_FLOPS_PER_NODE_F32,
-                     "kernel": "rows_kernel<float,3,AIR3D> (fused WENO5 stage)",
-                     "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (unit counts x max clock)",
-                     "hbm_achieved_gbs": achieved_gbs, "hbm_peak_gbs": hbm, "hbm_peak_source": hbm_kind,
-                     "hbm_frac": achieved_gbs / hbm},
-        "fp64": {"value": world * N_CELLS / (r64["ms_per_step"] / 1e3), "unit": "cell-updates/s",
-                 "ms_per_step": r64["ms_per_step"], "steps": len(r64["stage_ms"]) // 3,
-                 "roofline": {"bound": "alu", "achieved": FLOPS_PER_NODE_STAGE * N_CELLS / launch64_s / 1e12,
-                              "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                              "frac": FLOPS_PER_NODE_STAGE * N_CELLS / launch64_s / 1e12 / FP64_PEAK_TFLOPS,
-                              "peak_source": "152 SMs x 2 FP64 lanes x 2 x 2070 MHz",
-                              "hbm_achieved_gbs": words_per_launch * 8 * N_CELLS / launch64_s / 1e9,
-                              "hbm_frac": words_per_launch * 8 * N_CELLS / launch64_s / 1e9 / hbm}},
+        "roofline": roofline(r64, "float64"),
+        "fp32": {"value": world * K * N_CELLS / (r32["total_ms"] / 1e3), "unit": "cell-updates/s",
+                 "ms_per_step": r32["ms_per_step"], "steps": K, "roofline": roofline(r32, "float32"),
+                 "error": fp32_error},
         "e2e": {k: e2e[k] for k in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step")},
-        "gpu_launches": r32["launches"],
+        "gpu_launches": r64["launches"],
         "clocks": clk.summary(),
+        "alu_peaks": peaks,
     }
     line["e2e"]["rk3_steps_per_call"] = e2e["rk3_steps_per_step"]
+    line["e2e"]["dtype"] = "f64"
     if batch:
         line["batched"] = batch
     if serve:
@@ -692,8 +812,6 @@ def main():
     line["large_grids"] = large
     if rockets:
         line["rockets"] = rockets
-    if fp32_error:
-        line["fp32_error"] = fp32_error
     if rank == 0 and world == 1 and not args.no_cpu_baseline:  # the host baseline is taken at N = 1 only
         rate1, el1 = cpu_oracle_rate(spec, V0, args.cpu_steps)
         procs = host_cores()

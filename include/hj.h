@@ -84,10 +84,28 @@ enum { HJ_F32 = 1, HJ_F64 = 2 };
  * g_m = v_0 + m |v_0 - v_1| sign(v_0), or the plain signed slope v_0 - v_1. */
 enum { HJ_EXTRAP_AWAY_FROM_ZERO = 0, HJ_EXTRAP_LINEAR = 1 };
 
-/* Lax-Friedrichs dissipation (Sec. 4): alpha_d(x) at each node (the default),
- * or its maximum over the grid (global LF, the rockets listing's
- * artificialDissipationGLF); the CFL bound is then sum_d max_x alpha_d / dx_d. */
-enum { HJ_ALPHA_NODE = 0, HJ_ALPHA_GLOBAL = 1 };
+/* Lax-Friedrichs dissipation (Sec. 4, alpha_d = max |dHg/dp_d|):
+ *  - HJ_ALPHA_NODE: alpha_d(x) at each node, the maximum over every p (the
+ *    default); the CFL bound is max_x sum_d alpha_d(x) / dx_d.
+ *  - HJ_ALPHA_GLOBAL: its maximum over the grid (global LF, the rockets
+ *    listing's artificialDissipationGLF); the CFL bound is then
+ *    sum_d max_x alpha_d / dx_d.
+ *  - HJ_ALPHA_BOX: at each node, the maximum of |dHg/dp_d| over the box of
+ *    gradients spanned by that node's one-sided derivatives, p_j in
+ *    [min(p-_j, p+_j), max(p-_j, p+_j)] for every j (local in x and in p).
+ *    It differs from HJ_ALPHA_NODE where |dHg/dp_d| depends on p: the norm
+ *    Hamiltonian (c |p_d| / |p|) and the |.| coupling terms of air3D and the
+ *    rockets game. The time step keeps the HJ_ALPHA_NODE bound, which bounds
+ *    every box maximum from above, so the CFL condition holds and the step
+ *    schedule is known before the first step. */
+enum { HJ_ALPHA_NODE = 0, HJ_ALPHA_GLOBAL = 1, HJ_ALPHA_BOX = 2 };
+
+/* Which stage kernel runs (hj_method.kernel): the row-tiled kernel wherever
+ * the grid allows it, else the one-node-per-thread kernel (AUTO); always the
+ * row kernel (ROWS: HJ_EINVAL where the grid does not allow it); always the
+ * one-node-per-thread kernel (NODE). Both compute the same scheme; they
+ * differ in rounding order only. */
+enum { HJ_KERNEL_AUTO = 0, HJ_KERNEL_ROWS = 1, HJ_KERNEL_NODE = 2 };
 
 /* A dense Cartesian grid (Sec. 2.1, Listing 1: createGrid(min, max, N, pdim)).
  * ndim in 1..4; n[d] >= 2 for an extrapolated dimension, >= 1 for a periodic
@@ -111,7 +129,19 @@ typedef struct hj_method {
     double cfl;        /* CFL factor in (0, 1]; Sec. 4-5 (0.8 in the workloads) */
     double max_step;   /* upper bound on dt; +inf for none (Listing 6 maxStep) */
     int32_t order;     /* TVD-RK order of a time step: 1 (forward Euler), 2 or 3 (Shu-Osher); 0 means 3 */
-    int32_t alpha_mode;/* HJ_ALPHA_NODE or HJ_ALPHA_GLOBAL */
+    int32_t alpha_mode;/* HJ_ALPHA_NODE, HJ_ALPHA_GLOBAL or HJ_ALPHA_BOX */
+    int32_t kernel;    /* HJ_KERNEL_AUTO (0), HJ_KERNEL_ROWS or HJ_KERNEL_NODE */
+    /* Launch shape of the row kernel {ty, tz, occ, merged}, all 0 (the
+     * default): picked by the context's tuner (timed once per grid, dtype,
+     * dynamics and scheme, then cached). Otherwise: ty node rows per block,
+     * tz planes per chunk along the last dimension (3-D and 4-D grids), occ 1
+     * or 2 resident blocks per SM (2: FP32 blocks of at most 544 threads),
+     * merged 1 for blocks of n0*ty threads whose last node row also takes the
+     * row ends. Results do not depend on the shape (bit for bit). A shape that
+     * does not fit the grid is HJ_EINVAL. Used by hj_term, hj_rk3_step,
+     * hj_rk3_stage and hj_solve; a problem that sets it (or kernel = NODE) is
+     * solved on its own by hj_solve_batch and refused by hj_server_submit. */
+    int32_t tile_override[4];
 } hj_method;
 
 /* One reachability / level-set solve (Sec. 5, Listing 6: odeCFL3(func, tspan, v0)). */
@@ -136,7 +166,9 @@ typedef struct hj_stats {
     int64_t kernel_launches; /* kernels of this library launched by the call */
     double step_bound_inv;   /* max_x sum_d alpha_d(x)/dx_d (Sec. 4 CFL bound) */
     double t_final;          /* time reached at the last slice */
-    double elapsed_ms;       /* wall time of the call */
+    double elapsed_ms;       /* wall time of the call (served requests: submission to retirement) */
+    double queued_ms;        /* served requests: submission to admission (the rest is on the
+                              * device); 0 for hj_solve and hj_solve_batch */
 } hj_stats;
 
 typedef struct hj_ctx hj_ctx;

@@ -28,7 +28,8 @@ HJ_ENO1, HJ_ENO2, HJ_ENO3, HJ_WENO5 = 1, 2, 3, 5
 HJ_BRT_NONE, HJ_BRT_MIN0, HJ_BRT_MINV = 0, 1, 2
 HJ_F32, HJ_F64 = 1, 2
 HJ_EXTRAP_AWAY_FROM_ZERO, HJ_EXTRAP_LINEAR = 0, 1
-HJ_ALPHA_NODE, HJ_ALPHA_GLOBAL = 0, 1
+HJ_ALPHA_NODE, HJ_ALPHA_GLOBAL, HJ_ALPHA_BOX = 0, 1, 2
+HJ_KERNEL_AUTO, HJ_KERNEL_ROWS, HJ_KERNEL_NODE = 0, 1, 2
 
 # every function include/hj.h declares (checked by the test-suite against the .so)
 EXPORTS = ["hj_ctx_create", "hj_ctx_destroy", "hj_status_str", "hj_ctx_last_error", "hj_version",
@@ -50,7 +51,8 @@ class hj_grid(ctypes.Structure):
 class hj_method(ctypes.Structure):
     _fields_ = [("scheme", ctypes.c_int32), ("dynamics", ctypes.c_int32), ("params", ctypes.c_double * 8),
                 ("brt", ctypes.c_int32), ("extrap", ctypes.c_int32), ("cfl", ctypes.c_double),
-                ("max_step", ctypes.c_double), ("order", ctypes.c_int32), ("alpha_mode", ctypes.c_int32)]
+                ("max_step", ctypes.c_double), ("order", ctypes.c_int32), ("alpha_mode", ctypes.c_int32),
+                ("kernel", ctypes.c_int32), ("tile_override", ctypes.c_int32 * 4)]
 
 
 class hj_problem(ctypes.Structure):
@@ -61,7 +63,8 @@ class hj_problem(ctypes.Structure):
 
 class hj_stats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int64), ("cell_updates", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
-                ("step_bound_inv", ctypes.c_double), ("t_final", ctypes.c_double), ("elapsed_ms", ctypes.c_double)]
+                ("step_bound_inv", ctypes.c_double), ("t_final", ctypes.c_double), ("elapsed_ms", ctypes.c_double),
+                ("queued_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -164,7 +167,7 @@ def make_grid(spec) -> hj_grid:
 
 def make_method(scheme=HJ_WENO5, dynamics=HJ_DYN_DOUBLE_INTEGRATOR, params=(), brt=HJ_BRT_MIN0,
                 extrap=HJ_EXTRAP_AWAY_FROM_ZERO, cfl=0.8, max_step=math.inf, order=3,
-                alpha_mode=HJ_ALPHA_NODE) -> hj_method:
+                alpha_mode=HJ_ALPHA_NODE, kernel=HJ_KERNEL_AUTO, tile_override=(0, 0, 0, 0)) -> hj_method:
     m = hj_method()
     m.scheme = scheme
     m.dynamics = dynamics
@@ -176,6 +179,9 @@ def make_method(scheme=HJ_WENO5, dynamics=HJ_DYN_DOUBLE_INTEGRATOR, params=(), b
     m.max_step = float(max_step)
     m.order = int(order)
     m.alpha_mode = int(alpha_mode)
+    m.kernel = int(kernel)
+    for i, t in enumerate(tile_override):
+        m.tile_override[i] = int(t)
     return m
 
 

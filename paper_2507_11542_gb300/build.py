@@ -18,6 +18,9 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OBJ = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libhj.so")
+# The measured FP32/FP64 FMA ceilings for the benchmark's roofline (not part of libhj.so).
+PEAK_SRC = os.path.join(PKG, "peak", "alu_peak.cu")
+PEAK_LIB = os.path.join(PKG, "peak", "libhj_peak.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off",
                      "-I" + os.path.join(ROOT, "include")]
@@ -57,7 +60,21 @@ def _compile(src: str, verbose: bool) -> str:
     return obj
 
 
+def build_peak(force: bool = False) -> str:
+    """Compile libhj_peak.so (the FMA-throughput probe the benchmark's roofline uses)."""
+    if not force and os.path.exists(PEAK_LIB) and os.path.getmtime(PEAK_LIB) >= os.path.getmtime(PEAK_SRC):
+        return PEAK_LIB
+    tmp = PEAK_LIB + ".%d.tmp" % os.getpid()
+    cmd = [_nvcc()] + ARCH + ["-O3", "-std=c++17", "-shared", "-Xcompiler", "-fPIC", "-o", tmp, PEAK_SRC]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("nvcc failed for %s:\n%s\n%s" % (PEAK_SRC, r.stdout, r.stderr))
+    os.replace(tmp, PEAK_LIB)
+    return PEAK_LIB
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
+    build_peak(force)
     if not force and not stale():
         return LIB
     os.makedirs(OBJ, exist_ok=True)

@@ -118,6 +118,7 @@ extern "C" hj_status hj_solve_batch(hj_ctx* ctx, int32_t n, const hj_problem* pr
     if (stats)
         for (int i = 0; i < n; ++i) {
             stats[i].elapsed_ms = ms;
+            stats[i].queued_ms = 0.0;
             stats[i].kernel_launches = ctx->launches - launches0;
         }
     return HJ_OK;

@@ -55,13 +55,9 @@ __global__ void __launch_bounds__(RowsLimits<T>::kMaxThreads)
 template <typename T, int D, int DYN, int SCHEME, int KIND>
 cudaError_t launch_batch_kind(const BatchTile* tiles, int ntiles, const BatchInst* insts, int stage, int threads,
                               size_t smem, cudaStream_t s) {
-    static bool done = false;  // benign race: setting the attribute twice is harmless
-    if (!done) {
-        cudaError_t e = cudaFuncSetAttribute(batch_kernel<T, D, DYN, SCHEME, KIND>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        if (e != cudaSuccess) return e;
-        done = true;
-    }
+    static std::atomic<unsigned long long> done{0};
+    cudaError_t e = smem_optin(batch_kernel<T, D, DYN, SCHEME, KIND>, done);
+    if (e != cudaSuccess) return e;
     batch_kernel<T, D, DYN, SCHEME, KIND><<<ntiles, threads, smem, s>>>(tiles, insts, stage);
     return cudaGetLastError();
 }

@@ -67,14 +67,19 @@ hj_status check_method(hj_ctx* ctx, const hj_grid* g, const hj_method* m);
 hj_status check_solver_settings(hj_ctx* ctx, const hj_method* m);
 hj_status check_slices(hj_ctx* ctx, int n_slices, const double* slice_times, double t0);
 GridDev make_grid(const hj_grid* g, int extrap);
-double weno_floor(const GridDev& g, int dtype);
+// WENO5 epsilon floor along dimension d, in raw-difference units
+double weno_floor(const GridDev& g, int dtype, int d);
 hj_status ensure(hj_ctx* ctx, void** p, size_t* cap, size_t bytes);
 // cos/sin of the dimension-2 coordinate from the host math library: n cosines then n sines
 void angle_table(const hj_grid* g, std::vector<double>* out);
 hj_status step_bound(hj_ctx* ctx, const hj_grid* g, const hj_method* m, double* out);
 hj_status nonfinite(hj_ctx* ctx, const void* v, long long n, int dtype, bool* bad);
-bool rows_eligible(const GridDev& G, int scheme, int dynamics, int dtype);
+// Whether the row-tiled kernel can take a grid (kernel: hj_method.kernel;
+// HJ_KERNEL_NODE makes it false).
+bool rows_eligible(const GridDev& G, int scheme, int dynamics, int dtype, int kernel = HJ_KERNEL_AUTO);
 StageParams stage_params(hj_ctx* ctx, const GridDev& G, const hj_method* m, int dtype);
+// Whether a method leaves the launch choices to the library (kernel AUTO, no tile override).
+bool default_launch(const hj_method* m);
 
 // The time schedule of one solve (Sec. 5, Listing 6): dt of every RK3 step,
 // the number of steps completed at each slice, and the time reached there.

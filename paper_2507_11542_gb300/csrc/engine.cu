@@ -111,7 +111,7 @@ hj_status Engine::init(hj_ctx* ctx, cudaStream_t stream, int max_slots, size_t a
 bool Engine::eligible(const hj_problem* p) {
     const GridDev G = make_grid(&p->grid, p->method.extrap);
     const bool rk3_node = (p->method.order == 0 || p->method.order == 3) && p->method.alpha_mode == HJ_ALPHA_NODE;
-    return rk3_node && rows_eligible(G, p->method.scheme, p->method.dynamics, p->dtype) &&
+    return rk3_node && default_launch(&p->method) && rows_eligible(G, p->method.scheme, p->method.dynamics, p->dtype) &&
            G.n[0] + 1 <= max_block_threads(p->dtype);
 }
 

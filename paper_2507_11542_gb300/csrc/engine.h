@@ -55,7 +55,7 @@ struct Slot {
     size_t o_v = 0, o_v1 = 0, o_v2 = 0, o_td = 0, o_tf = 0, o_stage = 0, o_ends = 0, o_end_slice = 0, o_end_dt = 0;
     std::vector<double> table;       // host angle tables, alive until activation
     std::vector<float> table_f;
-    hj_stats stats;
+    hj_stats stats{};
     hj_status status = HJ_OK;
     uint64_t tag = 0;                // caller's identifier (problem index or ticket)
 };

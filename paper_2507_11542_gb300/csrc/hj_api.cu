@@ -70,8 +70,17 @@ hj_status check_method(hj_ctx* ctx, const hj_grid* g, const hj_method* m) {
     for (int k = 0; k < 8; ++k)
         if (!std::isfinite(m->params[k])) return fail(ctx, HJ_EINVAL, "params[%d] is not finite", k);
     if (m->order < 0 || m->order > 3) return fail(ctx, HJ_EINVAL, "order %d not in 1..3 (0 = 3)", m->order);
-    if (m->alpha_mode != HJ_ALPHA_NODE && m->alpha_mode != HJ_ALPHA_GLOBAL)
+    if (m->alpha_mode != HJ_ALPHA_NODE && m->alpha_mode != HJ_ALPHA_GLOBAL && m->alpha_mode != HJ_ALPHA_BOX)
         return fail(ctx, HJ_EINVAL, "unknown alpha_mode %d", m->alpha_mode);
+    if (m->kernel != HJ_KERNEL_AUTO && m->kernel != HJ_KERNEL_ROWS && m->kernel != HJ_KERNEL_NODE)
+        return fail(ctx, HJ_EINVAL, "unknown kernel %d", m->kernel);
+    const int32_t* to = m->tile_override;
+    if (to[0] < 0 || to[1] < 0 || to[2] < 0 || to[2] > 2 || to[3] < 0 || to[3] > 1)
+        return fail(ctx, HJ_EINVAL, "tile_override {%d, %d, %d, %d} malformed", to[0], to[1], to[2], to[3]);
+    if (to[0] == 0 && (to[1] || to[2] || to[3]))
+        return fail(ctx, HJ_EINVAL, "tile_override needs ty >= 1 (all zero: tuned)");
+    if (to[0] > 0 && m->kernel == HJ_KERNEL_NODE)
+        return fail(ctx, HJ_EINVAL, "tile_override applies to the row kernel, not to kernel = HJ_KERNEL_NODE");
     const int D = g->ndim;
     const double* q = m->params;
     switch (m->dynamics) {
@@ -140,14 +149,16 @@ GridDev make_grid(const hj_grid* g, int extrap) {
     return G;
 }
 
-// WENO5 epsilon floor in raw-difference units: FP64 uses 1e-99 (on derivatives,
-// so scaled by the smallest dx^2); FP32 uses 1e-18 directly so that the
-// squared sums stay normal numbers.
-double weno_floor(const GridDev& g, int dtype) {
+// WENO5 epsilon floor in raw-difference units along dimension d: FP64 uses
+// 1e-99 on divided differences (Sec. 3.3, Jiang-Peng), so 1e-99 dx_d^2 on raw
+// ones; FP32 uses 1e-18 directly so that the squared sums stay normal numbers.
+double weno_floor(const GridDev& g, int dtype, int d) {
     if (dtype == HJ_F32) return 1e-18;
-    double m = g.dx[0];
-    for (int d = 1; d < g.ndim; ++d) m = std::fmin(m, g.dx[d]);
-    return 1e-99 * m * m;
+    return 1e-99 * g.dx[d] * g.dx[d];
+}
+
+bool default_launch(const hj_method* m) {
+    return m->kernel == HJ_KERNEL_AUTO && m->tile_override[0] == 0;
 }
 
 hj_status ensure(hj_ctx* ctx, void** p, size_t* cap, size_t bytes) {
@@ -281,7 +292,8 @@ StageParams stage_params(hj_ctx* ctx, const GridDev& G, const hj_method* m, int 
     P.brt_min0 = (m->brt == HJ_BRT_MIN0);
     P.trig_d = ctx->trig_d;
     P.trig_f = ctx->trig_f;
-    P.weno_floor = weno_floor(G, dtype);
+    for (int d = 0; d < kMaxDim; ++d) P.weno_floor[d] = weno_floor(G, dtype, d);
+    P.alpha_box = (m->alpha_mode == HJ_ALPHA_BOX);
     return P;
 }
 
@@ -290,12 +302,10 @@ StageParams stage_params(hj_ctx* ctx, const GridDev& G, const hj_method* m, int 
 // ---------------------------------------------------------------------------
 
 
-bool rows_eligible(const GridDev& G, int scheme, int dynamics, int dtype) {
+bool rows_eligible(const GridDev& G, int scheme, int dynamics, int dtype, int kernel) {
     if ((scheme != HJ_WENO5 && scheme != HJ_ENO1 && scheme != HJ_ENO2 && scheme != HJ_ENO3) ||
-        !rows_supported(G.ndim, dynamics))
+        !rows_supported(G.ndim, dynamics) || kernel == HJ_KERNEL_NODE)
         return false;
-    if (const char* env = std::getenv("HJ_ROWS"))  // HJ_ROWS=0: always the one-node-per-thread kernel
-        if (env[0] == '0') return false;
     for (int d = 0; d < G.ndim; ++d)
         if (G.n[d] < 4) return false;
     if (G.n[0] + 1 > rows_max_threads(dtype == HJ_F64)) return false;
@@ -385,28 +395,25 @@ std::vector<RowsCfg> rows_candidates(hj_ctx* ctx, const StageParams& P, int dtyp
     return out;
 }
 
-// The launch shape for this grid: measured once per (shape, dtype, dynamics)
-// over the model's best candidates (groups of first-stage launches writing
-// to a scratch buffer, best of two groups), then cached in the context.
-// HJ_TUNE=0 keeps the model's first choice without timing.
-hj_status rows_config(hj_ctx* ctx, const StageParams& P, int dtype, RowsCfg* out) {
+// The launch shape for this grid: measured once per (shape, dtype, dynamics,
+// scheme, dissipation) over the model's best candidates (groups of
+// first-stage launches writing to a scratch buffer, best of two groups), then
+// cached in the context. A tile override {ty, tz, occ, merged} (ty >= 1)
+// pins the shape instead; it is validated once and cached like a tuned one.
+hj_status rows_config(hj_ctx* ctx, const StageParams& P, int dtype, const int32_t* tile, RowsCfg* out) {
     const GridDev& G = P.g;
-    std::vector<long long> key = {G.ndim, P.dynamics, P.scheme, dtype, G.n[0], G.n[1], G.n[2], G.n[3]};
-    // HJ_ROWS_CFG="ty,tz", "ty,tz,occ" or "ty,tz,occ,merged" pins the shape (used to check that
-    // results do not depend on it; merged = 1: a block of n0*ty threads, without row-end threads); a
-    // pinned shape is validated once and cached like a tuned one
-    if (const char* pin = std::getenv("HJ_ROWS_CFG")) {
+    std::vector<long long> key = {G.ndim, P.dynamics, P.scheme, dtype, G.n[0], G.n[1], G.n[2], G.n[3],
+                                  rows_box_variant(P) ? 1 : 0};
+    if (tile && tile[0] > 0) {
         std::vector<long long> pkey = key;
-        for (const char* c = pin; *c; ++c) pkey.push_back(-1 - (long long)(unsigned char)*c);
+        for (int k = 0; k < 4; ++k) pkey.push_back(-1 - (long long)tile[k]);
         auto hit = ctx->rows_cache.find(pkey);
         if (hit != ctx->rows_cache.end()) {
             *out = hit->second;
             return HJ_OK;
         }
-        int ty = 0, tz = 0, occ = 1, merged = 0;
-        const int got = std::sscanf(pin, "%d,%d,%d,%d", &ty, &tz, &occ, &merged);
-        if (got >= 2 && ty >= 1 && tz >= 1 && ty <= G.n[1] && (occ == 1 || occ == 2) && (merged == 0 || merged == 1) &&
-            (G.n[0] + 1 - merged) * ty <= rows_max_threads(dtype == HJ_F64) && ty <= G.n[0]) {
+        const int ty = tile[0], tz = tile[1] > 0 ? tile[1] : 1, occ = tile[2] > 0 ? tile[2] : 1, merged = tile[3];
+        if (ty <= G.n[1] && ty <= G.n[0] && (G.n[0] + 1 - merged) * ty <= rows_max_threads(dtype == HJ_F64)) {
             *out = make_rows_cfg(G, ty, tz, dtype);
             if (merged) out->nt = G.n[0] * ty;
             out->occ = occ;
@@ -416,7 +423,8 @@ hj_status rows_config(hj_ctx* ctx, const StageParams& P, int dtype, RowsCfg* out
                 return HJ_OK;
             }
         }
-        return fail(ctx, HJ_EINVAL, "HJ_ROWS_CFG=%s does not fit this grid", pin);
+        return fail(ctx, HJ_EINVAL, "tile_override {%d, %d, %d, %d} does not fit this grid", tile[0], tile[1],
+                    tile[2], tile[3]);
     }
     auto it = ctx->rows_cache.find(key);
     if (it != ctx->rows_cache.end()) {
@@ -425,9 +433,8 @@ hj_status rows_config(hj_ctx* ctx, const StageParams& P, int dtype, RowsCfg* out
     }
     std::vector<RowsCfg> cands = rows_candidates(ctx, P, dtype);
     if (cands.empty()) return fail(ctx, HJ_EINVAL, "no launch shape fits the row kernel");
-    const char* env = std::getenv("HJ_TUNE");
     RowsCfg best = cands[0];
-    if (!(env && env[0] == '0') && cands.size() > 1) {
+    if (cands.size() > 1) {
         const size_t bytes = (size_t)G.total * (dtype == HJ_F64 ? 8 : 4);
         hj_status st = ensure(ctx, &ctx->tune_buf, &ctx->tune_bytes, bytes);
         if (st) return st;
@@ -476,23 +483,53 @@ hj_status rows_config(hj_ctx* ctx, const StageParams& P, int dtype, RowsCfg* out
     return HJ_OK;
 }
 
-cudaError_t launch_stage(hj_ctx* ctx, const StageParams& P, int scheme, int dtype) {
-    if (rows_eligible(P.g, scheme, P.dynamics, dtype)) {
+// Which kernel runs a method's stages, and the row kernel's pinned shape
+// (hj_method.kernel and tile_override).
+struct KernelPick {
+    int kernel = HJ_KERNEL_AUTO;
+    int32_t tile[4] = {0, 0, 0, 0};
+};
+KernelPick pick_of(const hj_method* m) {
+    KernelPick k;
+    k.kernel = m->kernel;
+    for (int i = 0; i < 4; ++i) k.tile[i] = m->tile_override[i];
+    return k;
+}
+
+// Refuses a kernel choice the grid cannot take (before anything is enqueued).
+hj_status check_pick(hj_ctx* ctx, const GridDev& G, const hj_method* m, int dtype) {
+    const bool rows = rows_eligible(G, m->scheme, m->dynamics, dtype, m->kernel);
+    if (m->kernel == HJ_KERNEL_ROWS && !rows)
+        return fail(ctx, HJ_EINVAL, "kernel = HJ_KERNEL_ROWS: the row kernel cannot take this grid");
+    if (m->tile_override[0] > 0 && !rows)
+        return fail(ctx, HJ_EINVAL, "tile_override: the row kernel cannot take this grid");
+    return HJ_OK;
+}
+
+// Launches one stage; HJ_EINVAL (with the context's message set) if a pinned
+// shape does not fit.
+hj_status launch_stage(hj_ctx* ctx, const StageParams& P, int scheme, int dtype, const KernelPick& k) {
+    if (rows_eligible(P.g, scheme, P.dynamics, dtype, k.kernel)) {
         StageParams Q = P;
         Q.scheme = scheme;
         RowsCfg c;
-        if (rows_config(ctx, Q, dtype, &c) != HJ_OK) return cudaErrorInvalidConfiguration;
-        return rows_launch(ctx, Q, c, dtype);
+        hj_status st = rows_config(ctx, Q, dtype, k.tile, &c);
+        if (st) return st;
+        cudaError_t e = rows_launch(ctx, Q, c, dtype);
+        return e == cudaSuccess ? HJ_OK : cuda_fail(ctx, e, "stage launch");
     }
     ctx->launches += 1;
     const StageParams Q = finalize(P);
-    return dtype == HJ_F64 ? launch_stage_f64(Q, scheme, ctx->stream) : launch_stage_f32(Q, scheme, ctx->stream);
+    cudaError_t e = dtype == HJ_F64 ? launch_stage_f64(Q, scheme, ctx->stream)
+                                    : launch_stage_f32(Q, scheme, ctx->stream);
+    return e == cudaSuccess ? HJ_OK : cuda_fail(ctx, e, "stage launch");
 }
 
 // Three fused stage launches of one TVD-RK3 step (Listing 6):
 //   V1 = V + dt L(V);  V2 = 3/4 V + 1/4 (V1 + dt L(V1));  V <- 1/3 V + 2/3 (V2 + dt L(V2))
 // with V <- min(V_new, V_old) in the last stage for the BRT min-V rule.
-hj_status rk3_launch(hj_ctx* ctx, StageParams P, int scheme, int dtype, int brt, void* v, double dt);
+hj_status rk3_launch(hj_ctx* ctx, StageParams P, int scheme, int dtype, int brt, void* v, double dt,
+                     const KernelPick& k);
 
 // One TVD-RK step of order 1, 2 or 3 (0 = 3), in place on v:
 //   1: v <- v + dt L(v)                              (one launch, then a copy)
@@ -500,44 +537,39 @@ hj_status rk3_launch(hj_ctx* ctx, StageParams P, int scheme, int dtype, int brt,
 //   3: rk3_launch
 // with v <- min(v_new, v_old) for the BRT min-V rule.
 hj_status rk_launch(hj_ctx* ctx, const StageParams& P0, int scheme, int dtype, int brt, int order, void* v,
-                    double dt, size_t bytes) {
-    if (order == 0 || order == 3) return rk3_launch(ctx, P0, scheme, dtype, brt, v, dt);
+                    double dt, size_t bytes, const KernelPick& k) {
+    if (order == 0 || order == 3) return rk3_launch(ctx, P0, scheme, dtype, brt, v, dt, k);
     StageParams P = P0;
     P.mode = kStage;
     P.dt = dt;
+    hj_status st;
     if (order == 1) {
         P.u = v; P.out = ctx->work[0]; P.cv = 0.0; P.cu = 1.0;
         P.minv_after = (brt == HJ_BRT_MINV);
         P.vn = P.minv_after ? v : nullptr;
-        cudaError_t e = launch_stage(ctx, P, scheme, dtype);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "stage launch");
+        if ((st = launch_stage(ctx, P, scheme, dtype, k))) return st;
         HJ_CUDA(ctx, cudaMemcpyAsync(v, ctx->work[0], bytes, cudaMemcpyDeviceToDevice, ctx->stream));
         return HJ_OK;
     }
     P.u = v; P.vn = nullptr; P.out = ctx->work[0]; P.cv = 0.0; P.cu = 1.0; P.minv_after = 0;
-    cudaError_t e = launch_stage(ctx, P, scheme, dtype);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "stage 1 launch");
+    if ((st = launch_stage(ctx, P, scheme, dtype, k))) return st;
     P.u = ctx->work[0]; P.vn = v; P.out = v; P.cv = 0.5; P.cu = 0.5;
     P.minv_after = (brt == HJ_BRT_MINV);
-    e = launch_stage(ctx, P, scheme, dtype);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "stage 2 launch");
-    return HJ_OK;
+    return launch_stage(ctx, P, scheme, dtype, k);
 }
 
-hj_status rk3_launch(hj_ctx* ctx, StageParams P, int scheme, int dtype, int brt, void* v, double dt) {
+hj_status rk3_launch(hj_ctx* ctx, StageParams P, int scheme, int dtype, int brt, void* v, double dt,
+                     const KernelPick& k) {
     P.mode = kStage;
     P.dt = dt;
+    hj_status st;
     P.u = v; P.vn = nullptr; P.out = ctx->work[0]; P.cv = 0.0; P.cu = 1.0; P.minv_after = 0;
-    cudaError_t e = launch_stage(ctx, P, scheme, dtype);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "stage 1 launch");
+    if ((st = launch_stage(ctx, P, scheme, dtype, k))) return st;
     P.u = ctx->work[0]; P.vn = v; P.out = ctx->work[1]; P.cv = 0.75; P.cu = 0.25;
-    e = launch_stage(ctx, P, scheme, dtype);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "stage 2 launch");
+    if ((st = launch_stage(ctx, P, scheme, dtype, k))) return st;
     P.u = ctx->work[1]; P.vn = v; P.out = v; P.cv = 1.0 / 3.0; P.cu = 2.0 / 3.0;
     P.minv_after = (brt == HJ_BRT_MINV);
-    e = launch_stage(ctx, P, scheme, dtype);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "stage 3 launch");
-    return HJ_OK;
+    return launch_stage(ctx, P, scheme, dtype, k);
 }
 
 // alpha_max[d] = max over the grid of alpha_d(x) (global Lax-Friedrichs).
@@ -701,7 +733,7 @@ hj_status hj_upwind(hj_ctx* ctx, const hj_grid* grid, const hj_method* method, i
     P.u = v;
     P.pm = pm;
     P.pp = pp;
-    P.weno_floor = weno_floor(P.g, dtype);
+    P.weno_floor = weno_floor(P.g, dtype, dim);
     ctx->launches += 1;
     cudaError_t e = dtype == HJ_F64 ? launch_upwind_f64(P, method->scheme, ctx->stream)
                                     : launch_upwind_f32(P, method->scheme, ctx->stream);
@@ -720,13 +752,13 @@ hj_status hj_term(hj_ctx* ctx, const hj_grid* grid, const hj_method* method, int
     DeviceGuard guard(ctx->device);
     if ((st = upload_trig(ctx, grid, method->dynamics))) return st;
     StageParams P;
-    if ((st = method_params(ctx, grid, make_grid(grid, method->extrap), method, dtype, &P))) return st;
+    const GridDev G = make_grid(grid, method->extrap);
+    if ((st = check_pick(ctx, G, method, dtype))) return st;
+    if ((st = method_params(ctx, grid, G, method, dtype, &P))) return st;
     P.mode = kTerm;
     P.u = v;
     P.out = ydot;
-    cudaError_t e = launch_stage(ctx, P, method->scheme, dtype);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "term launch");
-    return HJ_OK;
+    return launch_stage(ctx, P, method->scheme, dtype, pick_of(method));
 }
 
 hj_status hj_step_bound(hj_ctx* ctx, const hj_grid* grid, const hj_method* method, double* out) {
@@ -751,12 +783,13 @@ hj_status hj_rk3_step(hj_ctx* ctx, const hj_grid* grid, const hj_method* method,
     if (!(dt >= 0.0) || !std::isfinite(dt)) return fail(ctx, HJ_EINVAL, "dt must be finite and >= 0");
     DeviceGuard guard(ctx->device);
     const GridDev G = make_grid(grid, method->extrap);
+    if ((st = check_pick(ctx, G, method, dtype))) return st;
     if ((st = ensure_work(ctx, (size_t)G.total * elem_size(dtype)))) return st;
     if ((st = upload_trig(ctx, grid, method->dynamics))) return st;
     StageParams P;
     if ((st = method_params(ctx, grid, G, method, dtype, &P))) return st;
     return rk_launch(ctx, P, method->scheme, dtype, method->brt, method->order, v, dt,
-                     (size_t)G.total * elem_size(dtype));
+                     (size_t)G.total * elem_size(dtype), pick_of(method));
 }
 
 hj_status hj_rk3_stage(hj_ctx* ctx, const hj_grid* grid, const hj_method* method, int32_t dtype, int32_t stage,
@@ -773,7 +806,9 @@ hj_status hj_rk3_stage(hj_ctx* ctx, const hj_grid* grid, const hj_method* method
     DeviceGuard guard(ctx->device);
     if ((st = upload_trig(ctx, grid, method->dynamics))) return st;
     StageParams P;
-    if ((st = method_params(ctx, grid, make_grid(grid, method->extrap), method, dtype, &P))) return st;
+    const GridDev G = make_grid(grid, method->extrap);
+    if ((st = check_pick(ctx, G, method, dtype))) return st;
+    if ((st = method_params(ctx, grid, G, method, dtype, &P))) return st;
     P.mode = kStage;
     P.dt = dt;
     P.u = u;
@@ -782,9 +817,7 @@ hj_status hj_rk3_stage(hj_ctx* ctx, const hj_grid* grid, const hj_method* method
     P.cv = stage == 1 ? 0.0 : (stage == 2 ? 0.75 : 1.0 / 3.0);
     P.cu = stage == 1 ? 1.0 : (stage == 2 ? 0.25 : 2.0 / 3.0);
     P.minv_after = (stage == 3 && method->brt == HJ_BRT_MINV);
-    cudaError_t e = launch_stage(ctx, P, method->scheme, dtype);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "stage launch");
-    return HJ_OK;
+    return launch_stage(ctx, P, method->scheme, dtype, pick_of(method));
 }
 
 hj_status hj_solve(hj_ctx* ctx, const hj_problem* pr, void* out_slices, int32_t out_on_device, double* out_times,
@@ -803,6 +836,7 @@ hj_status hj_solve(hj_ctx* ctx, const hj_problem* pr, void* out_slices, int32_t 
     if ((st = check_slices(ctx, pr->n_slices, pr->slice_times, pr->t0))) return st;
     DeviceGuard guard(ctx->device);
     const GridDev G = make_grid(&pr->grid, pr->method.extrap);
+    if ((st = check_pick(ctx, G, &pr->method, pr->dtype))) return st;
     const size_t bytes = (size_t)G.total * es;
     const long long launches0 = ctx->launches;
     if ((st = ensure_work(ctx, bytes))) return st;
@@ -824,7 +858,7 @@ hj_status hj_solve(hj_ctx* ctx, const hj_problem* pr, void* out_slices, int32_t 
     for (int s = 0; s < pr->n_slices; ++s) {
         for (; k < (size_t)S.slice_steps[s]; ++k)
             if ((st = rk_launch(ctx, P, pr->method.scheme, pr->dtype, pr->method.brt, pr->method.order, V, S.dts[k],
-                                bytes)))
+                                bytes, pick_of(&pr->method))))
                 return st;
         HJ_CUDA(ctx, cudaMemcpyAsync(static_cast<char*>(out_slices) + (size_t)s * bytes, V, bytes, out_kind,
                                      ctx->stream));
@@ -842,6 +876,7 @@ hj_status hj_solve(hj_ctx* ctx, const hj_problem* pr, void* out_slices, int32_t 
         stats->t_final = t;
         stats->elapsed_ms =
             std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        stats->queued_ms = 0.0;
     }
     return HJ_OK;
 }

@@ -10,6 +10,18 @@ namespace hj {
 
 constexpr int kMaxDim = 4;
 
+// Row and batch kernels take the dynamics as a template parameter. For the
+// Hamiltonians whose |dHg/dp_d| depends on p (norm, air3D, rockets), the
+// variant with Lax-Friedrichs dissipation local in p (HJ_ALPHA_BOX) is the
+// dynamics id plus kDynBox; the other dynamics need no such variant (their
+// box maximum is the maximum over every p).
+constexpr int kDynBox = 8;
+__host__ __device__ constexpr int dyn_base(int dyn) { return dyn & (kDynBox - 1); }
+__host__ __device__ constexpr bool dyn_is_box(int dyn) { return (dyn & kDynBox) != 0; }
+__host__ __device__ inline bool box_differs(int dyn) {
+    return dyn == 4 /* HJ_DYN_NORM */ || dyn == 2 /* HJ_DYN_AIR3D */ || dyn == 7 /* HJ_DYN_ROCKETS */;
+}
+
 // A named NVTX range for the lifetime of the object: solves, steps, batched
 // graph replays and server admissions show up as ranges in a profiler's
 // timeline (header-only NVTX: inert unless a tool is attached).
@@ -65,16 +77,22 @@ struct StageParams {
     void* out;
     const double* trig_d;  // cos, sin of the dimension-2 coordinate: [cos(0..n2-1), sin(0..n2-1)]
     const float* trig_f;
-    double weno_floor;     // additive floor of the WENO5 epsilon, in raw-difference units
+    double weno_floor[kMaxDim];   // additive floor of the WENO5 epsilon per dimension, in raw-difference units
     double half_inv_dx[kMaxDim];  // 1 / (2 dx): raw differences to (p- + p+)/2 and (p+ - p-)/2
     int alpha_global;             // dissipation alpha_d = alpha_g[d] (global LF) instead of alpha_d(x)
     double alpha_g[kMaxDim];
+    int alpha_box;                // dissipation alpha_d = max |dHg/dp_d| over the node's box of gradients
     // FP32 copies of the scalars above, so that FP32 kernels do no FP64 arithmetic
     float lo_f[kMaxDim], dx_f[kMaxDim], inv_dx_f[kMaxDim], half_inv_dx_f[kMaxDim], alpha_g_f[kMaxDim];
+    float weno_floor_f[kMaxDim];
     float params_f[8];
-    float dt_f, cv_f, cu_f, weno_floor_f;
+    float dt_f, cv_f, cu_f;
     int has_vn;            // the stage reads Vn (cv != 0 or minv_after)
 };
+
+// Whether a row-kernel launch takes a variant with dissipation local in p
+// (rows_f32_box.cu, rows_f64_box.cu).
+inline bool rows_box_variant(const StageParams& p) { return p.alpha_box && box_differs(p.dynamics); }
 
 // Fills the FP32 copies and has_vn from the FP64 fields (call before launching).
 inline StageParams finalize(StageParams p) {
@@ -85,12 +103,12 @@ inline StageParams finalize(StageParams p) {
         p.half_inv_dx[d] = 0.5 * p.g.inv_dx[d];
         p.half_inv_dx_f[d] = (float)p.half_inv_dx[d];
         p.alpha_g_f[d] = (float)p.alpha_g[d];
+        p.weno_floor_f[d] = (float)p.weno_floor[d];
     }
     for (int k = 0; k < 8; ++k) p.params_f[k] = (float)p.params[k];
     p.dt_f = (float)p.dt;
     p.cv_f = (float)p.cv;
     p.cu_f = (float)p.cu;
-    p.weno_floor_f = (float)p.weno_floor;
     p.has_vn = (p.mode == kStage) && (p.cv != 0.0 || p.minv_after);
     return p;
 }

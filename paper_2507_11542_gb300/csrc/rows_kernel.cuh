@@ -24,6 +24,7 @@
 // 6.1) and the TVD-RK3 stage combination (Sec. 5), one store per node.
 #pragma once
 
+#include <atomic>
 #include <type_traits>
 
 #include "stencil.cuh"
@@ -155,7 +156,6 @@ __device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T
     const T* __restrict__ u = R.u;
     const T* __restrict__ vn = R.vn;
     T* __restrict__ out = R.out;
-    const T floor_raw = SP<T>::floor(P);
     const bool per0 = g.periodic_mask & 1u, per1 = (g.periodic_mask >> 1) & 1u;
     const int extrap = g.extrap;
 
@@ -201,6 +201,7 @@ __device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T
     const int i2 = (D == 4) ? i2_in : 0;
     const int chunk = (D >= 3) ? chunk_in : 0;
     constexpr int SD = (D >= 3) ? D - 1 : 0;  // streamed dimension
+    const T fl0 = SP<T>::floor(P, 0), fl1 = SP<T>::floor(P, 1), flS = SP<T>::floor(P, SD);
     const int ns = (D >= 3) ? g.n[SD] : 1;
     const int zbeg = (D >= 3) ? chunk * tz : 0;
     const int zend = (D >= 3) ? min(ns, zbeg + tz) : 1;
@@ -229,9 +230,9 @@ __device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T
     T xc[D];
 #pragma unroll
     for (int d = 0; d < D; ++d) xc[d] = T(0);
-    if constexpr (uses_coord<D, DYN>(0)) xc[0] = SP<T>::lo(P, 0) + T(x) * SP<T>::dx(P, 0);
-    if constexpr (uses_coord<D, DYN>(1)) xc[1] = SP<T>::lo(P, 1) + T(y) * SP<T>::dx(P, 1);
-    if constexpr (D == 4 && uses_coord<D, DYN>(2)) xc[2] = SP<T>::lo(P, 2) + T(i2) * SP<T>::dx(P, 2);
+    if constexpr (uses_coord<D, DYN>(0)) xc[0] = coord(SP<T>::lo(P, 0), x, SP<T>::dx(P, 0));
+    if constexpr (uses_coord<D, DYN>(1)) xc[1] = coord(SP<T>::lo(P, 1), y, SP<T>::dx(P, 1));
+    if constexpr (D == 4 && uses_coord<D, DYN>(2)) xc[2] = coord(SP<T>::lo(P, 2), i2, SP<T>::dx(P, 2));
     const T* __restrict__ trig = Trig<T>::get(P);
     T cos2 = T(0), sin2 = T(0);  // angle of dimension 2 (fixed for the block in 4-D)
     if constexpr (D == 4 && uses_angle<D, DYN>()) {
@@ -318,7 +319,7 @@ __device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T
 #pragma unroll
         for (int k = 0; k < 6; ++k) q[k] = line_value(ucol, zbeg - 3 + k, ns, (long long)sS, perS, extrap);
         T unused;
-        iface_at<SCHEME>(q[0], q[1], q[2], q[3], q[4], q[5], floor_raw, unused, carry);
+        iface_at<SCHEME>(q[0], q[1], q[2], q[3], q[4], q[5], flS, unused, carry);
 #pragma unroll
         for (int k = 0; k < 5; ++k) q[k] = q[k + 1];
     }
@@ -356,27 +357,27 @@ __device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T
         if (do_xrow) {
             const T* a = bz + s_xrow;
             T ppj;
-            iface_at<SCHEME>(a[0], a[1], a[2], a[3], a[4], a[5], floor_raw, ppj, pmx);
+            iface_at<SCHEME>(a[0], a[1], a[2], a[3], a[4], a[5], fl0, ppj, pmx);
             bz[s_pxp] = ppj;
         }
         // merged blocks: the last interface of row er (between node n0-1 and the ghost n0)
         if (merged && spare) {
             const T* a = bz + (er + 3) * W + nx;
             T ppj, unused;
-            iface_at<SCHEME>(a[0], a[1], a[2], a[3], a[4], a[5], floor_raw, ppj, unused);
+            iface_at<SCHEME>(a[0], a[1], a[2], a[3], a[4], a[5], fl0, ppj, unused);
             bz[o_pxp + er * (nx + 1) + nx] = ppj;
         }
         // y-interface of gap gk (between tile rows gk-1 and gk) of column x
         if (gk >= 0) {
             const T* c = bz + s_ycol;
             T ppj;
-            iface_at<SCHEME>(c[0], c[W], c[2 * W], c[3 * W], c[4 * W], c[5 * W], floor_raw, ppj, pmy);
+            iface_at<SCHEME>(c[0], c[W], c[2 * W], c[3 * W], c[4 * W], c[5 * W], fl1, ppj, pmy);
             bz[s_pyw] = ppj;
         }
         if (do_ylast) {
             const T* c = bz + s_ylast;
             T ppj, unused;
-            iface_at<SCHEME>(c[0], c[W], c[2 * W], c[3 * W], c[4 * W], c[5 * W], floor_raw, ppj, unused);
+            iface_at<SCHEME>(c[0], c[W], c[2 * W], c[3 * W], c[4 * W], c[5 * W], fl1, ppj, unused);
             bz[o_pyp + TY * nx + x] = ppj;
         }
         cp_async_wait_all();  // this thread's copies into plane z+1
@@ -400,7 +401,7 @@ __device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T
             T next = T(0);
             if constexpr (D >= 3) {
                 T pps;
-                iface_at<SCHEME>(q[0], q[1], q[2], q[3], q[4], q[5], floor_raw, pps, next);
+                iface_at<SCHEME>(q[0], q[1], q[2], q[3], q[4], q[5], flS, pps, next);
                 pb[SD] = (carry + pps) * hS;
                 dd[SD] = (pps - carry) * hS;
             }
@@ -409,14 +410,15 @@ __device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T
                 T v[7];
                 gather7<T>(u, (long long)(col + fz), i2, g.n[2], g.stride[2], (g.periodic_mask >> 2) & 1u, extrap, v);
                 T pm2, pp2, unused0, unused1;
-                iface_at<SCHEME>(v[0], v[1], v[2], v[3], v[4], v[5], floor_raw, unused0, pm2);
-                iface_at<SCHEME>(v[1], v[2], v[3], v[4], v[5], v[6], floor_raw, pp2, unused1);
+                const T fl2 = SP<T>::floor(P, 2);
+                iface_at<SCHEME>(v[0], v[1], v[2], v[3], v[4], v[5], fl2, unused0, pm2);
+                iface_at<SCHEME>(v[1], v[2], v[3], v[4], v[5], v[6], fl2, pp2, unused1);
                 const T h2 = SP<T>::half_inv_dx(P, 2);
                 pb[2] = (pm2 + pp2) * h2;
                 dd[2] = (pp2 - pm2) * h2;
-                if constexpr (uses_coord<D, DYN>(3)) xc[3] = SP<T>::lo(P, 3) + T(z) * SP<T>::dx(P, 3);
+                if constexpr (uses_coord<D, DYN>(3)) xc[3] = coord(SP<T>::lo(P, 3), z, SP<T>::dx(P, 3));
             }
-            if constexpr (D == 3 && uses_coord<D, DYN>(2)) xc[2] = SP<T>::lo(P, 2) + T(z) * SP<T>::dx(P, 2);
+            if constexpr (D == 3 && uses_coord<D, DYN>(2)) xc[2] = coord(SP<T>::lo(P, 2), z, SP<T>::dx(P, 2));
             T yd = lf_combine<T, D, DYN>(P, xc, cosz, sinz, pb, dd);
             if (brt0) yd = fmin(yd, T(0));
             const int flat = col + fz;
@@ -466,16 +468,26 @@ inline void rows_shape(const StageParams& p, const RowsCfg& c, dim3& grid, dim3&
     smem = rows_smem_bytes<T>(p.g.n[0], c.ty);
 }
 
+// Opts a kernel into 200 KiB of dynamic shared memory, once per device (the
+// attribute belongs to the current device's copy of the kernel); `done` holds
+// one bit per device already set (devices 0..63; others are set every call).
+template <typename K>
+inline cudaError_t smem_optin(K* kernel, std::atomic<unsigned long long>& done) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = (dev >= 0 && dev < 64) ? (1ull << dev) : 0ull;
+    if (bit && (done.load(std::memory_order_relaxed) & bit)) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    done.fetch_or(bit, std::memory_order_relaxed);  // setting the attribute twice (a race) is harmless
+    return cudaSuccess;
+}
+
 template <typename T, int D, int DYN, int SCHEME, int KIND, int OCC>
 inline cudaError_t rows_prepare() {
-    static bool done = false;  // benign race: setting the attribute twice is harmless
-    if (!done) {
-        cudaError_t e = cudaFuncSetAttribute(rows_kernel<T, D, DYN, SCHEME, KIND, OCC>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        if (e != cudaSuccess) return e;
-        done = true;
-    }
-    return cudaSuccess;
+    static std::atomic<unsigned long long> done{0};
+    return smem_optin(rows_kernel<T, D, DYN, SCHEME, KIND, OCC>, done);
 }
 
 template <typename T, int D, int DYN, int SCHEME, int KIND, int OCC>
@@ -578,5 +590,17 @@ int rows_bps_eno3(const StageParams& p, const RowsCfg& c) {
     case 4 * 16 + HJ_DYN_DUBINS4D: return FN<T, 4, HJ_DYN_DUBINS4D>(__VA_ARGS__);     \
     default: break;                                                                    \
     }
+
+// The variants with dissipation local in p (HJ_ALPHA_BOX) of the dynamics
+// whose slopes depend on p; instantiated in translation units of their own.
+#define HJ_ROWS_BOX_DISPATCH(FN, T, ...)                                                                  \
+    switch (p.g.ndim * 16 + p.dynamics) {                                                                  \
+    case 2 * 16 + HJ_DYN_NORM: return FN<T, 2, HJ_DYN_NORM + kDynBox>(__VA_ARGS__);                        \
+    case 3 * 16 + HJ_DYN_NORM: return FN<T, 3, HJ_DYN_NORM + kDynBox>(__VA_ARGS__);                        \
+    case 3 * 16 + HJ_DYN_AIR3D: return FN<T, 3, HJ_DYN_AIR3D + kDynBox>(__VA_ARGS__);                      \
+    case 3 * 16 + HJ_DYN_ROCKETS: return FN<T, 3, HJ_DYN_ROCKETS + kDynBox>(__VA_ARGS__);                  \
+    default: break;                                                                                        \
+    }
+
 
 }  // namespace hj

@@ -40,6 +40,8 @@ struct Request {
     hj_status status = HJ_OK;
     hj_stats stats{};
     Clock::time_point t_submit;
+    Clock::time_point t_admit;  // when it left the queue (valid once state >= 1)
+    bool admitted = false;
 };
 }  // namespace
 
@@ -70,7 +72,9 @@ void finish(hj_server* s, uint64_t ticket, hj_status st) {
     Request& r = s->reqs[ticket];
     r.state = 2;
     r.status = st;
-    r.stats.elapsed_ms = std::chrono::duration<double, std::milli>(Clock::now() - r.t_submit).count();
+    const Clock::time_point now = Clock::now();
+    r.stats.elapsed_ms = std::chrono::duration<double, std::milli>(now - r.t_submit).count();
+    r.stats.queued_ms = std::chrono::duration<double, std::milli>((r.admitted ? r.t_admit : now) - r.t_submit).count();
     s->completed += 1;
 }
 
@@ -97,6 +101,8 @@ void engine_loop(hj_server* s) {
                 admit.push_back(s->queue.front());
                 s->queue.pop_front();
                 r.state = 1;
+                r.admitted = true;
+                r.t_admit = Clock::now();
             }
             if (admit.empty() && cancel_running.empty() && !s->eng.any_active()) {
                 s->cv_work.wait_for(lk, std::chrono::milliseconds(20));
@@ -130,6 +136,7 @@ void engine_loop(hj_server* s) {
             if (ast == HJ_EBUSY) {  // the arena is fragmented: retry later, keeping arrival order
                 for (size_t b = admit.size(); b-- > a;) {
                     s->reqs[admit[b]].state = 0;
+                    s->reqs[admit[b]].admitted = false;
                     s->queue.push_front(admit[b]);
                 }
                 break;

@@ -22,7 +22,6 @@ __global__ void __launch_bounds__(kBX * kBY) stage_kernel(const StageParams P) {
     const T* __restrict__ u = static_cast<const T*>(P.u);
     const T* __restrict__ vn = static_cast<const T*>(P.vn);
     T* __restrict__ out = static_cast<T*>(P.out);
-    const T floor_raw = SP<T>::floor(P);
     for (int z = blockIdx.z; z < nz; z += gridDim.z) {
         int idx[4] = {i0, i1, 0, 0};
         if (D > 2) { idx[2] = z % g.n[2]; }
@@ -35,7 +34,7 @@ __global__ void __launch_bounds__(kBX * kBY) stage_kernel(const StageParams P) {
         for (int d = 0; d < D; ++d) {
             T v[7];
             gather7<T>(u, flat, idx[d], g.n[d], g.stride[d], (g.periodic_mask >> d) & 1u, g.extrap, v);
-            upwind_pair<T, SCHEME>(v, g.dx[d], g.inv_dx[d], floor_raw, pm[d], pp[d]);
+            upwind_pair<T, SCHEME>(v, g.dx[d], g.inv_dx[d], SP<T>::floor(P, d), pm[d], pp[d]);
         }
         T y = lf_term<T, D>(P, idx, pm, pp);
         if (P.brt_min0) y = fmin(y, T(0));

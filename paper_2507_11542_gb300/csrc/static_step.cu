@@ -31,6 +31,12 @@ static __device__ __align__(256) unsigned char g_static_scratch[kScratchBytes];
 constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
 void* g_scratch_ptr[kMaxDevices] = {nullptr};
+// (n, lo, dx) of the angle tables last written into each device's scratch
+double g_angle_key[kMaxDevices][3];
+bool g_angle_valid[kMaxDevices] = {false};
+// host staging of the tables (filled under g_mutex; consumed by the copy before it returns)
+double g_angle_host_d[2 * HJ_STATIC_MAX_ANGLES];
+float g_angle_host_f[2 * HJ_STATIC_MAX_ANGLES];
 
 // Device address of the scratch on `device` (which must be current).
 hj_status scratch_address(int device, unsigned char** out) {
@@ -44,16 +50,32 @@ hj_status scratch_address(int device, unsigned char** out) {
     return HJ_OK;
 }
 
-// cos and sin of the dimension-2 coordinate, both precisions, on the device.
-__global__ void angle_tables(int n, double lo, double dx, double* td, float* tf) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const double x = lo + (double)i * dx;
-    const double c = cos(x), s = sin(x);
-    td[i] = c;
-    td[n + i] = s;
-    tf[i] = (float)c;
-    tf[n + i] = (float)s;
+// cos and sin of the dimension-2 coordinate, both precisions, from the host
+// math library (the values every other entry point uses), written into the
+// scratch on `stream` when the device's tables hold other angles. The copy
+// from pageable host memory has consumed its source when it returns.
+hj_status angle_tables(int device, int n, double lo, double dx, double* td, float* tf, cudaStream_t stream) {
+    std::lock_guard<std::mutex> lock(g_mutex);
+    double* key = g_angle_key[device];
+    if (g_angle_valid[device] && key[0] == (double)n && key[1] == lo && key[2] == dx) return HJ_OK;
+    for (int i = 0; i < n; ++i) {
+        const double x = lo + (double)i * dx;
+        g_angle_host_d[i] = std::cos(x);
+        g_angle_host_d[n + i] = std::sin(x);
+        g_angle_host_f[i] = (float)g_angle_host_d[i];
+        g_angle_host_f[n + i] = (float)g_angle_host_d[n + i];
+    }
+    g_angle_valid[device] = false;
+    if (cudaMemcpyAsync(td, g_angle_host_d, 2 * (size_t)n * sizeof(double), cudaMemcpyHostToDevice, stream) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(tf, g_angle_host_f, 2 * (size_t)n * sizeof(float), cudaMemcpyHostToDevice, stream) !=
+            cudaSuccess)
+        return HJ_ECUDA;
+    key[0] = (double)n;
+    key[1] = lo;
+    key[2] = dx;
+    g_angle_valid[device] = true;
+    return HJ_OK;
 }
 
 bool grid_valid(const hj_grid* g) {
@@ -74,6 +96,9 @@ bool method_valid(const hj_grid* g, const hj_method* m) {
     for (int k = 0; k < 8; ++k)
         if (!std::isfinite(m->params[k])) return false;
     if ((m->order != 0 && m->order != 3) || m->alpha_mode != HJ_ALPHA_NODE) return false;
+    if (m->kernel != HJ_KERNEL_AUTO && m->kernel != HJ_KERNEL_NODE) return false;
+    for (int k = 0; k < 4; ++k)
+        if (m->tile_override[k] != 0) return false;
     const int D = g->ndim;
     switch (m->dynamics) {
     case HJ_DYN_DOUBLE_INTEGRATOR: return D == 2 && m->params[0] >= 0;
@@ -132,6 +157,7 @@ extern "C" hj_status hj_rk3_step_static(void* cuda_stream, int32_t device, const
     if (device < 0 || device >= kMaxDevices) return HJ_EINVAL;
     long long total = 1;
     for (int d = 0; d < grid->ndim; ++d) {
+        if (grid->n[d] > HJ_STATIC_MAX_NODES) return HJ_EINVAL;  // checked before the product can overflow
         total *= grid->n[d];
         if (total > HJ_STATIC_MAX_NODES) return HJ_EINVAL;  // beyond the fixed scratch
     }
@@ -160,7 +186,6 @@ extern "C" hj_status hj_rk3_step_static(void* cuda_stream, int32_t device, const
     GridDev& G = P.g;
     G.ndim = grid->ndim;
     long long stride = 1;
-    double min_dx = 0.0;
     for (int d = 0; d < 4; ++d) {
         if (d < grid->ndim) {
             const bool periodic = (grid->periodic_mask >> d) & 1u;
@@ -170,7 +195,6 @@ extern "C" hj_status hj_rk3_step_static(void* cuda_stream, int32_t device, const
             G.lo[d] = grid->lo[d];
             G.dx[d] = (grid->hi[d] - grid->lo[d]) / (periodic ? (double)grid->n[d] : (double)(grid->n[d] - 1));
             G.inv_dx[d] = 1.0 / G.dx[d];
-            min_dx = d == 0 ? G.dx[d] : std::fmin(min_dx, G.dx[d]);
         } else {
             G.n[d] = 1;
             G.stride[d] = stride;
@@ -184,17 +208,14 @@ extern "C" hj_status hj_rk3_step_static(void* cuda_stream, int32_t device, const
     P.dynamics = method->dynamics;
     for (int k = 0; k < 8; ++k) P.params[k] = method->params[k];
     P.brt_min0 = method->brt == HJ_BRT_MIN0;
-    P.weno_floor = dtype == HJ_F32 ? 1e-18 : 1e-99 * min_dx * min_dx;
+    // WENO5 epsilon floor per dimension in raw-difference units (1e-99 on divided differences in FP64)
+    for (int d = 0; d < 4; ++d) P.weno_floor[d] = dtype == HJ_F32 ? 1e-18 : 1e-99 * G.dx[d] * G.dx[d];
 
     void* w1 = base;
     void* w2 = base + kStageBytes;
     double* td = reinterpret_cast<double*>(base + 2 * kStageBytes);
     float* tf = reinterpret_cast<float*>(base + 2 * kStageBytes + (size_t)HJ_STATIC_MAX_ANGLES * 2 * sizeof(double));
-    if (angles) {
-        const int n2 = G.n[2];
-        angle_tables<<<(n2 + 127) / 128, 128, 0, stream>>>(n2, G.lo[2], G.dx[2], td, tf);
-        if (cudaGetLastError() != cudaSuccess) return HJ_ECUDA;
-    }
+    if (angles && (st = angle_tables(device, G.n[2], G.lo[2], G.dx[2], td, tf, stream)) != HJ_OK) return st;
     P.trig_d = td;
     P.trig_f = tf;
 
@@ -202,7 +223,8 @@ extern "C" hj_status hj_rk3_step_static(void* cuda_stream, int32_t device, const
     if (cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return HJ_ECUDA;
     RowsCfg cfg;
     P.scheme = method->scheme;
-    const bool rows = pick_rows(P, dtype, sm_count, &cfg);  // every scheme has a row-kernel variant
+    // every scheme has a row-kernel variant; kernel = HJ_KERNEL_NODE asks for the other kernel
+    const bool rows = method->kernel != HJ_KERNEL_NODE && pick_rows(P, dtype, sm_count, &cfg);
 
     // stage 1: w1 = v + dt L(v); stage 2: w2 = 3/4 v + 1/4 (w1 + dt L(w1));
     // stage 3: v = 1/3 v + 2/3 (w2 + dt L(w2)) [then min(., v) for the min-V rule]

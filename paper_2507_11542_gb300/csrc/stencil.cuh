@@ -195,6 +195,13 @@ __device__ __forceinline__ void upwind_pair(const T v[7], double dx, double inv_
     }
 }
 
+// Node coordinate lo + i dx (Sec. 2.1), the product and the sum rounded
+// separately, as the host and the oracle compute it: a fused multiply-add
+// would move coordinates near 0 by a rounding step, and the dissipation local
+// in p takes sign decisions on products with them.
+template <typename T>
+__device__ __forceinline__ T coord(T lo, int i, T dx) { return add_rn(lo, mul_rn(T(i), dx)); }
+
 // Scalars of a stage launch in the kernel's precision.
 template <typename T> struct SP;
 template <> struct SP<double> {
@@ -207,7 +214,7 @@ template <> struct SP<double> {
     static __device__ __forceinline__ double dt(const StageParams& P) { return P.dt; }
     static __device__ __forceinline__ double cv(const StageParams& P) { return P.cv; }
     static __device__ __forceinline__ double cu(const StageParams& P) { return P.cu; }
-    static __device__ __forceinline__ double floor(const StageParams& P) { return P.weno_floor; }
+    static __device__ __forceinline__ double floor(const StageParams& P, int d) { return P.weno_floor[d]; }
 };
 template <> struct SP<float> {
     static __device__ __forceinline__ float lo(const StageParams& P, int d) { return P.lo_f[d]; }
@@ -219,7 +226,7 @@ template <> struct SP<float> {
     static __device__ __forceinline__ float dt(const StageParams& P) { return P.dt_f; }
     static __device__ __forceinline__ float cv(const StageParams& P) { return P.cv_f; }
     static __device__ __forceinline__ float cu(const StageParams& P) { return P.cu_f; }
-    static __device__ __forceinline__ float floor(const StageParams& P) { return P.weno_floor_f; }
+    static __device__ __forceinline__ float floor(const StageParams& P, int d) { return P.weno_floor_f[d]; }
 };
 
 // ---------------------------------------------------------------------------
@@ -234,7 +241,81 @@ template <> struct Trig<float>  { static __device__ __forceinline__ const float*
 // angle table of the launch).
 template <int D, int DYN>
 __host__ __device__ constexpr bool uses_angle() {
-    return (DYN == HJ_DYN_AIR3D && D == 3) || (DYN == HJ_DYN_DUBINS4D && D == 4) || (DYN == HJ_DYN_ROCKETS && D == 3);
+    constexpr int B = dyn_base(DYN);
+    return (B == HJ_DYN_AIR3D && D == 3) || (B == HJ_DYN_DUBINS4D && D == 4) || (B == HJ_DYN_ROCKETS && D == 3);
+}
+
+// max |d + k sigma| over the signs sigma a box of gradients allows (plus: +1,
+// minus: -1).
+template <typename T>
+__device__ __forceinline__ T max_over_signs(T d, T k, bool plus, bool minus) {
+    T best = T(0);
+    if (plus) best = fmax(best, fabs(d + k));
+    if (minus) best = fmax(best, fabs(d - k));
+    return best;
+}
+
+// Lax-Friedrichs dissipation local in p (HJ_ALPHA_BOX; Sec. 4, alpha_d =
+// max |dHg/dp_d|): the maximum over the node's box of gradients, p_j from
+// pb_j - |dd_j| to pb_j + |dd_j| (the node's p- and p+). A linear part of Hg
+// has a constant slope; a term k |l . p| has slope k sign(l . p) l_d, where
+// the box allows sign +1 if the maximum of l . p over the box is >= 0 and -1
+// if its minimum is <= 0. A slope made of two such terms is largest where
+// both signs can be equal at one point of the box, which is checked on the
+// box. The norm Hamiltonian -c|p| has |dHg/dp_d| = c |p_d| / |p|, largest at
+// the largest |p_d| and the smallest |p_j| (j != d) the box holds; at p = 0
+// its generalized gradient is the ball of radius c.
+template <typename T, int D, int B>
+__device__ __forceinline__ void box_alpha(const StageParams& P, const T* xc, T c, T s, const T* pb, const T* dd,
+                                          T* a) {
+    const auto q = [&P](int k) { return SP<T>::param(P, k); };
+    T lo[D], hi[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        const T w = fabs(dd[d]);
+        lo[d] = pb[d] - w;
+        hi[d] = pb[d] + w;
+    }
+    if constexpr (B == HJ_DYN_NORM) {
+        const T cn = q(0);
+        T small2[D];
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            const T m = (lo[j] <= T(0) && hi[j] >= T(0)) ? T(0) : fmin(fabs(lo[j]), fabs(hi[j]));
+            small2[j] = m * m;
+        }
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            const T big = fmax(fabs(lo[d]), fabs(hi[d]));
+            T others = T(0);
+#pragma unroll
+            for (int j = 0; j < D; ++j)
+                if (j != d) others += small2[j];
+            a[d] = (big == T(0)) ? ((others == T(0)) ? cn : T(0)) : cn * big / sqrt(big * big + others);
+        }
+    } else if constexpr (B == HJ_DYN_AIR3D && D == 3) {
+        const T va = q(0), vb = q(1), amax = q(2), bmax = q(3);
+        const T f0 = -va + vb * c, f1 = vb * s;
+        const T y0 = lo[0] * xc[1], y1 = hi[0] * xc[1];  // range of p0 y
+        const T x0 = lo[1] * xc[0], x1 = hi[1] * xc[0];  // range of p1 x
+        const T a0 = fmin(y0, y1), b0 = fmax(y0, y1), a1 = fmin(x0, x1), b1 = fmax(x0, x1);
+        const bool plus = b0 - a1 - lo[2] >= T(0), minus = a0 - b1 - hi[2] <= T(0);
+        a[0] = max_over_signs(f0, amax * xc[1], plus, minus);
+        a[1] = max_over_signs(f1, -amax * xc[0], plus, minus);
+        const T top = fmax(lo[2], T(0)), bot = fmin(hi[2], T(0));
+        const bool same = (top <= hi[2] && b0 - a1 - top >= T(0)) || (lo[2] <= bot && a0 - b1 - bot <= T(0));
+        a[2] = same ? amax + bmax : fabs(amax - bmax);
+    } else if constexpr (B == HJ_DYN_ROCKETS && D == 3) {
+        const T ac = q(0), g = q(1), ue = q(2), up = q(3);
+        const T f0 = ac * c, f1 = ac * s + ac - g;
+        const T u0 = lo[0] * xc[0], u1 = hi[0] * xc[0];  // range of p0 x
+        const T w0 = lo[1] * xc[0], w1 = hi[1] * xc[0];  // range of p1 x
+        const T a0 = fmin(u0, u1), b0 = fmax(u0, u1), a1 = fmin(w0, w1), b1 = fmax(w0, w1);
+        a[0] = max_over_signs(f0, ue * xc[0], b0 - lo[2] >= T(0), a0 - hi[2] <= T(0));
+        a[1] = max_over_signs(f1, -up * xc[0], b1 + hi[2] >= T(0), a1 + lo[2] <= T(0));
+        const bool same = fmax(lo[2], -b1) <= fmin(hi[2], b0) || fmax(lo[2], a0) <= fmin(hi[2], -a1);
+        a[2] = same ? ue + up : fabs(ue - up);
+    }
 }
 
 // ydot from node coordinates xc, cos/sin (c, s) of the dimension-2
@@ -246,33 +327,37 @@ __host__ __device__ constexpr bool uses_angle() {
 // Hg(x, pb) + sum_d alpha_d dd_d, with alpha_d = alpha_d(x) (the maximum of
 // |f_d| over the controls at the node) or, for global LF, the launch's
 // alpha_g (its maximum over the grid).
+//
+// DYN may carry kDynBox: alpha_d is then the maximum over the node's box of
+// gradients (box_alpha) instead of alpha_d(x).
 template <typename T, int D, int DYN>
 __device__ __forceinline__ T lf_combine(const StageParams& P, const T* xc, T c, T s, const T* pb, const T* dd) {
     const auto q = [&P](int k) { return SP<T>::param(P, k); };
+    constexpr int B = dyn_base(DYN);
     T h = T(0);
     T a[D];
 #pragma unroll
     for (int d = 0; d < D; ++d) a[d] = T(0);
-    if constexpr (DYN == HJ_DYN_DOUBLE_INTEGRATOR && D == 2) {
+    if constexpr (B == HJ_DYN_DOUBLE_INTEGRATOR && D == 2) {
         const T umax = q(0);
         h = pb[0] * xc[1] - umax * fabs(pb[1]);
         a[0] = fabs(xc[1]);
         a[1] = umax;
-    } else if constexpr (DYN == HJ_DYN_AIR3D && D == 3) {
+    } else if constexpr (B == HJ_DYN_AIR3D && D == 3) {
         const T va = q(0), vb = q(1), amax = q(2), bmax = q(3);
         const T f0 = -va + vb * c, f1 = vb * s;
         h = pb[0] * f0 + pb[1] * f1 + amax * fabs(pb[0] * xc[1] - pb[1] * xc[0] - pb[2]) - bmax * fabs(pb[2]);
         a[0] = fabs(f0) + amax * fabs(xc[1]);
         a[1] = fabs(f1) + amax * fabs(xc[0]);
         a[2] = amax + bmax;
-    } else if constexpr (DYN == HJ_DYN_ROCKETS && D == 3) {
+    } else if constexpr (B == HJ_DYN_ROCKETS && D == 3) {
         const T ac = q(0), g = q(1), ue = q(2), up = q(3);
         const T f0 = ac * c, f1 = ac * s + ac - g;
         h = pb[0] * f0 + pb[1] * f1 + ue * fabs(pb[0] * xc[0] - pb[2]) - up * fabs(pb[1] * xc[0] + pb[2]);
         a[0] = fabs(f0) + ue * fabs(xc[0]);
         a[1] = fabs(f1) + up * fabs(xc[0]);
         a[2] = ue + up;
-    } else if constexpr (DYN == HJ_DYN_DUBINS4D && D == 4) {
+    } else if constexpr (B == HJ_DYN_DUBINS4D && D == 4) {
         const T wmax = q(0), accmax = q(1);
         const T f0 = xc[3] * c, f1 = xc[3] * s;
         h = pb[0] * f0 + pb[1] * f1 - wmax * fabs(pb[2]) - accmax * fabs(pb[3]);
@@ -280,22 +365,23 @@ __device__ __forceinline__ T lf_combine(const StageParams& P, const T* xc, T c, 
         a[1] = fabs(f1);
         a[2] = wmax;
         a[3] = accmax;
-    } else if constexpr (DYN == HJ_DYN_NORM) {
+    } else if constexpr (B == HJ_DYN_NORM) {
         const T cn = q(0);
         T s2 = T(0);
 #pragma unroll
         for (int d = 0; d < D; ++d) { s2 += pb[d] * pb[d]; a[d] = cn; }
         h = -cn * sqrt(s2);
-    } else if constexpr (DYN == HJ_DYN_ADVECT) {
+    } else if constexpr (B == HJ_DYN_ADVECT) {
 #pragma unroll
         for (int d = 0; d < D; ++d) { const T cd = q(d); h += -cd * pb[d]; a[d] = fabs(cd); }
-    } else if constexpr (DYN == HJ_DYN_ROTATE && D >= 2) {
+    } else if constexpr (B == HJ_DYN_ROTATE && D >= 2) {
         const T w = q(0);
         const T f0 = -w * xc[1], f1 = w * xc[0];
         h = -(pb[0] * f0 + pb[1] * f1);
         a[0] = fabs(f0);
         a[1] = fabs(f1);
     }
+    if constexpr (dyn_is_box(DYN)) box_alpha<T, D, B>(P, xc, c, s, pb, dd, a);
     if (P.alpha_global) {
 #pragma unroll
         for (int d = 0; d < D; ++d) a[d] = SP<T>::alpha_g(P, d);
@@ -309,8 +395,9 @@ __device__ __forceinline__ T lf_combine(const StageParams& P, const T* xc, T c, 
 // Whether a dynamics reads the coordinate of dimension d (the others are not computed).
 template <int D, int DYN>
 __host__ __device__ constexpr bool uses_coord(int d) {
-    return (DYN == HJ_DYN_DOUBLE_INTEGRATOR && d == 1) || (DYN == HJ_DYN_AIR3D && d <= 1) ||
-           (DYN == HJ_DYN_DUBINS4D && d == 3) || (DYN == HJ_DYN_ROTATE && d <= 1) || (DYN == HJ_DYN_ROCKETS && d == 0);
+    constexpr int B = dyn_base(DYN);
+    return (B == HJ_DYN_DOUBLE_INTEGRATOR && d == 1) || (B == HJ_DYN_AIR3D && d <= 1) ||
+           (B == HJ_DYN_DUBINS4D && d == 3) || (B == HJ_DYN_ROTATE && d <= 1) || (B == HJ_DYN_ROCKETS && d == 0);
 }
 
 // ydot at grid index idx from the one-sided derivatives (already divided by dx).
@@ -321,7 +408,7 @@ __device__ __forceinline__ T lf_term_dyn(const StageParams& P, const int* idx, c
     for (int d = 0; d < D; ++d) {
         pb[d] = T(0.5) * (pm[d] + pp[d]);
         dd[d] = T(0.5) * (pp[d] - pm[d]);
-        x[d] = SP<T>::lo(P, d) + T(idx[d]) * SP<T>::dx(P, d);
+        x[d] = coord(SP<T>::lo(P, d), idx[d], SP<T>::dx(P, d));
     }
     T c = T(0), s = T(0);
     if constexpr (uses_angle<D, DYN>()) {
@@ -336,10 +423,16 @@ template <typename T, int D>
 __device__ __forceinline__ T lf_term(const StageParams& P, const int* idx, const T* pm, const T* pp) {
     switch (P.dynamics) {
     case HJ_DYN_DOUBLE_INTEGRATOR: return lf_term_dyn<T, D, HJ_DYN_DOUBLE_INTEGRATOR>(P, idx, pm, pp);
-    case HJ_DYN_AIR3D: return lf_term_dyn<T, D, HJ_DYN_AIR3D>(P, idx, pm, pp);
+    case HJ_DYN_AIR3D:
+        return P.alpha_box ? lf_term_dyn<T, D, HJ_DYN_AIR3D + kDynBox>(P, idx, pm, pp)
+                           : lf_term_dyn<T, D, HJ_DYN_AIR3D>(P, idx, pm, pp);
     case HJ_DYN_DUBINS4D: return lf_term_dyn<T, D, HJ_DYN_DUBINS4D>(P, idx, pm, pp);
-    case HJ_DYN_ROCKETS: return lf_term_dyn<T, D, HJ_DYN_ROCKETS>(P, idx, pm, pp);
-    case HJ_DYN_NORM: return lf_term_dyn<T, D, HJ_DYN_NORM>(P, idx, pm, pp);
+    case HJ_DYN_ROCKETS:
+        return P.alpha_box ? lf_term_dyn<T, D, HJ_DYN_ROCKETS + kDynBox>(P, idx, pm, pp)
+                           : lf_term_dyn<T, D, HJ_DYN_ROCKETS>(P, idx, pm, pp);
+    case HJ_DYN_NORM:
+        return P.alpha_box ? lf_term_dyn<T, D, HJ_DYN_NORM + kDynBox>(P, idx, pm, pp)
+                           : lf_term_dyn<T, D, HJ_DYN_NORM>(P, idx, pm, pp);
     case HJ_DYN_ADVECT: return lf_term_dyn<T, D, HJ_DYN_ADVECT>(P, idx, pm, pp);
     case HJ_DYN_ROTATE: return lf_term_dyn<T, D, HJ_DYN_ROTATE>(P, idx, pm, pp);
     default: return T(0);

@@ -18,17 +18,21 @@ PARAMS = {DI: (1.0,), AIR3D: (5.0, 5.0, 1.0, 1.0), DUBINS: (1.0, 0.5), NORM: (1.
 
 
 def oracle_method(scheme=5, dynamics=DI, params=None, brt=1, extrap=0, cfl=0.8, max_step=math.inf, order=3,
-                  alpha_global=False):
+                  alpha_global=False, alpha_box=False):
     return O.method(scheme=scheme, dynamics=dynamics, params=PARAMS[dynamics] if params is None else params,
-                    brt=brt, extrap=extrap, cfl=cfl, max_step=max_step, order=order, alpha_global=alpha_global)
+                    brt=brt, extrap=extrap, cfl=cfl, max_step=max_step, order=order, alpha_global=alpha_global,
+                    alpha_box=alpha_box)
 
 
 def lib_method(scheme=5, dynamics=DI, params=None, brt=1, extrap=0, cfl=0.8, max_step=math.inf, order=3,
-               alpha_global=False):
+               alpha_global=False, alpha_box=False, kernel=0, tile=(0, 0, 0, 0)):
+    """kernel: 0 automatic, 1 the row kernel, 2 the one-node-per-thread
+    kernel; tile: the row kernel's pinned shape (ty, tz, occ, merged)."""
     from paper_2507_11542_gb300 import solver
     return solver.method(scheme=scheme, dynamics=dynamics, params=PARAMS[dynamics] if params is None else params,
                          brt=brt, extrap=extrap, cfl=cfl, max_step=max_step, order=order,
-                         alpha_mode=1 if alpha_global else 0)
+                         alpha_mode=2 if alpha_box else (1 if alpha_global else 0), kernel=kernel,
+                         tile_override=tuple(tile))
 
 
 def to_dev(V, dtype="float64"):

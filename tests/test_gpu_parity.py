@@ -145,6 +145,20 @@ def test_solve_air3d_full_horizon_fp64(ctx):
         assert rel_err(got[k], ref[k]) <= TOL64, k
 
 
+def test_solve_air3d_full_size_first_slice_fp64(ctx):
+    # the air3D configuration at its full size, 101^3, through its first slice
+    # (tau = 0.28, 78 RK3 steps; the oracle takes about 40 s): every node
+    spec, V0 = W.air3d(101)
+    ts = list(W.slice_times(2.8)[:2])
+    got, ref, stats, steps_o, times, times_o = _solve_both(ctx, spec, V0, AIR3D, ts)
+    assert stats["steps"] == steps_o == 78
+    np.testing.assert_array_equal(times, times_o)
+    for k in range(len(ts)):
+        err = rel_err(got[k], ref[k])
+        print("air3D 101^3 slice %d (tau = %.2f): max|GPU - oracle| / max|oracle| = %.3g" % (k, ts[k], err))
+        assert err <= TOL64, (k, err)
+
+
 def test_solve_dubins_full_horizon_fp64_host_io(ctx):
     spec, V0 = W.dubins4d(15)
     ts = W.slice_times(2.0, 3)
@@ -154,25 +168,35 @@ def test_solve_dubins_full_horizon_fp64_host_io(ctx):
         assert rel_err(got[k], ref[k]) <= TOL64, k
 
 
-def test_solve_dubins_31_full_horizon_within_its_conditioning(ctx, monkeypatch):
-    # The reduced 4-D configuration, 31^4 over the whole horizon (54 steps; the
-    # oracle takes about half a minute). Its extrapolated speed edges are
-    # ill-conditioned inside the target (V nearly constant in v, so the ghost
-    # slope is rounding noise): two FP64 evaluations of this library that
-    # differ only in rounding order (the row kernel and the one-node-per-thread
-    # kernel) already differ by 9e-13 at t = 1 and 9e-11 at t = 2. So the
-    # distance to the oracle is bounded by that spread, and must meet the
-    # 1e-12 bar away from the speed edges at t = 1.
-    from paper_2507_11542_gb300 import solver
+def test_solve_dubins_31_full_horizon_within_the_oracles_own_sensitivity(ctx):
+    # The reduced 4-D configuration, 31^4 over the whole horizon (54 steps; an
+    # oracle run takes about half a minute). Its extrapolated speed edges are
+    # ill-conditioned inside the target: V is nearly constant in v there, so
+    # the ghost slope is rounding noise and its sign picks the direction of
+    # the extrapolation (R3). The yardstick comes from the oracle alone: the
+    # same oracle source compiled with contraction (a*b + c rounded once where
+    # the compiler fuses it) lands `spread` away from the strict build. The GPU
+    # must stay within 1e-12 + K * spread of the strict oracle, K = 4 (its
+    # rounding order differs from the strict build's at more operations than
+    # contraction changes: the interface form of WENO5, the shared reciprocal),
+    # and within 1e-12 away from the speed edges at t = 1.
     spec, V0 = W.dubins4d(31)
     ts = W.slice_times(2.0, 3)
     got, ref, stats, steps_o, _, _ = _solve_both(ctx, spec, V0, DUBINS, ts)
-    monkeypatch.setenv("HJ_ROWS", "0")
-    alt, _, _ = solver.solve(ctx, spec, lib_method(dynamics=DUBINS, brt=1), to_dev(V0), ts)
-    monkeypatch.delenv("HJ_ROWS")
+    mo = oracle_method(dynamics=DUBINS, brt=1)
+    # other correct evaluations: the contracted build, and both builds on V0
+    # moved by one unit in the last place at every node (seeded signs), the
+    # rounding V0 itself carries
+    rng = np.random.default_rng(3)
+    V0u = np.asfortranarray(V0 + rng.choice([-1.0, 1.0], size=V0.shape) * np.spacing(V0))
+    others = [O.solve(spec, mo, V0, ts, fma=True), O.solve(spec, mo, V0u, ts), O.solve(spec, mo, V0u, ts, fma=True)]
+    assert all(o[1] == steps_o for o in others) and stats["steps"] == steps_o
     for k in range(1, len(ts)):
-        cond = rel_err(to_host(alt[k], spec.n), got[k])
-        assert rel_err(got[k], ref[k]) <= TOL64 + 4 * cond, (k, cond)
+        spread = max(rel_err(o[0][k], ref[k]) for o in others)
+        err = rel_err(got[k], ref[k])
+        print("slice %d: GPU - oracle %.3g; other oracle evaluations - oracle, largest %.3g (relative to max|V|)"
+              % (k, err, spread))
+        assert err <= TOL64 + 4 * spread, (k, err, spread)
     inner = (slice(None),) * 3 + (slice(3, -3),)
     assert np.max(np.abs(got[1][inner] - ref[1][inner])) <= TOL64 * np.max(np.abs(ref[1]))
 
@@ -326,9 +350,20 @@ def test_errors_are_reported_not_raised_on_device(ctx):
             solver.solve(ctx, spec, bad_method, to_dev(V0), [0.1])
         assert e.value.status == L.HJ_EINVAL
     m_bad = lib_method(dynamics=DI)
-    m_bad.alpha_mode = 2
+    m_bad.alpha_mode = 3
     with pytest.raises(L.HJError) as e:
         solver.term(ctx, spec, m_bad, to_dev(V0))
+    assert e.value.status == L.HJ_EINVAL
+    # launch choices: an unknown kernel, a malformed or unfitting tile override,
+    # the row kernel asked for where it cannot run
+    for kernel, tile in ((3, (0, 0, 0, 0)), (0, (0, 4, 0, 0)), (0, (2, 1, 3, 0)), (2, (2, 1, 1, 0)),
+                         (0, (40, 1, 1, 0))):
+        with pytest.raises(L.HJError) as e:
+            solver.term(ctx, spec, lib_method(dynamics=DI, kernel=kernel, tile=tile), to_dev(V0))
+        assert e.value.status == L.HJ_EINVAL, (kernel, tile)
+    thin = W.GridSpec((21, 3), (-1.0, -1.0), (1.0, 1.0))   # 3 nodes along a dimension: no row kernel
+    with pytest.raises(L.HJError) as e:
+        solver.term(ctx, thin, lib_method(dynamics=DI, kernel=1), to_dev(np.zeros((21, 3))))
     assert e.value.status == L.HJ_EINVAL
     # empty and malformed grids are rejected before any work
     m = lib_method(dynamics=NORM, brt=0)
@@ -371,7 +406,8 @@ def test_errors_are_reported_not_raised_on_device(ctx):
 ])
 @pytest.mark.parametrize("dtype", ["float64", "float32"])
 @pytest.mark.parametrize("scheme", [5, 3, 2, 1])
-def test_row_kernel_is_independent_of_tiling(ctx, monkeypatch, dyn, shape, cfgs, dtype, scheme):
+def test_row_kernel_is_independent_of_tiling(ctx, dyn, shape, cfgs, dtype, scheme):
+    # launch shapes pinned through hj_method.tile_override (ty, tz, occ, merged)
     from paper_2507_11542_gb300 import solver
     base = SPECS[dyn]
     spec = W.GridSpec(shape, base.lo, base.hi, base.periodic)
@@ -381,20 +417,21 @@ def test_row_kernel_is_independent_of_tiling(ctx, monkeypatch, dyn, shape, cfgs,
     outs = []
     max_threads = 512 if dtype == "float64" else 1024
     for cfg in cfgs:
-        if (shape[0] + 1) * int(cfg.split(",")[0]) > max_threads:
+        tile = [int(c) for c in cfg.split(",")] + [0] * (4 - len(cfg.split(",")))
+        if (shape[0] + 1) * tile[0] > max_threads:
             continue
-        monkeypatch.setenv("HJ_ROWS_CFG", cfg)
         Vd = to_dev(V, dtype)
-        solver.rk3_step(ctx, spec, m, Vd, dt)
+        solver.rk3_step(ctx, spec, lib_method(scheme=scheme, dynamics=dyn, brt=1, kernel=1, tile=tile), Vd, dt)
         outs.append(to_host(Vd, spec.n))
-    monkeypatch.delenv("HJ_ROWS_CFG")
     for o in outs[1:]:
         np.testing.assert_array_equal(o, outs[0])
-    # the one-node-per-thread kernel (two-sided WENO5 everywhere) agrees to rounding
-    monkeypatch.setenv("HJ_ROWS", "0")
+    # the tuned shape gives the same bits
     Vd = to_dev(V, dtype)
     solver.rk3_step(ctx, spec, m, Vd, dt)
-    monkeypatch.delenv("HJ_ROWS")
+    np.testing.assert_array_equal(to_host(Vd, spec.n), outs[0])
+    # the one-node-per-thread kernel (two-sided WENO5 everywhere) agrees to rounding
+    Vd = to_dev(V, dtype)
+    solver.rk3_step(ctx, spec, lib_method(scheme=scheme, dynamics=dyn, brt=1, kernel=2), Vd, dt)
     assert rel_err(to_host(Vd, spec.n), outs[0]) <= (1e-13 if dtype == "float64" else 1e-5)
     if dtype == "float64":
         ref = O.rk3_step(spec, oracle_method(scheme=scheme, dynamics=dyn, brt=1), V, dt)
@@ -465,7 +502,7 @@ def test_solve_orders_and_global_alpha_fp64(ctx, order, alpha_global, dyn, schem
 
 
 @pytest.mark.parametrize("dtype,n0", [("float64", 511), ("float32", 1023)])
-def test_row_kernel_widest_rows(ctx, monkeypatch, dtype, n0):
+def test_row_kernel_widest_rows(ctx, dtype, n0):
     # the widest rows a row-kernel block holds (one node row of n0 nodes plus
     # its row-end thread fill a 512- or 1024-thread block, no gap threads)
     from paper_2507_11542_gb300 import solver
@@ -476,10 +513,8 @@ def test_row_kernel_widest_rows(ctx, monkeypatch, dtype, n0):
     Vd = to_dev(V, dtype)
     solver.rk3_step(ctx, spec, m, Vd, dt)
     got = to_host(Vd, spec.n)
-    monkeypatch.setenv("HJ_ROWS", "0")
     Vo = to_dev(V, dtype)
-    solver.rk3_step(ctx, spec, m, Vo, dt)
-    monkeypatch.delenv("HJ_ROWS")
+    solver.rk3_step(ctx, spec, lib_method(dynamics=DI, brt=1, kernel=2), Vo, dt)
     assert rel_err(got, to_host(Vo, spec.n)) <= (1e-13 if dtype == "float64" else 1e-5)
     if dtype == "float64":
         assert rel_err(got, O.rk3_step(spec, oracle_method(dynamics=DI), V, dt)) <= TOL64
@@ -521,3 +556,101 @@ def test_resume_from_a_slice_equals_the_uninterrupted_solve(ctx, dtype):
     with pytest.raises(L.HJError) as e:  # a slice before t0
         solver.solve(ctx, spec, m, part[0].clone(), [0.2], t0=0.25)
     assert e.value.status == L.HJ_EINVAL
+
+
+# ---------------------------------------------------------------------------
+# Lax-Friedrichs dissipation local in p (HJ_ALPHA_BOX): alpha_d = max of
+# |dHg/dp_d| over each node's box of one-sided gradients
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dyn", [NORM, AIR3D, ROCKETS, DI, DUBINS])
+@pytest.mark.parametrize("scheme", [2, 5])
+@pytest.mark.parametrize("kernel", [0, 2])
+def test_box_alpha_term_parity_fp64(ctx, dyn, scheme, kernel):
+    from paper_2507_11542_gb300 import solver
+    spec = SPECS[dyn]
+    V = _field(spec, 50 + dyn)
+    y_o = O.term(spec, oracle_method(scheme=scheme, dynamics=dyn, brt=0, alpha_box=True), V)
+    y = solver.term(ctx, spec, lib_method(scheme=scheme, dynamics=dyn, brt=0, alpha_box=True, kernel=kernel),
+                    to_dev(V))
+    assert rel_err(to_host(y, spec.n), y_o) <= TOL64
+    if dyn in (NORM, AIR3D, ROCKETS):   # slopes that depend on p: a different term from the node scheme
+        y_n = O.term(spec, oracle_method(scheme=scheme, dynamics=dyn, brt=0), V)
+        assert rel_err(y_o, y_n) > 1e-6
+    # the CFL bound keeps the maximum over every p
+    assert solver.step_bound(ctx, spec, lib_method(dynamics=dyn, alpha_box=True)) == \
+        O.step_bound_inv(spec, oracle_method(dynamics=dyn))
+
+
+@pytest.mark.parametrize("dyn", [NORM, AIR3D, ROCKETS])
+@pytest.mark.parametrize("brt", [0, 1, 2])
+def test_box_alpha_rk3_step_parity_fp64(ctx, dyn, brt):
+    from paper_2507_11542_gb300 import solver
+    spec = SPECS[dyn]
+    V = _field(spec, 60 + dyn)
+    dt = 0.8 / O.step_bound_inv(spec, oracle_method(dynamics=dyn))
+    ref = O.rk3_step(spec, oracle_method(dynamics=dyn, brt=brt, alpha_box=True), V, dt)
+    for kernel in (0, 2):
+        Vd = to_dev(V)
+        solver.rk3_step(ctx, spec, lib_method(dynamics=dyn, brt=brt, alpha_box=True, kernel=kernel), Vd, dt)
+        assert rel_err(to_host(Vd, spec.n), ref) <= TOL64, kernel
+
+
+def test_box_alpha_row_kernel_is_independent_of_tiling(ctx):
+    from paper_2507_11542_gb300 import solver
+    spec = W.GridSpec((37, 29, 23), SPECS[AIR3D].lo, SPECS[AIR3D].hi, SPECS[AIR3D].periodic)
+    V = _field(spec, 61)
+    dt = 0.8 / O.step_bound_inv(spec, oracle_method(dynamics=AIR3D))
+    outs = []
+    for tile in [(1, 1, 1, 0), (4, 23, 1, 0), (7, 3, 1, 1)]:
+        for dtype in ("float64", "float32"):
+            Vd = to_dev(V, dtype)
+            solver.rk3_step(ctx, spec, lib_method(dynamics=AIR3D, alpha_box=True, kernel=1, tile=tile), Vd, dt)
+            outs.append((dtype, to_host(Vd, spec.n)))
+    for dtype in ("float64", "float32"):
+        same = [o for d, o in outs if d == dtype]
+        for o in same[1:]:
+            np.testing.assert_array_equal(o, same[0])
+
+
+@pytest.mark.parametrize("dyn,make,ts", [
+    (NORM, lambda: (W.GridSpec((41, 37, 33), (-1.0,) * 3, (1.0,) * 3),), [0.0, 0.2, 0.4]),
+    (AIR3D, lambda: W.air3d(31), list(W.slice_times(2.8, 3))),
+    (ROCKETS, lambda: W.rockets(25), list(W.slice_times(2.5, 3))),
+])
+def test_box_alpha_solve_parity_fp64(ctx, dyn, make, ts):
+    from paper_2507_11542_gb300 import solver
+    made = make()
+    if dyn == NORM:
+        spec = made[0]
+        V0 = W.sphere(spec, (0.05, -0.1, 0.02), 0.3)
+        brt, scheme = 0, 5
+    else:
+        spec, V0 = made
+        brt, scheme = 1, (2 if dyn == ROCKETS else 5)
+    # a seeded perturbation keeps the kinks' sign tests away from exact ties
+    V0 = np.asfortranarray(V0 + 1e-3 * W.random_field(spec, 70 + dyn))
+    mo = oracle_method(scheme=scheme, dynamics=dyn, brt=brt, alpha_box=True)
+    ref, steps_o, times_o = O.solve(spec, mo, V0, ts)
+    out, times, stats = solver.solve(ctx, spec, lib_method(scheme=scheme, dynamics=dyn, brt=brt, alpha_box=True),
+                                     to_dev(V0), ts)
+    assert stats["steps"] == steps_o
+    np.testing.assert_array_equal(times, times_o)
+    for k in range(len(ts)):
+        err = rel_err(to_host(out[k], spec.n), ref[k])
+        assert err <= TOL64, (k, err)
+
+
+def test_box_alpha_fp32_sphere_zero_set(ctx):
+    # FP32 with the box dissipation: the expanding sphere's zero set against
+    # the FP64 oracle (0.1 cell) and the Hopf-Lax solution
+    from paper_2507_11542_gb300 import solver
+    spec = W.GridSpec((65, 65, 65), (-1.0,) * 3, (1.0,) * 3)
+    V0 = W.sphere(spec, (0.0, 0.0, 0.0), 0.25)
+    ts = [0.0, 0.25, 0.5]
+    ref, _, _ = O.solve(spec, oracle_method(dynamics=NORM, brt=0, alpha_box=True), V0, ts)
+    out, _, _ = solver.solve(ctx, spec, lib_method(dynamics=NORM, brt=0, alpha_box=True), to_dev(V0, "float32"), ts)
+    for k in range(len(ts)):
+        got = to_host(out[k], spec.n)
+        assert zero_set_displacement(got, ref[k], spec) < 0.1
+        assert crossing_displacement(got, ref[k], spec) < 0.1
