@@ -19,12 +19,14 @@ cudaError_t launch_batch_stage_f32(const BatchTile* tiles, int ntiles, const Bat
 // After stage 3 of a step: count the step, and set up the next one. Every
 // step uses dt_full except the one that completes a slice, which is clipped
 // to land on the slice time (Listing 6) and also writes the slice output.
-// Only instances of lane min_lane and above took this step.
-__global__ void batch_advance_kernel(BatchInst* insts, int n, int min_lane) {
+// Only instances of lanes lane_lo .. lane_hi took this step (the lane is
+// tested first: other lanes' descriptors may be advancing concurrently).
+__global__ void batch_advance_kernel(BatchInst* insts, int n, int lane_lo, int lane_hi) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     BatchInst& I = insts[i];
-    if (I.k >= I.steps_total || I.lane < min_lane) return;
+    if (I.lane < lane_lo || I.lane > lane_hi) return;
+    if (I.k >= I.steps_total) return;
     const int k = ++I.k;
     I.slice_out = nullptr;
     if (k < I.steps_total) {
@@ -39,8 +41,8 @@ __global__ void batch_advance_kernel(BatchInst* insts, int n, int min_lane) {
     }
 }
 
-cudaError_t launch_batch_advance(BatchInst* insts, int n, int min_lane, cudaStream_t s) {
-    batch_advance_kernel<<<(n + 127) / 128, 128, 0, s>>>(insts, n, min_lane);
+cudaError_t launch_batch_advance(BatchInst* insts, int n, int lane_lo, int lane_hi, cudaStream_t s) {
+    batch_advance_kernel<<<(n + 127) / 128, 128, 0, s>>>(insts, n, lane_lo, lane_hi);
     return cudaGetLastError();
 }
 

@@ -78,6 +78,14 @@ void Engine::drop_graphs() {
 
 void Engine::shutdown() {
     drop_graphs();
+    for (int l = 0; l < kLanes; ++l) {
+        if (lane_stream_[l]) cudaStreamDestroy(lane_stream_[l]);
+        if (lane_ev_[l]) cudaEventDestroy(lane_ev_[l]);
+        lane_stream_[l] = nullptr;
+        lane_ev_[l] = nullptr;
+    }
+    if (fork_ev_) cudaEventDestroy(fork_ev_);
+    fork_ev_ = nullptr;
     for (Group& g : groups_) cudaFree(g.d_tiles);
     groups_.clear();
     if (cap_stream_) cudaStreamDestroy(cap_stream_);
@@ -102,6 +110,13 @@ hj_status Engine::init(hj_ctx* ctx, cudaStream_t stream, int max_slots, size_t a
     HJ_CUDA(ctx, cudaMemsetAsync(d_insts_, 0, sizeof(BatchInst) * max_slots_, stream_));
     HJ_CUDA(ctx, cudaMalloc(&d_words_, 16 * (size_t)max_slots_));
     HJ_CUDA(ctx, cudaStreamCreateWithFlags(&cap_stream_, cudaStreamNonBlocking));
+    if (multirate_) {
+        HJ_CUDA(ctx, cudaEventCreateWithFlags(&fork_ev_, cudaEventDisableTiming));
+        for (int l = 0; l < kLanes; ++l) {
+            HJ_CUDA(ctx, cudaStreamCreateWithFlags(&lane_stream_[l], cudaStreamNonBlocking));
+            HJ_CUDA(ctx, cudaEventCreateWithFlags(&lane_ev_[l], cudaEventDisableTiming));
+        }
+    }
     h_insts_.assign(max_slots_, BatchInst());
     std::memset(h_insts_.data(), 0, sizeof(BatchInst) * h_insts_.size());
     slots.assign(max_slots_, Slot());
@@ -523,12 +538,13 @@ hj_status Engine::rebuild_tiles() {
 }
 
 // One RK3 step of the instances of lane `lane` and above.
-cudaError_t Engine::enqueue_step(cudaStream_t s, bool count, int lane) {
+cudaError_t Engine::enqueue_step(cudaStream_t s, bool count, int lane, bool exact) {
     for (int stage = 1; stage <= 3; ++stage)
         for (const Group& g : groups_) {
             const size_t off = g.lane_off[lane];
-            if (g.tiles.size() <= off) continue;
-            const int nt = (int)(g.tiles.size() - off);
+            const size_t end = exact ? lane_end(g, lane) : g.tiles.size();
+            if (end <= off) continue;
+            const int nt = (int)(end - off);
             cudaError_t e = g.dtype == HJ_F64 ? launch_batch_stage_f64(g.d_tiles + off, nt, d_insts_, stage, g.ndim,
                                                                        g.dyn, g.scheme, g.threads, g.smem, s)
                                               : launch_batch_stage_f32(g.d_tiles + off, nt, d_insts_, stage, g.ndim,
@@ -543,7 +559,7 @@ cudaError_t Engine::enqueue_step(cudaStream_t s, bool count, int lane) {
         launches += 1;
         ctx_->launches += 1;
     }
-    return launch_batch_advance(d_insts_, max_slots_, lane, s);
+    return launch_batch_advance(d_insts_, max_slots_, lane, exact ? lane : kLanes - 1, s);
 }
 
 long long Engine::dead_tiles() const {
@@ -577,18 +593,23 @@ hj_status Engine::run(int K) {
         if (st) return st;
     }
     cudaError_t e = cudaSuccess;
-    // lane l takes (kLaneMult[l] - kLaneMult[l-1]) * K steps after the K steps of every lane
+    // Without lanes: K steps of every instance on stream_. With lanes: lane l
+    // takes kLaneMult[l] * K steps of its own instances on its own stream,
+    // all lanes forked from stream_ and joined back into it.
+    if (multirate_) e = cudaEventRecord(fork_ev_, stream_);
     for (int l = 0; l < (multirate_ ? kLanes : 1) && e == cudaSuccess; ++l) {
         bool any = false;
         long long per_step = 1;
         for (const Group& g : groups_)
-            if (g.tiles.size() > g.lane_off[l]) {
+            if ((multirate_ ? lane_end(g, l) : g.tiles.size()) > g.lane_off[l]) {
                 any = true;
                 per_step += 3;
             }
         if (!any) continue;
-        const int Kl = l == 0 ? K : (kLaneMult[l] - kLaneMult[l - 1]) * K;
-        if (Kl >= 2) {
+        const int Kl = multirate_ ? kLaneMult[l] * K : K;
+        cudaStream_t s = multirate_ ? lane_stream_[l] : stream_;
+        if (multirate_) e = cudaStreamWaitEvent(s, fork_ev_, 0);
+        if (e == cudaSuccess && Kl >= 2) {
             if (!exec_[l] || exec_K_[l] != Kl) {
                 if (exec_[l]) {
                     cudaStreamSynchronize(stream_);
@@ -597,21 +618,23 @@ hj_status Engine::run(int K) {
                 }
                 cudaGraph_t graph = nullptr;
                 e = cudaStreamBeginCapture(cap_stream_, cudaStreamCaptureModeThreadLocal);
-                for (int k = 0; k < Kl && e == cudaSuccess; ++k) e = enqueue_step(cap_stream_, false, l);
+                for (int k = 0; k < Kl && e == cudaSuccess; ++k) e = enqueue_step(cap_stream_, false, l, multirate_);
                 cudaError_t e2 = cudaStreamEndCapture(cap_stream_, &graph);
                 if (e == cudaSuccess) e = e2;
                 if (e == cudaSuccess) e = cudaGraphInstantiate(&exec_[l], graph, 0);
                 if (graph) cudaGraphDestroy(graph);
                 exec_K_[l] = Kl;
             }
-            if (e == cudaSuccess) e = cudaGraphLaunch(exec_[l], stream_);
+            if (e == cudaSuccess) e = cudaGraphLaunch(exec_[l], s);
             if (e == cudaSuccess) {
                 launches += per_step * Kl;
                 ctx_->launches += per_step * Kl;
             }
         } else {
-            for (int k = 0; k < Kl && e == cudaSuccess; ++k) e = enqueue_step(stream_, true, l);
+            for (int k = 0; k < Kl && e == cudaSuccess; ++k) e = enqueue_step(s, true, l, multirate_);
         }
+        if (multirate_ && e == cudaSuccess) e = cudaEventRecord(lane_ev_[l], s);
+        if (multirate_ && e == cudaSuccess) e = cudaStreamWaitEvent(stream_, lane_ev_[l], 0);
     }
     if (e != cudaSuccess) return cuda_fail(ctx_, e, "batched step launch");
     for (int i = 0; i < max_slots_; ++i) {

@@ -66,7 +66,8 @@ class Engine {
     // Allocates the arena (arena_bytes), descriptor table and reduction words.
     // With multirate, instances are sorted by size into rate lanes: per K
     // steps of the largest, smaller ones take kLaneMult[lane] * K (a server's
-    // small requests do not wait for the pace of its largest ones).
+    // small requests do not wait for the pace of its largest ones). The lanes'
+    // step blocks run concurrently, each on its own stream.
     hj_status init(hj_ctx* ctx, cudaStream_t stream, int max_slots, size_t arena_bytes, bool multirate = false);
     void shutdown();
 
@@ -115,7 +116,9 @@ class Engine {
     };
     hj_status shape_group(Group& g, const std::vector<int>& members, const std::vector<int>& fresh);
     hj_status rebuild_tiles();
-    cudaError_t enqueue_step(cudaStream_t s, bool count, int lane);
+    // One RK3 step of the instances of lane `lane` (exact) or of lanes >= lane.
+    cudaError_t enqueue_step(cudaStream_t s, bool count, int lane, bool exact);
+    size_t lane_end(const Group& g, int lane) const { return lane + 1 < kLanes ? g.lane_off[lane + 1] : g.tiles.size(); }
     long long dead_tiles() const;
 
     hj_ctx* ctx_ = nullptr;
@@ -133,6 +136,11 @@ class Engine {
     bool multirate_ = false;
     cudaGraphExec_t exec_[kLanes] = {nullptr, nullptr, nullptr};  // the step blocks of each lane
     int exec_K_[kLanes] = {0, 0, 0};
+    // multirate: each lane's step block runs on a stream of its own, forked
+    // from and joined back into stream_, so that the lanes overlap on the GPU
+    cudaStream_t lane_stream_[kLanes] = {nullptr, nullptr, nullptr};
+    cudaEvent_t fork_ev_ = nullptr;
+    cudaEvent_t lane_ev_[kLanes] = {nullptr, nullptr, nullptr};
     void drop_graphs();
     std::vector<int> pending_;
 };

@@ -217,8 +217,8 @@ cudaError_t launch_batch_stage_f32(const BatchTile* tiles, int ntiles, const Bat
                                    int dynamics, int scheme, int threads, size_t smem, cudaStream_t s);
 cudaError_t launch_batch_stage_f64(const BatchTile* tiles, int ntiles, const BatchInst* insts, int stage, int ndim,
                                    int dynamics, int scheme, int threads, size_t smem, cudaStream_t s);
-// Advances the instances of lane min_lane and above (BatchInst::lane).
-cudaError_t launch_batch_advance(BatchInst* insts, int n, int min_lane, cudaStream_t s);
+// Advances the instances of lanes lane_lo .. lane_hi (BatchInst::lane).
+cudaError_t launch_batch_advance(BatchInst* insts, int n, int lane_lo, int lane_hi, cudaStream_t s);
 
 // max over nodes of sum_d alpha_d(x)/dx_d, as the FP64 bit pattern, atomically
 // max-ed into *acc (which the caller zeroes first).

@@ -613,21 +613,22 @@ def test_box_alpha_row_kernel_is_independent_of_tiling(ctx):
             np.testing.assert_array_equal(o, same[0])
 
 
-@pytest.mark.parametrize("dyn,make,ts", [
-    (NORM, lambda: (W.GridSpec((41, 37, 33), (-1.0,) * 3, (1.0,) * 3),), [0.0, 0.2, 0.4]),
-    (AIR3D, lambda: W.air3d(31), list(W.slice_times(2.8, 3))),
-    (ROCKETS, lambda: W.rockets(25), list(W.slice_times(2.5, 3))),
+@pytest.mark.parametrize("dyn,scheme,make,ts", [
+    (NORM, 5, lambda: (W.GridSpec((41, 37, 33), (-1.0,) * 3, (1.0,) * 3),), [0.0, 0.2, 0.4]),
+    (AIR3D, 5, lambda: W.air3d(31), list(W.slice_times(2.8, 3))),
+    (ROCKETS, 5, lambda: W.rockets(25), list(W.slice_times(2.5, 3))),
+    (ROCKETS, 2, lambda: W.rockets(25), list(W.slice_times(2.5, 3))),
 ])
-def test_box_alpha_solve_parity_fp64(ctx, dyn, make, ts):
+def test_box_alpha_solve_parity_fp64(ctx, dyn, scheme, make, ts):
     from paper_2507_11542_gb300 import solver
     made = make()
     if dyn == NORM:
         spec = made[0]
         V0 = W.sphere(spec, (0.05, -0.1, 0.02), 0.3)
-        brt, scheme = 0, 5
+        brt = 0
     else:
         spec, V0 = made
-        brt, scheme = 1, (2 if dyn == ROCKETS else 5)
+        brt = 1
     # a seeded perturbation keeps the kinks' sign tests away from exact ties
     V0 = np.asfortranarray(V0 + 1e-3 * W.random_field(spec, 70 + dyn))
     mo = oracle_method(scheme=scheme, dynamics=dyn, brt=brt, alpha_box=True)
@@ -636,9 +637,25 @@ def test_box_alpha_solve_parity_fp64(ctx, dyn, make, ts):
                                      to_dev(V0), ts)
     assert stats["steps"] == steps_o
     np.testing.assert_array_equal(times, times_o)
+    bound = [TOL64] * len(ts)
+    if scheme == 2:
+        # ENO2 makes exact ties (a node's p- and p+ equal, zero one-sided
+        # derivatives at the extrapolated angle edges) on which the box's sign
+        # tests flip: the oracle itself moves by about 1e-5 when V0 moves by
+        # one ulp. The bound is 1e-12 + 4 x that spread, from the oracle alone
+        # (three seeded one-ulp moves of V0), as for the Dubins car.
+        rng = np.random.default_rng(5)
+        spread = np.zeros(len(ts))
+        for _ in range(3):
+            V0u = np.asfortranarray(V0 + rng.choice([-1.0, 1.0], size=V0.shape) * np.spacing(V0))
+            alt, _, _ = O.solve(spec, mo, V0u, ts)
+            spread = np.maximum(spread, [rel_err(alt[k], ref[k]) for k in range(len(ts))])
+        bound = [TOL64 + 4 * sp for sp in spread]
     for k in range(len(ts)):
         err = rel_err(to_host(out[k], spec.n), ref[k])
-        assert err <= TOL64, (k, err)
+        print("box alpha, dynamics %d, scheme %d, slice %d: GPU - oracle %.3g (bound %.3g)" % (dyn, scheme, k, err,
+                                                                                               bound[k]))
+        assert err <= bound[k], (k, err, bound[k])
 
 
 def test_box_alpha_fp32_sphere_zero_set(ctx):
