@@ -153,7 +153,7 @@ GridDev make_grid(const hj_grid* g, int extrap) {
 // 1e-99 on divided differences (Sec. 3.3, Jiang-Peng), so 1e-99 dx_d^2 on raw
 // ones; FP32 uses 1e-18 directly so that the squared sums stay normal numbers.
 double weno_floor(const GridDev& g, int dtype, int d) {
-    if (dtype == HJ_F32) return 1e-18;
+    if (dtype == HJ_F32) return (double)kWenoFloorF32;
     return 1e-99 * g.dx[d] * g.dx[d];
 }
 

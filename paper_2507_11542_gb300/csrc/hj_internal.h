@@ -10,6 +10,10 @@ namespace hj {
 
 constexpr int kMaxDim = 4;
 
+// WENO5 epsilon floor of FP32 kernels, in raw-difference units: 1e-99 (the
+// FP64 floor) underflows in FP32; with 1e-18 the squared sums stay normal.
+constexpr float kWenoFloorF32 = 1e-18f;
+
 // Row and batch kernels take the dynamics as a template parameter. For the
 // Hamiltonians whose |dHg/dp_d| depends on p (norm, air3D, rockets), the
 // variant with Lax-Friedrichs dissipation local in p (HJ_ALPHA_BOX) is the

@@ -104,6 +104,7 @@ template <> __device__ __forceinline__ void cp_async_elem<double>(double* dst, c
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+
 // One tile: rows y0 = row_tile*TY .. +TY-1 of the plane(s) at dimension-2 index
 // i2 (4-D) and the planes of chunk `chunk` along the streamed dimension
 // (planes chunk*tz .. +tz-1), computed by the NT threads of a 1-D block.
@@ -224,7 +225,10 @@ __device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T
 
     const T h0 = SP<T>::half_inv_dx(P, 0), h1 = SP<T>::half_inv_dx(P, 1), hS = SP<T>::half_inv_dx(P, SD);
     const T dt = R.dt, cv = R.cv, cu = R.cu;
-    const bool minv = R.minv, brt0 = R.brt0;
+    const bool minv = R.minv;
+    // BRT min(0, .) as a clamp (+inf: none), global dissipation as a flag, both read once
+    const T clamp = R.brt0 ? T(0) : T(INFINITY);
+    const bool alpha_global = P.alpha_global;
     T* __restrict__ also_out = R.also_out;
     // node coordinates that do not change along the streamed dimension
     T xc[D];
@@ -233,11 +237,12 @@ __device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T
     if constexpr (uses_coord<D, DYN>(0)) xc[0] = coord(SP<T>::lo(P, 0), x, SP<T>::dx(P, 0));
     if constexpr (uses_coord<D, DYN>(1)) xc[1] = coord(SP<T>::lo(P, 1), y, SP<T>::dx(P, 1));
     if constexpr (D == 4 && uses_coord<D, DYN>(2)) xc[2] = coord(SP<T>::lo(P, 2), i2, SP<T>::dx(P, 2));
-    const T* __restrict__ trig = Trig<T>::get(P);
+    const T* __restrict__ trig = Trig<T>::get(P);       // cos of the dimension-2 coordinate
+    const T* __restrict__ trig_s = uses_angle<D, DYN>() ? trig + g.n[2] : trig;  // sin
     T cos2 = T(0), sin2 = T(0);  // angle of dimension 2 (fixed for the block in 4-D)
     if constexpr (D == 4 && uses_angle<D, DYN>()) {
         cos2 = trig[i2];
-        sin2 = trig[g.n[2] + i2];
+        sin2 = trig_s[i2];
     }
 
     // Halo rows (three above, three below, and rows past the grid edge in a
@@ -309,6 +314,7 @@ __device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T
         }
     };
 
+
     // Streamed-dimension queue: q[k] = V at plane z-2+k (k = 0..5); carry = raw p- at z.
     // A warm-up step evaluates the interface below the first plane, so that
     // every interface goes through the same code and results do not depend
@@ -322,6 +328,16 @@ __device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T
         iface_at<SCHEME>(q[0], q[1], q[2], q[3], q[4], q[5], flS, unused, carry);
 #pragma unroll
         for (int k = 0; k < 5; ++k) q[k] = q[k + 1];
+    }
+
+    // V^n of the node's next plane is loaded one plane ahead of its use (2-D
+    // and 3-D grids), so that its global-memory latency is covered by a whole
+    // plane of work. Where out aliases V^n, the value read is this thread's own
+    // node, which it writes one plane later.
+    constexpr bool kVnAhead = KIND == kKindCombine && D <= 3;
+    T vn_next = T(0);
+    if constexpr (kVnAhead) {
+        if (node) vn_next = ld(vn + col + zbeg * sS);
     }
 
     // prologue: planes zbeg and zbeg+1 (ghost cells of zbeg+1 follow in phase A(zbeg))
@@ -346,10 +362,17 @@ __device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T
         T cosz = cos2, sinz = sin2;
         if constexpr (D == 3 && uses_angle<D, DYN>()) {
             cosz = trig[z];
-            sinz = trig[g.n[2] + z];
+            sinz = trig_s[z];
         }
         if (D >= 3 && node)
             q[5] = z_inside ? ld(ucol + fz + 3 * sS) : line_value(ucol, z + 3, ns, (long long)sS, perS, extrap);
+        T vv = T(0);
+        if constexpr (kVnAhead) {
+            if (node) {
+                vv = vn_next;
+                if (z + 1 < zend) vn_next = ld(vn + col + fz + sS);
+            }
+        }
 
         // phase A: interfaces of plane z along dimensions 0 and 1
         T pmx = T(0), pmy = T(0);
@@ -419,8 +442,7 @@ __device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T
                 if constexpr (uses_coord<D, DYN>(3)) xc[3] = coord(SP<T>::lo(P, 3), z, SP<T>::dx(P, 3));
             }
             if constexpr (D == 3 && uses_coord<D, DYN>(2)) xc[2] = coord(SP<T>::lo(P, 2), z, SP<T>::dx(P, 2));
-            T yd = lf_combine<T, D, DYN>(P, xc, cosz, sinz, pb, dd);
-            if (brt0) yd = fmin(yd, T(0));
+            const T yd = fmin(lf_combine<T, D, DYN>(P, xc, cosz, sinz, pb, dd, alpha_global), clamp);
             const int flat = col + fz;
             T res;
             if constexpr (KIND == kKindTerm) {
@@ -428,7 +450,7 @@ __device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T
             } else if constexpr (KIND == kKindFirst) {
                 res = center + dt * yd;
             } else {
-                const T vv = ld(vn + flat);
+                if constexpr (!kVnAhead) vv = ld(vn + flat);
                 res = cv * vv + cu * (center + dt * yd);
                 if (minv) res = fmin(res, vv);
             }

@@ -209,7 +209,7 @@ extern "C" hj_status hj_rk3_step_static(void* cuda_stream, int32_t device, const
     for (int k = 0; k < 8; ++k) P.params[k] = method->params[k];
     P.brt_min0 = method->brt == HJ_BRT_MIN0;
     // WENO5 epsilon floor per dimension in raw-difference units (1e-99 on divided differences in FP64)
-    for (int d = 0; d < 4; ++d) P.weno_floor[d] = dtype == HJ_F32 ? 1e-18 : 1e-99 * G.dx[d] * G.dx[d];
+    for (int d = 0; d < 4; ++d) P.weno_floor[d] = dtype == HJ_F32 ? (double)kWenoFloorF32 : 1e-99 * G.dx[d] * G.dx[d];
 
     void* w1 = base;
     void* w2 = base + kStageBytes;

@@ -226,7 +226,8 @@ template <> struct SP<float> {
     static __device__ __forceinline__ float dt(const StageParams& P) { return P.dt_f; }
     static __device__ __forceinline__ float cv(const StageParams& P) { return P.cv_f; }
     static __device__ __forceinline__ float cu(const StageParams& P) { return P.cu_f; }
-    static __device__ __forceinline__ float floor(const StageParams& P, int d) { return P.weno_floor_f[d]; }
+    // the FP32 floor is one constant for every dimension (no parameter load)
+    static __device__ __forceinline__ float floor(const StageParams&, int) { return kWenoFloorF32; }
 };
 
 // ---------------------------------------------------------------------------
@@ -331,7 +332,8 @@ __device__ __forceinline__ void box_alpha(const StageParams& P, const T* xc, T c
 // DYN may carry kDynBox: alpha_d is then the maximum over the node's box of
 // gradients (box_alpha) instead of alpha_d(x).
 template <typename T, int D, int DYN>
-__device__ __forceinline__ T lf_combine(const StageParams& P, const T* xc, T c, T s, const T* pb, const T* dd) {
+__device__ __forceinline__ T lf_combine(const StageParams& P, const T* xc, T c, T s, const T* pb, const T* dd,
+                                        bool alpha_global) {
     const auto q = [&P](int k) { return SP<T>::param(P, k); };
     constexpr int B = dyn_base(DYN);
     T h = T(0);
@@ -382,7 +384,7 @@ __device__ __forceinline__ T lf_combine(const StageParams& P, const T* xc, T c, 
         a[1] = fabs(f1);
     }
     if constexpr (dyn_is_box(DYN)) box_alpha<T, D, B>(P, xc, c, s, pb, dd, a);
-    if (P.alpha_global) {
+    if (alpha_global) {
 #pragma unroll
         for (int d = 0; d < D; ++d) a[d] = SP<T>::alpha_g(P, d);
     }
@@ -416,7 +418,7 @@ __device__ __forceinline__ T lf_term_dyn(const StageParams& P, const int* idx, c
         c = tr[idx[2]];
         s = tr[P.g.n[2] + idx[2]];
     }
-    return lf_combine<T, D, DYN>(P, x, c, s, pb, dd);
+    return lf_combine<T, D, DYN>(P, x, c, s, pb, dd, P.alpha_global);
 }
 
 template <typename T, int D>
