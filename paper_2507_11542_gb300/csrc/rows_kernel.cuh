@@ -319,13 +319,23 @@ __device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T
     // A warm-up step evaluates the interface below the first plane, so that
     // every interface goes through the same code and results do not depend
     // on where chunks start.
+    // In FP64 WENO5 the streamed-dimension interfaces slide along the column:
+    // each reuses the differences of the one below it (Weno5Line, bit for bit
+    // the same results as a full evaluation).
+    constexpr bool kSlide = std::is_same<T, double>::value && SCHEME == HJ_WENO5 && D >= 3;
     T q[6];
     T carry = T(0);
+    Weno5Line zline;
     if (D >= 3 && node) {
 #pragma unroll
         for (int k = 0; k < 6; ++k) q[k] = line_value(ucol, zbeg - 3 + k, ns, (long long)sS, perS, extrap);
         T unused;
-        iface_at<SCHEME>(q[0], q[1], q[2], q[3], q[4], q[5], flS, unused, carry);
+        if constexpr (kSlide) {
+            zline.start(q[0], q[1], q[2], q[3], q[4], q[5]);
+            zline.eval(flS, unused, carry);
+        } else {
+            iface_at<SCHEME>(q[0], q[1], q[2], q[3], q[4], q[5], flS, unused, carry);
+        }
 #pragma unroll
         for (int k = 0; k < 5; ++k) q[k] = q[k + 1];
     }
@@ -424,7 +434,12 @@ __device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T
             T next = T(0);
             if constexpr (D >= 3) {
                 T pps;
-                iface_at<SCHEME>(q[0], q[1], q[2], q[3], q[4], q[5], flS, pps, next);
+                if constexpr (kSlide) {
+                    zline.slide(q[4], q[5]);
+                    zline.eval(flS, pps, next);
+                } else {
+                    iface_at<SCHEME>(q[0], q[1], q[2], q[3], q[4], q[5], flS, pps, next);
+                }
                 pb[SD] = (carry + pps) * hS;
                 dd[SD] = (pps - carry) * hS;
             }

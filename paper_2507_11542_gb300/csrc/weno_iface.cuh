@@ -97,18 +97,19 @@ __device__ __forceinline__ double rcp_newton(double x) {
 // and both sides share one reciprocal 1/(denL denR). When that product
 // leaves [1e-290, 1e290] (nearly flat or huge data) each side divides alone,
 // and an exactly flat window (den = 0) returns its central candidate.
-__device__ __forceinline__ void weno_iface(double e1, double e2, double e3, double e4, double e5, double floor_raw,
-                                           double& pp_j, double& pm_j1) {
+// The core takes tA, tB, tC (the second differences of the windows' first
+// differences) and their squares, which consecutive interfaces along a line
+// share (Weno5Line).
+__device__ __forceinline__ void weno_core(double e1, double e2, double e3, double e4, double e5, double tA, double tB,
+                                          double tC, double sqA, double sqB, double sqC, double floor_raw,
+                                          double& pp_j, double& pm_j1) {
     const double k = 3.0 / 13.0;
-    const double tA = fma(-2.0, e2, e1) + e3;
-    const double tB = fma(-2.0, e3, e2) + e4;
-    const double tC = fma(-2.0, e4, e3) + e5;
     const double uA = fma(2.0, e3 - e2, tA);
     const double uB = e2 - e4;
     const double uC = fma(2.0, e3 - e4, tC);
-    const double SA = fma(tA, tA, uA * (k * uA));
-    const double SB = fma(tB, tB, uB * (k * uB));
-    const double SC = fma(tC, tC, uC * (k * uC));
+    const double SA = fma(k * uA, uA, sqA);
+    const double SB = fma(k * uB, uB, sqB);
+    const double SC = fma(k * uC, uC, sqC);
     const double amax = nonneg_max(nonneg_max(nonneg_max(abs_bits(e1), abs_bits(e2)),
                                               nonneg_max(abs_bits(e3), abs_bits(e4))), abs_bits(e5));
     const double eps = fma((12.0 / 13.0) * 1e-6, amax * amax, (12.0 / 13.0) * floor_raw);
@@ -137,6 +138,43 @@ __device__ __forceinline__ void weno_iface(double e1, double e2, double e3, doub
         pp_j = denR > 0.0 ? psi2 - numR / denR : psi2;
     }
 }
+
+// a - 2b + c for three consecutive first differences (raw units).
+__device__ __forceinline__ double curv(double a, double b, double c) { return fma(-2.0, b, a) + c; }
+
+__device__ __forceinline__ void weno_iface(double e1, double e2, double e3, double e4, double e5, double floor_raw,
+                                           double& pp_j, double& pm_j1) {
+    const double tA = curv(e1, e2, e3), tB = curv(e2, e3, e4), tC = curv(e3, e4, e5);
+    weno_core(e1, e2, e3, e4, e5, tA, tB, tC, tA * tA, tB * tB, tC * tC, floor_raw, pp_j, pm_j1);
+}
+
+// FP64 WENO5 along a grid line, one interface after the other: the interface
+// between nodes j and j+1 reuses four of the five first differences, two of
+// the three values tA, tB, tC and their squares of the interface before it,
+// so each step computes one of each. The results are those of weno_iface,
+// bit for bit (the same operations on the same operands).
+struct Weno5Line {
+    double e[5];   // first differences of the current window
+    double t[3];   // tA, tB, tC
+    double sq[3];  // their squares
+    // the window of the values v0..v5 at nodes j-2 .. j+3
+    __device__ __forceinline__ void start(double v0, double v1, double v2, double v3, double v4, double v5) {
+        e[0] = v1 - v0; e[1] = v2 - v1; e[2] = v3 - v2; e[3] = v4 - v3; e[4] = v5 - v4;
+        t[0] = curv(e[0], e[1], e[2]);
+        t[1] = curv(e[1], e[2], e[3]);
+        t[2] = curv(e[2], e[3], e[4]);
+        sq[0] = t[0] * t[0]; sq[1] = t[1] * t[1]; sq[2] = t[2] * t[2];
+    }
+    // slide by one node: v4, v5 are the values at the new window's last two nodes
+    __device__ __forceinline__ void slide(double v4, double v5) {
+        e[0] = e[1]; e[1] = e[2]; e[2] = e[3]; e[3] = e[4]; e[4] = v5 - v4;
+        t[0] = t[1]; t[1] = t[2]; t[2] = curv(e[2], e[3], e[4]);
+        sq[0] = sq[1]; sq[1] = sq[2]; sq[2] = t[2] * t[2];
+    }
+    __device__ __forceinline__ void eval(double floor_raw, double& pp_j, double& pm_j1) const {
+        weno_core(e[0], e[1], e[2], e[3], e[4], t[0], t[1], t[2], sq[0], sq[1], sq[2], floor_raw, pp_j, pm_j1);
+    }
+};
 
 // Second-order ENO (Sec. 3.2; Osher & Fedkiw 2003 Sec. 3.3) per interface.
 // Both one-sided derivatives at the interface between nodes j and j+1 (p+ of
