@@ -227,7 +227,8 @@ __device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T
     const T dt = R.dt, cv = R.cv, cu = R.cu;
     const bool minv = R.minv;
     // BRT min(0, .) as a clamp (+inf: none), global dissipation as a flag, both read once
-    const T clamp = R.brt0 ? T(0) : T(INFINITY);
+    const bool brt0 = R.brt0;
+    const T clamp = brt0 ? T(0) : T(INFINITY);
     const bool alpha_global = P.alpha_global;
     T* __restrict__ also_out = R.also_out;
     // node coordinates that do not change along the streamed dimension
@@ -457,7 +458,13 @@ __device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T
                 if constexpr (uses_coord<D, DYN>(3)) xc[3] = coord(SP<T>::lo(P, 3), z, SP<T>::dx(P, 3));
             }
             if constexpr (D == 3 && uses_coord<D, DYN>(2)) xc[2] = coord(SP<T>::lo(P, 2), z, SP<T>::dx(P, 2));
-            const T yd = fmin(lf_combine<T, D, DYN>(P, xc, cosz, sinz, pb, dd, alpha_global), clamp);
+            T yd = lf_combine<T, D, DYN>(P, xc, cosz, sinz, pb, dd, alpha_global);
+            if constexpr (std::is_same<T, double>::value) {
+                // BRT min(0, .) on the bit pattern: positive values (and +NaN) become 0
+                if (brt0 && __double_as_longlong(yd) > 0) yd = 0.0;
+            } else {
+                yd = fminf(yd, clamp);
+            }
             const int flat = col + fz;
             T res;
             if constexpr (KIND == kKindTerm) {

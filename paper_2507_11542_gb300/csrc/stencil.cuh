@@ -19,6 +19,19 @@ __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, 
 __device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
 
+// |x|, and the maximum of two non-negative values, for FP64 as integer
+// operations on the bit patterns (non-negative doubles order like their bits):
+// exact, and off the FP64 pipe that bounds the FP64 kernels. FP32 as usual.
+__device__ __forceinline__ double absv(double a) {
+    return __longlong_as_double(__double_as_longlong(a) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ float absv(float a) { return fabsf(a); }
+__device__ __forceinline__ double max_nonneg(double a, double b) {
+    const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+    return __longlong_as_double(ia > ib ? ia : ib);
+}
+__device__ __forceinline__ float max_nonneg(float a, float b) { return fmaxf(a, b); }
+
 template <typename T> __device__ __forceinline__ T sgn(T v) {
     return (v > T(0)) ? T(1) : ((v < T(0)) ? T(-1) : T(0));
 }
@@ -251,8 +264,8 @@ __host__ __device__ constexpr bool uses_angle() {
 template <typename T>
 __device__ __forceinline__ T max_over_signs(T d, T k, bool plus, bool minus) {
     T best = T(0);
-    if (plus) best = fmax(best, fabs(d + k));
-    if (minus) best = fmax(best, fabs(d - k));
+    if (plus) best = max_nonneg(best, absv(d + k));
+    if (minus) best = max_nonneg(best, absv(d - k));
     return best;
 }
 
@@ -273,7 +286,7 @@ __device__ __forceinline__ void box_alpha(const StageParams& P, const T* xc, T c
     T lo[D], hi[D];
 #pragma unroll
     for (int d = 0; d < D; ++d) {
-        const T w = fabs(dd[d]);
+        const T w = absv(dd[d]);
         lo[d] = pb[d] - w;
         hi[d] = pb[d] + w;
     }
@@ -282,12 +295,12 @@ __device__ __forceinline__ void box_alpha(const StageParams& P, const T* xc, T c
         T small2[D];
 #pragma unroll
         for (int j = 0; j < D; ++j) {
-            const T m = (lo[j] <= T(0) && hi[j] >= T(0)) ? T(0) : fmin(fabs(lo[j]), fabs(hi[j]));
+            const T m = (lo[j] <= T(0) && hi[j] >= T(0)) ? T(0) : fmin(absv(lo[j]), absv(hi[j]));
             small2[j] = m * m;
         }
 #pragma unroll
         for (int d = 0; d < D; ++d) {
-            const T big = fmax(fabs(lo[d]), fabs(hi[d]));
+            const T big = max_nonneg(absv(lo[d]), absv(hi[d]));
             T others = T(0);
 #pragma unroll
             for (int j = 0; j < D; ++j)
@@ -305,7 +318,7 @@ __device__ __forceinline__ void box_alpha(const StageParams& P, const T* xc, T c
         a[1] = max_over_signs(f1, -amax * xc[0], plus, minus);
         const T top = fmax(lo[2], T(0)), bot = fmin(hi[2], T(0));
         const bool same = (top <= hi[2] && b0 - a1 - top >= T(0)) || (lo[2] <= bot && a0 - b1 - bot <= T(0));
-        a[2] = same ? amax + bmax : fabs(amax - bmax);
+        a[2] = same ? amax + bmax : absv(amax - bmax);
     } else if constexpr (B == HJ_DYN_ROCKETS && D == 3) {
         const T ac = q(0), g = q(1), ue = q(2), up = q(3);
         const T f0 = ac * c, f1 = ac * s + ac - g;
@@ -315,7 +328,7 @@ __device__ __forceinline__ void box_alpha(const StageParams& P, const T* xc, T c
         a[0] = max_over_signs(f0, ue * xc[0], b0 - lo[2] >= T(0), a0 - hi[2] <= T(0));
         a[1] = max_over_signs(f1, -up * xc[0], b1 + hi[2] >= T(0), a1 + lo[2] <= T(0));
         const bool same = fmax(lo[2], -b1) <= fmin(hi[2], b0) || fmax(lo[2], a0) <= fmin(hi[2], -a1);
-        a[2] = same ? ue + up : fabs(ue - up);
+        a[2] = same ? ue + up : absv(ue - up);
     }
 }
 
@@ -342,29 +355,29 @@ __device__ __forceinline__ T lf_combine(const StageParams& P, const T* xc, T c, 
     for (int d = 0; d < D; ++d) a[d] = T(0);
     if constexpr (B == HJ_DYN_DOUBLE_INTEGRATOR && D == 2) {
         const T umax = q(0);
-        h = pb[0] * xc[1] - umax * fabs(pb[1]);
-        a[0] = fabs(xc[1]);
+        h = pb[0] * xc[1] - umax * absv(pb[1]);
+        a[0] = absv(xc[1]);
         a[1] = umax;
     } else if constexpr (B == HJ_DYN_AIR3D && D == 3) {
         const T va = q(0), vb = q(1), amax = q(2), bmax = q(3);
         const T f0 = -va + vb * c, f1 = vb * s;
-        h = pb[0] * f0 + pb[1] * f1 + amax * fabs(pb[0] * xc[1] - pb[1] * xc[0] - pb[2]) - bmax * fabs(pb[2]);
-        a[0] = fabs(f0) + amax * fabs(xc[1]);
-        a[1] = fabs(f1) + amax * fabs(xc[0]);
+        h = pb[0] * f0 + pb[1] * f1 + amax * absv(pb[0] * xc[1] - pb[1] * xc[0] - pb[2]) - bmax * absv(pb[2]);
+        a[0] = absv(f0) + amax * absv(xc[1]);
+        a[1] = absv(f1) + amax * absv(xc[0]);
         a[2] = amax + bmax;
     } else if constexpr (B == HJ_DYN_ROCKETS && D == 3) {
         const T ac = q(0), g = q(1), ue = q(2), up = q(3);
         const T f0 = ac * c, f1 = ac * s + ac - g;
-        h = pb[0] * f0 + pb[1] * f1 + ue * fabs(pb[0] * xc[0] - pb[2]) - up * fabs(pb[1] * xc[0] + pb[2]);
-        a[0] = fabs(f0) + ue * fabs(xc[0]);
-        a[1] = fabs(f1) + up * fabs(xc[0]);
+        h = pb[0] * f0 + pb[1] * f1 + ue * absv(pb[0] * xc[0] - pb[2]) - up * absv(pb[1] * xc[0] + pb[2]);
+        a[0] = absv(f0) + ue * absv(xc[0]);
+        a[1] = absv(f1) + up * absv(xc[0]);
         a[2] = ue + up;
     } else if constexpr (B == HJ_DYN_DUBINS4D && D == 4) {
         const T wmax = q(0), accmax = q(1);
         const T f0 = xc[3] * c, f1 = xc[3] * s;
-        h = pb[0] * f0 + pb[1] * f1 - wmax * fabs(pb[2]) - accmax * fabs(pb[3]);
-        a[0] = fabs(f0);
-        a[1] = fabs(f1);
+        h = pb[0] * f0 + pb[1] * f1 - wmax * absv(pb[2]) - accmax * absv(pb[3]);
+        a[0] = absv(f0);
+        a[1] = absv(f1);
         a[2] = wmax;
         a[3] = accmax;
     } else if constexpr (B == HJ_DYN_NORM) {
@@ -375,13 +388,13 @@ __device__ __forceinline__ T lf_combine(const StageParams& P, const T* xc, T c, 
         h = -cn * sqrt(s2);
     } else if constexpr (B == HJ_DYN_ADVECT) {
 #pragma unroll
-        for (int d = 0; d < D; ++d) { const T cd = q(d); h += -cd * pb[d]; a[d] = fabs(cd); }
+        for (int d = 0; d < D; ++d) { const T cd = q(d); h += -cd * pb[d]; a[d] = absv(cd); }
     } else if constexpr (B == HJ_DYN_ROTATE && D >= 2) {
         const T w = q(0);
         const T f0 = -w * xc[1], f1 = w * xc[0];
         h = -(pb[0] * f0 + pb[1] * f1);
-        a[0] = fabs(f0);
-        a[1] = fabs(f1);
+        a[0] = absv(f0);
+        a[1] = absv(f1);
     }
     if constexpr (dyn_is_box(DYN)) box_alpha<T, D, B>(P, xc, c, s, pb, dd, a);
     if (alpha_global) {

@@ -184,12 +184,19 @@ struct Weno5Line {
 // (undivided) units, from the values v0..v3 at nodes j-1 .. j+2:
 //   e = v2 - v1, dL = e - (v1 - v0), dR = (v3 - v2) - e,
 //   c = |dL| <= |dR| ? dL : dR,  p+_j = e - c/2,  p-_{j+1} = e + c/2.
+// |a| <= |b|: for FP64 on the bit patterns (an integer comparison, exact for
+// finite values).
+__device__ __forceinline__ bool abs_le(double a, double b) {
+    return (__double_as_longlong(a) & 0x7fffffffffffffffLL) <= (__double_as_longlong(b) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ bool abs_le(float a, float b) { return fabsf(a) <= fabsf(b); }
+
 template <typename T>
 __device__ __forceinline__ void eno2_iface(T v0, T v1, T v2, T v3, T& pp_j, T& pm_j1) {
     const T e = v2 - v1;
     const T dL = e - (v1 - v0);
     const T dR = (v3 - v2) - e;
-    const T c = (fabs(dL) <= fabs(dR)) ? dL : dR;
+    const T c = abs_le(dL, dR) ? dL : dR;
     pp_j = e - T(0.5) * c;
     pm_j1 = e + T(0.5) * c;
 }
@@ -209,11 +216,11 @@ template <typename T>
 __device__ __forceinline__ void eno3_iface(T v0, T v1, T v2, T v3, T v4, T v5, T& pp_j, T& pm_j1) {
     const T e0 = v1 - v0, e1 = v2 - v1, e2 = v3 - v2, e3 = v4 - v3, e4 = v5 - v4;
     const T dm = e1 - e0, d0 = e2 - e1, d1 = e3 - e2, d2 = e4 - e3;  // second differences at j-1, j, j+1, j+2
-    const bool left = fabs(d0) <= fabs(d1);
+    const bool left = abs_le(d0, d1);
     const T c = left ? d0 : d1;
     const T a = left ? d0 - dm : d1 - d0;  // third differences next to k*
     const T b = left ? d1 - d0 : d2 - d1;
-    const T cs = (fabs(a) <= fabs(b)) ? a : b;
+    const T cs = abs_le(a, b) ? a : b;
     const T third = cs * T(1.0 / 6.0);
     pp_j = e2 - T(0.5) * c + (left ? -third : T(2) * third);
     pm_j1 = e2 + T(0.5) * c + (left ? T(2) * third : -third);
