@@ -425,13 +425,16 @@ __device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T
         }
         if (node) {
             const T center = (D >= 3) ? q[2] : ld(ucol);
-            T pb[D], dd[D];
+            // raw sums and differences of the one-sided derivatives, and 1/(2 dx)
+            T sm[D], df[D], hh[D];
             const T ppx = bz[s_pxp + 1];
             const T ppy = bz[s_pyr];
-            pb[0] = (pmx + ppx) * h0;
-            dd[0] = (ppx - pmx) * h0;
-            pb[1] = (pmy + ppy) * h1;
-            dd[1] = (ppy - pmy) * h1;
+            sm[0] = pmx + ppx;
+            df[0] = ppx - pmx;
+            hh[0] = h0;
+            sm[1] = pmy + ppy;
+            df[1] = ppy - pmy;
+            hh[1] = h1;
             T next = T(0);
             if constexpr (D >= 3) {
                 T pps;
@@ -441,8 +444,9 @@ __device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T
                 } else {
                     iface_at<SCHEME>(q[0], q[1], q[2], q[3], q[4], q[5], flS, pps, next);
                 }
-                pb[SD] = (carry + pps) * hS;
-                dd[SD] = (pps - carry) * hS;
+                sm[SD] = carry + pps;
+                df[SD] = pps - carry;
+                hh[SD] = hS;
             }
             if constexpr (D == 4) {
                 // dimension 2: both interfaces of the node from a 7-point line
@@ -452,13 +456,13 @@ __device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T
                 const T fl2 = SP<T>::floor(P, 2);
                 iface_at<SCHEME>(v[0], v[1], v[2], v[3], v[4], v[5], fl2, unused0, pm2);
                 iface_at<SCHEME>(v[1], v[2], v[3], v[4], v[5], v[6], fl2, pp2, unused1);
-                const T h2 = SP<T>::half_inv_dx(P, 2);
-                pb[2] = (pm2 + pp2) * h2;
-                dd[2] = (pp2 - pm2) * h2;
+                sm[2] = pm2 + pp2;
+                df[2] = pp2 - pm2;
+                hh[2] = SP<T>::half_inv_dx(P, 2);
                 if constexpr (uses_coord<D, DYN>(3)) xc[3] = coord(SP<T>::lo(P, 3), z, SP<T>::dx(P, 3));
             }
             if constexpr (D == 3 && uses_coord<D, DYN>(2)) xc[2] = coord(SP<T>::lo(P, 2), z, SP<T>::dx(P, 2));
-            T yd = lf_combine<T, D, DYN>(P, xc, cosz, sinz, pb, dd, alpha_global);
+            T yd = lf_combine_raw<T, D, DYN>(P, xc, cosz, sinz, sm, df, hh, alpha_global);
             if constexpr (std::is_same<T, double>::value) {
                 // BRT min(0, .) on the bit pattern: positive values (and +NaN) become 0
                 if (brt0 && __double_as_longlong(yd) > 0) yd = 0.0;

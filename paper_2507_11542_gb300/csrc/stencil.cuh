@@ -407,6 +407,22 @@ __device__ __forceinline__ T lf_combine(const StageParams& P, const T* xc, T c, 
     return y;
 }
 
+// The Lax-Friedrichs term from the raw (undivided) one-sided derivatives:
+// sums S_d = p-_d + p+_d and differences Q_d = p+_d - p-_d, with h_d =
+// 1/(2 dx_d), so that the mean is h_d S_d and the half difference h_d Q_d.
+// (Folding h_d into the air3D coefficients instead was measured slower.)
+template <typename T, int D, int DYN>
+__device__ __forceinline__ T lf_combine_raw(const StageParams& P, const T* xc, T c, T s, const T* S, const T* Q,
+                                            const T* h, bool alpha_global) {
+    T pb[D], dd[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        pb[d] = S[d] * h[d];
+        dd[d] = Q[d] * h[d];
+    }
+    return lf_combine<T, D, DYN>(P, xc, c, s, pb, dd, alpha_global);
+}
+
 // Whether a dynamics reads the coordinate of dimension d (the others are not computed).
 template <int D, int DYN>
 __host__ __device__ constexpr bool uses_coord(int d) {

@@ -65,7 +65,7 @@ __device__ __forceinline__ void weno_iface(float e1, float e2, float e3, float e
     const float numR = fmaf(0.05f, X, (1.0f / 30.0f) * Y);
     const float c5 = (5.0f / 6.0f) * e3;
     const float phi2 = fmaf(1.0f / 3.0f, e4, fmaf(-1.0f / 6.0f, e2, c5));
-    const float psi2 = fmaf(1.0f / 3.0f, e2, fmaf(-1.0f / 6.0f, e4, c5));
+    const float psi2 = fmaf(0.5f, uB, phi2);  // psi2 - phi2 = (e2 - e4) / 2
     pm_j1 = fmaf(numL, rcp_approx(denL), phi2);
     pp_j = fmaf(-numR, rcp_approx(denR), psi2);
 }
@@ -125,7 +125,7 @@ __device__ __forceinline__ void weno_core(double e1, double e2, double e3, doubl
     const double numR = fma(0.05, X, (1.0 / 30.0) * Y);
     const double c5 = (5.0 / 6.0) * e3;
     const double phi2 = fma(1.0 / 3.0, e4, fma(-1.0 / 6.0, e2, c5));
-    const double psi2 = fma(1.0 / 3.0, e2, fma(-1.0 / 6.0, e4, c5));
+    const double psi2 = fma(0.5, uB, phi2);  // psi2 - phi2 = (e2 - e4) / 2
     const double den2 = denL * denR;
     const long long bits = __double_as_longlong(den2);
     const int expo = (int)((bits >> 52) & 0x7ff);  // 1e-290 < den2 < 1e290 (integer test)
