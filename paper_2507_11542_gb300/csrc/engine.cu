@@ -325,7 +325,7 @@ hj_status Engine::activate(std::vector<int>* failed) {
             D.cursor = 1;
         }
         D.dt_f = (float)D.dt;
-        S.lane = !multirate_ ? 0 : (S.N > kLaneNodes[0] ? 0 : (S.N > kLaneNodes[1] ? 1 : 2));
+        S.lane = !multirate_ ? 0 : lane_of(S.N);
         D.lane = S.lane;
         // group
         const int dyn = S.prob.method.dynamics;
@@ -495,7 +495,9 @@ hj_status Engine::shape_group(Group& g, const std::vector<int>& members, const s
 }
 
 hj_status Engine::rebuild_tiles() {
-    if (exec_[0] || exec_[1] || exec_[2]) {
+    bool any_graph = false;
+    for (int l = 0; l < kLanes; ++l) any_graph = any_graph || exec_[l] != nullptr;
+    if (any_graph) {
         HJ_CUDA(ctx_, cudaStreamSynchronize(stream_));
         drop_graphs();
     }

@@ -100,17 +100,21 @@ class Engine {
     long long launches = 0;
 
  private:
-    static constexpr int kLanes = 3;
-    static constexpr int kLaneMult[kLanes] = {1, 4, 16};
-    // lane of an instance of N nodes: 0 above kLaneNodes[0], 1 above kLaneNodes[1], else 2
-    static constexpr long long kLaneNodes[2] = {1LL << 22, 1LL << 20};
+    // Multipliers about inversely proportional to size, so that requests of
+    // different sizes get similar shares of the GPU per tick (the smallest
+    // lane's multiplier is capped: more steps of tiny launches only slow the
+    // other lanes down). Chosen by measurement on the served workload.
+    static constexpr int kLanes = 5;
+    static constexpr int kLaneMult[kLanes] = {1, 2, 4, 8, 8};
+    // lane of an instance of N nodes: the first l with N > kLaneNodes[l], else the last
+    static constexpr long long kLaneNodes[kLanes - 1] = {1LL << 24, 1LL << 23, 1LL << 22, 1LL << 21};
 
     struct Group {
         int dtype = 0, ndim = 0, dyn = 0, scheme = HJ_WENO5;
         int threads = 0, tz_target = 8;
         size_t smem = 0;
         std::vector<BatchTile> tiles;     // instances by lane, then by size (largest first)
-        size_t lane_off[kLanes] = {0, 0, 0};  // first tile of an instance of lane >= l
+        size_t lane_off[kLanes] = {};  // first tile of an instance of lane >= l
         BatchTile* d_tiles = nullptr;
         size_t tile_cap = 0;
     };
@@ -119,6 +123,11 @@ class Engine {
     // One RK3 step of the instances of lane `lane` (exact) or of lanes >= lane.
     cudaError_t enqueue_step(cudaStream_t s, bool count, int lane, bool exact);
     size_t lane_end(const Group& g, int lane) const { return lane + 1 < kLanes ? g.lane_off[lane + 1] : g.tiles.size(); }
+    static int lane_of(long long nodes) {
+        int l = 0;
+        while (l < kLanes - 1 && nodes <= kLaneNodes[l]) ++l;
+        return l;
+    }
     long long dead_tiles() const;
 
     hj_ctx* ctx_ = nullptr;
@@ -134,13 +143,13 @@ class Engine {
     bool tiles_dirty_ = true;
     long long tiles_total_ = 0;
     bool multirate_ = false;
-    cudaGraphExec_t exec_[kLanes] = {nullptr, nullptr, nullptr};  // the step blocks of each lane
-    int exec_K_[kLanes] = {0, 0, 0};
+    cudaGraphExec_t exec_[kLanes] = {};  // the step blocks of each lane
+    int exec_K_[kLanes] = {};
     // multirate: each lane's step block runs on a stream of its own, forked
     // from and joined back into stream_, so that the lanes overlap on the GPU
-    cudaStream_t lane_stream_[kLanes] = {nullptr, nullptr, nullptr};
+    cudaStream_t lane_stream_[kLanes] = {};
     cudaEvent_t fork_ev_ = nullptr;
-    cudaEvent_t lane_ev_[kLanes] = {nullptr, nullptr, nullptr};
+    cudaEvent_t lane_ev_[kLanes] = {};
     void drop_graphs();
     std::vector<int> pending_;
 };

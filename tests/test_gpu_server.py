@@ -70,17 +70,17 @@ def test_served_results_equal_solo_solves(ctx, dtype, tol):
 
 
 def test_rate_lanes_let_small_requests_finish_first(ctx):
-    # Instances above 4M nodes step once per server step, those above 1M four
-    # times, smaller ones sixteen times: submitted together, a small request
-    # retires long before a large one, and every result still equals the
-    # problem solved alone.
+    # Rate lanes: instances above 16M nodes step once per server step, then
+    # twice (above 8M), four times (above 4M), eight times (smaller): a
+    # request that needs fewer server steps retires first, and every result
+    # still equals the problem solved alone.
     from paper_2507_11542_gb300 import _lib as L, solver
     reqs = []
-    g, V0 = W.air3d(161, 5.0)  # 4.17M nodes: lane 0
+    g, V0 = W.air3d(161, 5.0)  # 4.17M nodes: four steps per server step, 140 steps
     reqs.append((g, lib_method(dynamics=AIR3D), to_dev(V0, "float32"), [0.1, 0.3]))
-    g, V0 = W.air3d(101, 4.0)  # 1.03M nodes: lane 1
+    g, V0 = W.air3d(101, 4.0)  # 1.03M nodes: eight steps per server step, 84 steps
     reqs.append((g, lib_method(dynamics=AIR3D), to_dev(V0, "float32"), [0.3]))
-    g, V0 = W.double_integrator(81, 0.5)  # 6561 nodes: lane 2
+    g, V0 = W.double_integrator(81, 0.5)  # 6561 nodes: eight steps per server step, 50 steps
     reqs.append((g, lib_method(dynamics=DI), to_dev(V0, "float32"), [0.25, 0.5]))
     with solver.Server(ctx, hbm_budget=1 << 30, max_slots=4) as srv:
         tickets = [srv.submit(g, m, v0, ts) for g, m, v0, ts in reqs]
