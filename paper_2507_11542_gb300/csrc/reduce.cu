@@ -109,6 +109,20 @@ __global__ void __launch_bounds__(256) step_bound_kernel(const BoundArgs A) {
     }
 }
 
+// Streaming multiprocessors of the current device (grid-stride kernels size
+// their grids in multiples of it), read once per device.
+static int device_sms() {
+    static int sms[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+    if (!sms[dev]) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+        sms[dev] = n;  // benign race: every writer stores the same value
+    }
+    return sms[dev];
+}
+
 cudaError_t launch_step_bound(const GridDev& g, int dynamics, const double* params, const double* trig_d,
                               unsigned long long* acc, int per_dim, cudaStream_t s) {
     BoundArgs A;
@@ -119,7 +133,8 @@ cudaError_t launch_step_bound(const GridDev& g, int dynamics, const double* para
     A.trig = trig_d;
     A.acc = acc;
     long long blocks = (g.total + 255) / 256;
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    const long long cap = 16LL * device_sms();  // a few waves of resident blocks
+    if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     step_bound_kernel<<<(unsigned)blocks, 256, 0, s>>>(A);
     return cudaGetLastError();
@@ -138,7 +153,8 @@ __global__ void __launch_bounds__(256) nonfinite_kernel(const T* __restrict__ v,
 template <typename T>
 static cudaError_t launch_nonfinite(const T* v, long long n, int* flag, cudaStream_t s) {
     long long blocks = (n + 255) / 256;
-    if (blocks > 152 * 8) blocks = 152 * 8;
+    const long long cap = 8LL * device_sms();
+    if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     nonfinite_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(v, n, flag);
     return cudaGetLastError();
