@@ -131,13 +131,15 @@ typedef struct hj_method {
     int32_t order;     /* TVD-RK order of a time step: 1 (forward Euler), 2 or 3 (Shu-Osher); 0 means 3 */
     int32_t alpha_mode;/* HJ_ALPHA_NODE, HJ_ALPHA_GLOBAL or HJ_ALPHA_BOX */
     int32_t kernel;    /* HJ_KERNEL_AUTO (0), HJ_KERNEL_ROWS or HJ_KERNEL_NODE */
-    /* Launch shape of the row kernel {ty, tz, occ, merged}, all 0 (the
+    /* Launch shape of the row kernel {ty, tz, occ, flags}, all 0 (the
      * default): picked by the context's tuner (timed once per grid, dtype,
      * dynamics and scheme, then cached). Otherwise: ty node rows per block,
      * tz planes per chunk along the last dimension (3-D and 4-D grids), occ 1
-     * or 2 resident blocks per SM (2: FP32 blocks of at most 544 threads),
-     * merged 1 for blocks of n0*ty threads whose last node row also takes the
-     * row ends. Results do not depend on the shape (bit for bit). A shape that
+     * or 2 resident blocks per SM (2: FP32 blocks of at most 544 threads);
+     * flags bit 0: blocks of n0*ty threads whose last node row also takes the
+     * row ends; bit 1: tiles away from the grid's edges keep the general body
+     * (the ENO schemes otherwise run them on a body compiled without ghost
+     * logic). Results do not depend on the shape (bit for bit). A shape that
      * does not fit the grid is HJ_EINVAL. Used by hj_term, hj_rk3_step,
      * hj_rk3_stage and hj_solve; a problem that sets it (or kernel = NODE) is
      * solved on its own by hj_solve_batch and refused by hj_server_submit. */

@@ -75,7 +75,7 @@ hj_status check_method(hj_ctx* ctx, const hj_grid* g, const hj_method* m) {
     if (m->kernel != HJ_KERNEL_AUTO && m->kernel != HJ_KERNEL_ROWS && m->kernel != HJ_KERNEL_NODE)
         return fail(ctx, HJ_EINVAL, "unknown kernel %d", m->kernel);
     const int32_t* to = m->tile_override;
-    if (to[0] < 0 || to[1] < 0 || to[2] < 0 || to[2] > 2 || to[3] < 0 || to[3] > 1)
+    if (to[0] < 0 || to[1] < 0 || to[2] < 0 || to[2] > 2 || to[3] < 0 || to[3] > 3)
         return fail(ctx, HJ_EINVAL, "tile_override {%d, %d, %d, %d} malformed", to[0], to[1], to[2], to[3]);
     if (to[0] == 0 && (to[1] || to[2] || to[3]))
         return fail(ctx, HJ_EINVAL, "tile_override needs ty >= 1 (all zero: tuned)");
@@ -319,6 +319,7 @@ RowsCfg make_rows_cfg(const GridDev& G, int ty, int tz, int dtype) {
     c.ty = ty;
     c.nt = rows_block_threads(G.n[0], ty, rows_max_threads(dtype == HJ_F64));
     c.occ = 1;
+    c.split = 0;
     c.row_tiles = (G.n[1] + ty - 1) / ty;
     const int ns = G.ndim >= 3 ? G.n[G.ndim - 1] : 1;
     c.tz = G.ndim >= 3 ? tz : 1;
@@ -412,11 +413,13 @@ hj_status rows_config(hj_ctx* ctx, const StageParams& P, int dtype, const int32_
             *out = hit->second;
             return HJ_OK;
         }
-        const int ty = tile[0], tz = tile[1] > 0 ? tile[1] : 1, occ = tile[2] > 0 ? tile[2] : 1, merged = tile[3];
+        const int ty = tile[0], tz = tile[1] > 0 ? tile[1] : 1, occ = tile[2] > 0 ? tile[2] : 1;
+        const int merged = tile[3] & 1, split = (tile[3] & 2) ? 0 : 1;
         if (ty <= G.n[1] && ty <= G.n[0] && (G.n[0] + 1 - merged) * ty <= rows_max_threads(dtype == HJ_F64)) {
             *out = make_rows_cfg(G, ty, tz, dtype);
             if (merged) out->nt = G.n[0] * ty;
             out->occ = occ;
+            out->split = split;
             if (occ == 2 && (dtype == HJ_F64 || out->nt > kRowsOcc2Threads)) out->occ = 0;
             if (out->occ && out->nchunks <= 65535 && rows_bps(P, *out, dtype) > 0) {
                 ctx->rows_cache[pkey] = *out;
@@ -475,8 +478,28 @@ hj_status rows_config(hj_ctx* ctx, const StageParams& P, int dtype, const int32_
                 best = c;
             }
         }
+        // the ENO schemes: the best shape once more with interior tiles on
+        // their own body (the WENO5 kernels have no second body)
+        cudaError_t e = cudaSuccess;
+        if (P.scheme != HJ_WENO5) {
+            RowsCfg c = best;
+            c.split = 1;
+            e = rows_launch(ctx, T, c, dtype);
+            float ms_min = 1e30f;
+            for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+                cudaEventRecord(e0, ctx->stream);
+                for (int k = 0; k < group && e == cudaSuccess; ++k) e = rows_launch(ctx, T, c, dtype);
+                cudaEventRecord(e1, ctx->stream);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float ms = 0.f;
+                if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+                ms_min = std::min(ms_min, ms);
+            }
+            if (e == cudaSuccess && ms_min < best_ms) best = c;
+        }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "tuning launch");
     }
     ctx->rows_cache[key] = best;
     *out = best;

@@ -142,6 +142,7 @@ struct RowsCfg {
     int nchunks;    // chunks along the streamed dimension
     int row_tiles;  // ceil(n1 / ty)
     int occ;        // 1, or 2: FP32 kernel compiled for two resident blocks of <= kRowsOcc2Threads threads per SM
+    int split;      // 1: interior tiles take the body compiled without ghost and wrap logic (ENO schemes)
 };
 
 // Threads of a row-kernel block with ty node rows of n0 nodes: one thread per

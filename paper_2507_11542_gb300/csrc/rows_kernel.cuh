@@ -140,7 +140,11 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 //               from the column queues, halo rows and row ends copied
 //               asynchronously), two planes ahead of its use.
 // Flat indices are 32-bit (the grid has fewer than 2^31 nodes).
-template <typename T, int D, int DYN, int SCHEME, int KIND>
+//
+// IN: the tile is interior (all TY rows in the grid, its halo rows and the
+// chunk's streamed-dimension reads inside the grid): no ghost or wrap logic
+// is compiled for its staging and queue loads (a block-uniform dispatch).
+template <typename T, int D, int DYN, int SCHEME, int KIND, bool IN = false>
 __device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T>& R, const int TY, const int NT,
                                           const int tz, const int row_tile, const int i2_in, const int chunk_in,
                                           const int t, T* const smem) {
@@ -209,7 +213,7 @@ __device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T
     const int sS = (D >= 3) ? (int)g.stride[SD] : 0;
     const bool perS = (D >= 3) ? ((g.periodic_mask >> SD) & 1u) : false;
     // the chunk's streamed-dimension reads stay inside the grid: no ghost logic needed
-    const bool z_inside = (D < 3) || (zbeg >= 3 && zend + 3 <= ns);
+    const bool z_inside = IN || (D < 3) || (zbeg >= 3 && zend + 3 <= ns);
     const int plane0 = (D == 4) ? i2 * (int)g.stride[2] : 0;      // flat index of (0, 0, i2, 0)
     const int col = plane0 + min(x, nx - 1) + min(y, ny - 1) * nx;  // flat index of (x, y) at streamed index 0
     const T* __restrict__ ucol = u + col;
@@ -262,9 +266,9 @@ __device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T
         const int rr = (h < 3) ? h - 3 : rows_valid + (h - 3);
         int yy = y0 + rr;
         T* dst = b + (rr + 3) * W + 3 + hx;
-        if (per1 && (yy < 0 || yy >= ny)) yy = (yy % ny + ny) % ny;
+        if (!IN && per1 && (yy < 0 || yy >= ny)) yy = (yy % ny + ny) % ny;
         const T* base = u + plane0 + fp + hx;
-        if (yy >= 0 && yy < ny) cp_async_elem(dst, base + yy * nx);
+        if (IN || (yy >= 0 && yy < ny)) cp_async_elem(dst, base + yy * nx);
         else *dst = line_value(base, yy, ny, (long long)nx, false, extrap);
     };
     // this thread's first halo slot (the same in every plane): destination and source
@@ -273,8 +277,8 @@ __device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T
     const int h0_rr = (h0_h < 3) ? h0_h - 3 : rows_valid + (h0_h - 3);
     const int h0_dst = (h0_rr + 3) * W + 3 + h0_x;
     int h0_yy = y0 + h0_rr;
-    if (per1 && (h0_yy < 0 || h0_yy >= ny)) h0_yy = (h0_yy % ny + ny) % ny;
-    const bool h0_in = h0_yy >= 0 && h0_yy < ny;
+    if (!IN && per1 && (h0_yy < 0 || h0_yy >= ny)) h0_yy = (h0_yy % ny + ny) % ny;
+    const bool h0_in = IN || (h0_yy >= 0 && h0_yy < ny);
     const int h0_src = plane0 + h0_x + (h0_in ? h0_yy * nx : 0);
     auto stage_rest = [&](int p, T* b) {
         const int fp = p * sS;
@@ -329,7 +333,8 @@ __device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T
     Weno5Line zline;
     if (D >= 3 && node) {
 #pragma unroll
-        for (int k = 0; k < 6; ++k) q[k] = line_value(ucol, zbeg - 3 + k, ns, (long long)sS, perS, extrap);
+        for (int k = 0; k < 6; ++k)
+            q[k] = IN ? ld(ucol + (zbeg - 3 + k) * sS) : line_value(ucol, zbeg - 3 + k, ns, (long long)sS, perS, extrap);
         T unused;
         if constexpr (kSlide) {
             zline.start(q[0], q[1], q[2], q[3], q[4], q[5]);
@@ -491,14 +496,38 @@ __device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T
     }
 }
 
+// Whether tile (row_tile, chunk) is interior: all its TY rows and three halo
+// rows on each side inside the grid along dimension 1, and its chunk's planes
+// with three on each side inside the grid along the streamed dimension.
+template <int D>
+__device__ __forceinline__ bool rows_interior(const GridDev& g, int ty, int tz, int row_tile, int chunk) {
+    const int y0 = row_tile * ty;
+    bool in = y0 >= 3 && y0 + ty + 3 <= g.n[1];
+    if constexpr (D >= 3) {
+        const int zbeg = chunk * tz, zend = min(g.n[D - 1], zbeg + tz);
+        in = in && zbeg >= 3 && zend + 3 <= g.n[D - 1];
+    }
+    return in;
+}
+
 template <typename T, int D, int DYN, int SCHEME, int KIND, int OCC>
 __global__ void __launch_bounds__(RowsBounds<T, OCC>::kThreads, OCC) rows_kernel(const StageParams P, const RowsCfg C) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const StageRun<T> R = stage_run<T>(P);
     const int i2 = (D == 4) ? (int)blockIdx.y : 0;
     const int chunk = (D == 3) ? (int)blockIdx.y : ((D == 4) ? (int)blockIdx.z : 0);
-    rows_tile<T, D, DYN, SCHEME, KIND>(P, R, C.ty, C.nt, C.tz, blockIdx.x, i2, chunk, threadIdx.x,
-                                       reinterpret_cast<T*>(smem_raw));
+    // the interior body is compiled for the ENO schemes only: there it pays
+    // (their per-node arithmetic is small beside the staging logic), while a
+    // second WENO5 body measured slower on every grid
+    if constexpr (SCHEME != HJ_WENO5) {
+        if (C.split && rows_interior<D>(P.g, C.ty, C.tz, blockIdx.x, chunk)) {
+            rows_tile<T, D, DYN, SCHEME, KIND, true>(P, R, C.ty, C.nt, C.tz, blockIdx.x, i2, chunk, threadIdx.x,
+                                                     reinterpret_cast<T*>(smem_raw));
+            return;
+        }
+    }
+    rows_tile<T, D, DYN, SCHEME, KIND, false>(P, R, C.ty, C.nt, C.tz, blockIdx.x, i2, chunk, threadIdx.x,
+                                              reinterpret_cast<T*>(smem_raw));
 }
 
 // Shared memory of a rows_kernel block.

@@ -131,6 +131,7 @@ bool pick_rows(const StageParams& P, int dtype, int sm_count, RowsCfg* c) {
     c->ty = ty;
     c->nt = rows_block_threads(nx, ty, max_threads);
     c->occ = 1;
+    c->split = 1;  // interior tiles on the body without ghost logic (the same bits either way)
     c->row_tiles = (ny + ty - 1) / ty;
     const int ns = D >= 3 ? G.n[D - 1] : 1;
     const long long per_plane = (long long)c->row_tiles * (D == 4 ? G.n[2] : 1);

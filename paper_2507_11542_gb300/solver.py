@@ -43,7 +43,7 @@ def method(scheme=L.HJ_WENO5, dynamics=L.HJ_DYN_DOUBLE_INTEGRATOR, params=(), br
            extrap=L.HJ_EXTRAP_AWAY_FROM_ZERO, cfl=0.8, max_step=math.inf, order=3,
            alpha_mode=L.HJ_ALPHA_NODE, kernel=L.HJ_KERNEL_AUTO, tile_override=(0, 0, 0, 0)) -> L.hj_method:
     """An hj_method; kernel and tile_override choose the stage kernel and pin
-    the row kernel's launch shape {ty, tz, occ, merged} (all 0: tuned)."""
+    the row kernel's launch shape {ty, tz, occ, flags} (all 0: tuned; see include/hj.h)."""
     return L.make_method(scheme, dynamics, params, brt, extrap, cfl, max_step, order, alpha_mode, kernel,
                          tile_override)
 

@@ -27,7 +27,7 @@ def oracle_method(scheme=5, dynamics=DI, params=None, brt=1, extrap=0, cfl=0.8, 
 def lib_method(scheme=5, dynamics=DI, params=None, brt=1, extrap=0, cfl=0.8, max_step=math.inf, order=3,
                alpha_global=False, alpha_box=False, kernel=0, tile=(0, 0, 0, 0)):
     """kernel: 0 automatic, 1 the row kernel, 2 the one-node-per-thread
-    kernel; tile: the row kernel's pinned shape (ty, tz, occ, merged)."""
+    kernel; tile: the row kernel's pinned shape (ty, tz, occ, flags)."""
     from paper_2507_11542_gb300 import solver
     return solver.method(scheme=scheme, dynamics=dynamics, params=PARAMS[dynamics] if params is None else params,
                          brt=brt, extrap=extrap, cfl=cfl, max_step=max_step, order=order,

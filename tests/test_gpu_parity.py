@@ -356,8 +356,8 @@ def test_errors_are_reported_not_raised_on_device(ctx):
     assert e.value.status == L.HJ_EINVAL
     # launch choices: an unknown kernel, a malformed or unfitting tile override,
     # the row kernel asked for where it cannot run
-    for kernel, tile in ((3, (0, 0, 0, 0)), (0, (0, 4, 0, 0)), (0, (2, 1, 3, 0)), (2, (2, 1, 1, 0)),
-                         (0, (40, 1, 1, 0))):
+    for kernel, tile in ((3, (0, 0, 0, 0)), (0, (0, 4, 0, 0)), (0, (2, 1, 3, 0)), (0, (2, 1, 1, 4)),
+                         (2, (2, 1, 1, 0)), (0, (40, 1, 1, 0))):
         with pytest.raises(L.HJError) as e:
             solver.term(ctx, spec, lib_method(dynamics=DI, kernel=kernel, tile=tile), to_dev(V0))
         assert e.value.status == L.HJ_EINVAL, (kernel, tile)
@@ -397,17 +397,20 @@ def test_errors_are_reported_not_raised_on_device(ctx):
 # ---------------------------------------------------------------------------
 
 @pytest.mark.parametrize("dyn,shape,cfgs", [
-    # "ty,tz,1,1": blocks of n0*ty threads, whose last node row takes the row ends
-    (AIR3D, (37, 29, 23), ["1,1", "2,5", "4,23", "7,3", "13,8", "1,4,1,1", "2,5,1,1", "13,8,1,1"]),
-    (DUBINS, (13, 11, 9, 7), ["1,1", "3,2", "11,7", "3,2,1,1", "11,7,1,1"]),
-    (DI, (37, 29), ["1,1", "5,1", "13,1", "5,1,1,1"]),
+    # "ty,tz,1,1": blocks of n0*ty threads, whose last node row takes the row ends;
+    # "ty,tz,1,2" / "ty,tz,1,3": tiles away from the edges keep the general body
+    # (the ENO schemes otherwise take a body without ghost logic there)
+    (AIR3D, (37, 29, 23), ["1,1", "2,5", "4,23", "7,3", "13,8", "1,4,1,1", "2,5,1,1", "13,8,1,1", "2,5,1,2",
+                           "2,5,1,3"]),
+    (DUBINS, (13, 11, 9, 7), ["1,1", "3,2", "11,7", "3,2,1,1", "11,7,1,1", "1,1,1,2", "3,2,1,3"]),
+    (DI, (37, 29), ["1,1", "5,1", "13,1", "5,1,1,1", "5,1,1,2"]),
     # rows of 128 threads: 4 node rows leave no room for an extra thread row in FP64 blocks (512), 8 in FP32 (1024)
     (DI, (127, 29), ["1,1", "3,1", "4,1", "7,1", "8,1", "8,1,1,1"]),
 ])
 @pytest.mark.parametrize("dtype", ["float64", "float32"])
 @pytest.mark.parametrize("scheme", [5, 3, 2, 1])
 def test_row_kernel_is_independent_of_tiling(ctx, dyn, shape, cfgs, dtype, scheme):
-    # launch shapes pinned through hj_method.tile_override (ty, tz, occ, merged)
+    # launch shapes pinned through hj_method.tile_override (ty, tz, occ, flags)
     from paper_2507_11542_gb300 import solver
     base = SPECS[dyn]
     spec = W.GridSpec(shape, base.lo, base.hi, base.periodic)
