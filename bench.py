@@ -368,10 +368,11 @@ def bench_rockets(ctx):
     return out
 
 
-def bench_large(ctx, world, flush):
+def bench_large(ctx, world, flush, only=None):
     """The grids far larger than L2: the expanding sphere on 512^3 (FP32) and
     the Dubins car on 81^4 (FP32 and FP64), device-resident RK3 steps. Their
-    HBM fraction counts the algorithmic 8 words per cell-update."""
+    HBM fraction counts the algorithmic 8 words per cell-update. only: the
+    names of the cases to run (None: all, with the initial-surface kernel)."""
     from paper_2507_11542_gb300 import solver, workloads as W
     hbm, _ = measured_hbm_gbs()
     out = {}
@@ -381,8 +382,11 @@ def bench_large(ctx, world, flush):
              ("sphere512_f32_eno2", sphere, solver.method(scheme=2, dynamics=4, params=(1.0,), brt=0), "float32", 10),
              ("dubins81_f32", W.dubins4d(81), solver.method(dynamics=3, params=(1.0, 0.5), brt=1), "float32", 6),
              ("dubins81_f64", W.dubins4d(81), solver.method(dynamics=3, params=(1.0, 0.5), brt=1), "float64", 3)]
-    out["surface512_f32"] = bench_surface(ctx, hbm)
+    if only is None:
+        out["surface512_f32"] = bench_surface(ctx, hbm)
     for name, (spec, V0), m, dtype, K in cases:
+        if only is not None and name not in only:
+            continue
         n = int(np.prod(spec.n))
         r = bench_dtype(ctx, spec, V0, dtype, K, 3, world, flush, m=m)
         rate = world * n / (r["ms_per_step"] / 1e3)
@@ -724,6 +728,9 @@ def main():
                          "(a profiling run: --legs f64, f64,f32, f64,large or f64,batch) prints timings instead of "
                          "the JSON line")
     ap.add_argument("--serve-requests", type=int, default=1000)
+    ap.add_argument("--large-cases", default=None,
+                    help="comma list of the large-grid cases to run in a partial run (default: all), e.g. "
+                         "sphere512_f32,sphere512_f32_eno1,sphere512_f32_eno2,dubins81_f32,dubins81_f64")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -749,7 +756,8 @@ def main():
             if r32:
                 print("f32 leg: %.3f ms per step" % r32["ms_per_step"], flush=True)
             if "large" in legs:
-                print("large grids: %s" % json.dumps(bench_large(ctx, world, flush)), flush=True)
+                only = set(args.large_cases.split(",")) if args.large_cases else None
+                print("large grids: %s" % json.dumps(bench_large(ctx, world, flush, only)), flush=True)
             if "batch" in legs:
                 print("batched: %s" % json.dumps(bench_batch(ctx, rank=rank, world=world)), flush=True)
             if "serve" in legs:
