@@ -334,9 +334,6 @@ __device__ __forceinline__ void box_alpha(const StageParams& P, const T* xc, T c
 
 // ydot from node coordinates xc, cos/sin (c, s) of the dimension-2
 // coordinate (dynamics with uses_angle), the mean derivatives
-// pb = (p- + p+)/2 and the half differences dd = (p+ - p-)/2.
-// ydot from node coordinates xc, cos/sin (c, s) of the dimension-2
-// coordinate (dynamics with uses_angle), the mean derivatives
 // pb = (p- + p+)/2 and the half differences dd = (p+ - p-)/2:
 // Hg(x, pb) + sum_d alpha_d dd_d, with alpha_d = alpha_d(x) (the maximum of
 // |f_d| over the controls at the node) or, for global LF, the launch's
