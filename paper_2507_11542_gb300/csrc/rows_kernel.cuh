@@ -227,7 +227,12 @@ __device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T
     const int s_pyw = o_pyp + gk * nx + x;       // p+ of tile row gk - 1 (written)
     const int s_pyr = o_pyp + (r + 1) * nx + x;  // p+ of tile row r (read)
 
-    const T h0 = SP<T>::half_inv_dx(P, 0), h1 = SP<T>::half_inv_dx(P, 1), hS = SP<T>::half_inv_dx(P, SD);
+    // 1/(2 dx), or 1/(12 dx) where the interface evaluation returns six times the derivatives
+    const auto half_inv = [&P](int d) -> T {
+        if constexpr (iface_times6<T, SCHEME>()) return P.half_inv_dx6[d];
+        else return SP<T>::half_inv_dx(P, d);
+    };
+    const T h0 = half_inv(0), h1 = half_inv(1), hS = half_inv(SD);
     const T dt = R.dt, cv = R.cv, cu = R.cu;
     const bool minv = R.minv;
     // BRT min(0, .) as a clamp (+inf: none), global dissipation as a flag, both read once
@@ -463,7 +468,7 @@ __device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T
                 iface_at<SCHEME>(v[1], v[2], v[3], v[4], v[5], v[6], fl2, pp2, unused1);
                 sm[2] = pm2 + pp2;
                 df[2] = pp2 - pm2;
-                hh[2] = SP<T>::half_inv_dx(P, 2);
+                hh[2] = half_inv(2);
                 if constexpr (uses_coord<D, DYN>(3)) xc[3] = coord(SP<T>::lo(P, 3), z, SP<T>::dx(P, 3));
             }
             if constexpr (D == 3 && uses_coord<D, DYN>(2)) xc[2] = coord(SP<T>::lo(P, 2), z, SP<T>::dx(P, 2));

@@ -18,13 +18,15 @@
 // Evaluated here in an equivalent form (the weights sum to one):
 //   p- = phi2 + (w1 T1/3 + w3 T2/6),   p+ = psi2 - (w1' T2/3 + w3' T1/6)
 // with the third differences T1 = e1-3e2+3e3-e4 = tA-tB and T2 = e2-3e3+3e4-e5
-// = tB-tC shared by both sides, and the smoothness indicators scaled by 12/13
-// (S~ = t^2 + 3/13 u^2, eps scaled alike), which leaves every weight unchanged.
-// All differences and both results are raw (not divided by dx): the caller
-// scales them once per node and dimension.
+// = tB-tC shared by both sides. The smoothness indicators are scaled by a
+// constant (FP32: 12/13, S~ = t^2 + 3/13 u^2; FP64: 4, below), eps alike,
+// which leaves every weight unchanged. All differences and both results are
+// raw (not divided by dx): the caller scales them once per node and dimension.
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include <type_traits>
 
 #include "../../include/hj.h"
 
@@ -92,60 +94,82 @@ __device__ __forceinline__ double rcp_newton(double x) {
     return fma(r, e, r);
 }
 
-// FP64. Weights normalised by products of the d_k = (S~_k + eps~)^2:
+// FP64. Weights normalised by products of the d_k = (S'_k + eps')^2:
 //   w_k = c_k prod_{i!=k} d_i / sum_m c_m prod_{i!=m} d_i,
-// and both sides share one reciprocal 1/(denL denR). When that product
-// leaves [1e-290, 1e290] (nearly flat or huge data) each side divides alone,
-// and an exactly flat window (den = 0) returns its central candidate.
+// and both sides share one reciprocal 1/(DL DR). Three rescalings that leave
+// every weight unchanged save FP64 operations (the FP64 pipe bounds this
+// kernel):
+//   * the smoothness indicators and epsilon times 4: S' = 13/3 t^2 + u^2,
+//     eps' = 4e-6 max(e_k^2) + 4 floor;
+//   * the ideal weights times 10: DL = PA + 6 PB + 3 PC, DR = 3 PA + 6 PB + PC;
+//   * both results times 6: 6 p- = (-e2 + 5e3 + 2e4) + (2X + 3Y)/DL and
+//     6 p+ = 6 phi2 + 3 (e2 - e4) - (3X + 2Y)/DR, X = PA T1, Y = PC T2
+//     (2X + 3Y = 2(X+Y) + Y, 3X + 2Y = 2(X+Y) + X).
+// The caller divides the factor 6 out with its 1/(2 dx) (iface_times6).
 // The core takes tA, tB, tC (the second differences of the windows' first
-// differences) and their squares, which consecutive interfaces along a line
-// share (Weno5Line).
+// differences) and q = 13/3 t^2 for each, which consecutive interfaces along
+// a line share (Weno5Line).
 __device__ __forceinline__ void weno_core(double e1, double e2, double e3, double e4, double e5, double tA, double tB,
-                                          double tC, double sqA, double sqB, double sqC, double floor_raw,
+                                          double tC, double qA, double qB, double qC, double floor_raw,
                                           double& pp_j, double& pm_j1) {
-    const double k = 3.0 / 13.0;
     const double uA = fma(2.0, e3 - e2, tA);
     const double uB = e2 - e4;
     const double uC = fma(2.0, e3 - e4, tC);
-    const double SA = fma(k * uA, uA, sqA);
-    const double SB = fma(k * uB, uB, sqB);
-    const double SC = fma(k * uC, uC, sqC);
+    const double SA = fma(uA, uA, qA);
+    const double SB = fma(uB, uB, qB);
+    const double SC = fma(uC, uC, qC);
     const double amax = nonneg_max(nonneg_max(nonneg_max(abs_bits(e1), abs_bits(e2)),
                                               nonneg_max(abs_bits(e3), abs_bits(e4))), abs_bits(e5));
-    const double eps = fma((12.0 / 13.0) * 1e-6, amax * amax, (12.0 / 13.0) * floor_raw);
-    const double sA = SA + eps, sB = SB + eps, sC = SC + eps;
+    const double eps = fma(4e-6, amax * amax, 4.0 * floor_raw);
+    // sA, sB, sC scaled by the power of two that brings the largest into
+    // [1, 2): an exact integer subtraction on the bit patterns of these
+    // positive normal numbers. eps bounds their ratios (s_min >= 3e-8 s_max:
+    // S' <= 133.4 max(e_k^2)), so DL and DR stay within [9e-16, 160] and one
+    // shared reciprocal serves every window, flat and tiny ones included.
+    // The weights do not change.
+    const long long bA = __double_as_longlong(SA + eps), bB = __double_as_longlong(SB + eps),
+                    bC = __double_as_longlong(SC + eps);
+    const long long bm = bA > bB ? (bA > bC ? bA : bC) : (bB > bC ? bB : bC);
+    const long long shift = (bm & 0x7ff0000000000000LL) - 0x3ff0000000000000LL;
+    const double sA = __longlong_as_double(bA - shift), sB = __longlong_as_double(bB - shift),
+                 sC = __longlong_as_double(bC - shift);
     const double dA = sA * sA, dB = sB * sB, dC = sC * sC;
     const double PA = dB * dC, PB = dA * dC, PC = dA * dB;
     const double T1 = tA - tB, T2 = tB - tC;
     const double X = PA * T1, Y = PC * T2;
-    const double b6 = 0.6 * PB;
-    const double denL = fma(0.1, PA, fma(0.3, PC, b6));
-    const double denR = fma(0.3, PA, fma(0.1, PC, b6));
-    const double numL = fma(1.0 / 30.0, X, 0.05 * Y);
-    const double numR = fma(0.05, X, (1.0 / 30.0) * Y);
-    const double c5 = (5.0 / 6.0) * e3;
-    const double phi2 = fma(1.0 / 3.0, e4, fma(-1.0 / 6.0, e2, c5));
-    const double psi2 = fma(0.5, uB, phi2);  // psi2 - phi2 = (e2 - e4) / 2
-    const double den2 = denL * denR;
-    const long long bits = __double_as_longlong(den2);
-    const int expo = (int)((bits >> 52) & 0x7ff);  // 1e-290 < den2 < 1e290 (integer test)
-    if (expo > 60 && expo < 1986) {
-        const double r = rcp_newton(den2);
-        pm_j1 = fma(numL * denR, r, phi2);
-        pp_j = fma(-numR * denL, r, psi2);
-    } else {
-        pm_j1 = denL > 0.0 ? phi2 + numL / denL : phi2;
-        pp_j = denR > 0.0 ? psi2 - numR / denR : psi2;
-    }
+    // no a*b + c is left for the compiler to contract: every inlined copy of
+    // this function rounds alike, so results do not depend on which thread
+    // role evaluates an interface
+    const double XY = __dadd_rn(X, Y);
+    const double numL = fma(2.0, XY, Y);  // 2X + 3Y
+    const double numR = fma(2.0, XY, X);  // 3X + 2Y
+    const double DL = fma(3.0, PC, fma(6.0, PB, PA));
+    const double DR = fma(3.0, PA, fma(6.0, PB, PC));
+    const double phi6 = fma(5.0, e3, fma(2.0, e4, -e2));  // 6 phi2
+    const double psi6 = fma(3.0, uB, phi6);               // 6 psi2
+    const double r = rcp_newton(DL * DR);
+    pm_j1 = fma(numL * DR, r, phi6);
+    pp_j = fma(-numR * DL, r, psi6);
 }
 
 // a - 2b + c for three consecutive first differences (raw units).
 __device__ __forceinline__ double curv(double a, double b, double c) { return fma(-2.0, b, a) + c; }
+// 13/3 t^2, the share of t in the rescaled smoothness indicator
+__device__ __forceinline__ double curv_sq(double t) { return (13.0 / 3.0 * t) * t; }
 
+// Six times the FP64 one-sided derivatives (weno_core).
 __device__ __forceinline__ void weno_iface(double e1, double e2, double e3, double e4, double e5, double floor_raw,
                                            double& pp_j, double& pm_j1) {
     const double tA = curv(e1, e2, e3), tB = curv(e2, e3, e4), tC = curv(e3, e4, e5);
-    weno_core(e1, e2, e3, e4, e5, tA, tB, tC, tA * tA, tB * tB, tC * tC, floor_raw, pp_j, pm_j1);
+    weno_core(e1, e2, e3, e4, e5, tA, tB, tC, curv_sq(tA), curv_sq(tB), curv_sq(tC), floor_raw, pp_j, pm_j1);
+}
+
+// The factor the caller applies, with 1/(2 dx), to an interface result: the
+// FP64 WENO5 evaluation returns six times the derivatives, every other
+// evaluation the derivatives themselves.
+template <typename T, int SCHEME>
+__host__ __device__ constexpr bool iface_times6() {
+    return std::is_same<T, double>::value && SCHEME == HJ_WENO5;
 }
 
 // FP64 WENO5 along a grid line, one interface after the other: the interface
@@ -156,20 +180,20 @@ __device__ __forceinline__ void weno_iface(double e1, double e2, double e3, doub
 struct Weno5Line {
     double e[5];   // first differences of the current window
     double t[3];   // tA, tB, tC
-    double sq[3];  // their squares
+    double sq[3];  // 13/3 of their squares
     // the window of the values v0..v5 at nodes j-2 .. j+3
     __device__ __forceinline__ void start(double v0, double v1, double v2, double v3, double v4, double v5) {
         e[0] = v1 - v0; e[1] = v2 - v1; e[2] = v3 - v2; e[3] = v4 - v3; e[4] = v5 - v4;
         t[0] = curv(e[0], e[1], e[2]);
         t[1] = curv(e[1], e[2], e[3]);
         t[2] = curv(e[2], e[3], e[4]);
-        sq[0] = t[0] * t[0]; sq[1] = t[1] * t[1]; sq[2] = t[2] * t[2];
+        sq[0] = curv_sq(t[0]); sq[1] = curv_sq(t[1]); sq[2] = curv_sq(t[2]);
     }
     // slide by one node: v4, v5 are the values at the new window's last two nodes
     __device__ __forceinline__ void slide(double v4, double v5) {
         e[0] = e[1]; e[1] = e[2]; e[2] = e[3]; e[3] = e[4]; e[4] = v5 - v4;
         t[0] = t[1]; t[1] = t[2]; t[2] = curv(e[2], e[3], e[4]);
-        sq[0] = sq[1]; sq[1] = sq[2]; sq[2] = t[2] * t[2];
+        sq[0] = sq[1]; sq[1] = sq[2]; sq[2] = curv_sq(t[2]);
     }
     __device__ __forceinline__ void eval(double floor_raw, double& pp_j, double& pm_j1) const {
         weno_core(e[0], e[1], e[2], e[3], e[4], t[0], t[1], t[2], sq[0], sq[1], sq[2], floor_raw, pp_j, pm_j1);
