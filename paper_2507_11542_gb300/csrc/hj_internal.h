@@ -83,12 +83,13 @@ struct StageParams {
     const float* trig_f;
     double weno_floor[kMaxDim];   // additive floor of the WENO5 epsilon per dimension, in raw-difference units
     double half_inv_dx[kMaxDim];  // 1 / (2 dx): raw differences to (p- + p+)/2 and (p+ - p-)/2
-    double half_inv_dx6[kMaxDim]; // 1 / (12 dx): the same from six times the raw differences (FP64 WENO5)
+    double half_inv_dx6[kMaxDim]; // 1 / (12 dx): the same from six times the raw differences (WENO5)
     int alpha_global;             // dissipation alpha_d = alpha_g[d] (global LF) instead of alpha_d(x)
     double alpha_g[kMaxDim];
     int alpha_box;                // dissipation alpha_d = max |dHg/dp_d| over the node's box of gradients
     // FP32 copies of the scalars above, so that FP32 kernels do no FP64 arithmetic
-    float lo_f[kMaxDim], dx_f[kMaxDim], inv_dx_f[kMaxDim], half_inv_dx_f[kMaxDim], alpha_g_f[kMaxDim];
+    float lo_f[kMaxDim], dx_f[kMaxDim], inv_dx_f[kMaxDim], half_inv_dx_f[kMaxDim], half_inv_dx6_f[kMaxDim];
+    float alpha_g_f[kMaxDim];
     float weno_floor_f[kMaxDim];
     float params_f[8];
     float dt_f, cv_f, cu_f;
@@ -107,6 +108,7 @@ inline StageParams finalize(StageParams p) {
         p.inv_dx_f[d] = (float)p.g.inv_dx[d];
         p.half_inv_dx[d] = 0.5 * p.g.inv_dx[d];
         p.half_inv_dx6[d] = p.half_inv_dx[d] / 6.0;
+        p.half_inv_dx6_f[d] = (float)p.half_inv_dx6[d];
         p.half_inv_dx_f[d] = (float)p.half_inv_dx[d];
         p.alpha_g_f[d] = (float)p.alpha_g[d];
         p.weno_floor_f[d] = (float)p.weno_floor[d];

@@ -229,7 +229,7 @@ __device__ __forceinline__ void rows_tile(const StageParams& P, const StageRun<T
 
     // 1/(2 dx), or 1/(12 dx) where the interface evaluation returns six times the derivatives
     const auto half_inv = [&P](int d) -> T {
-        if constexpr (iface_times6<T, SCHEME>()) return P.half_inv_dx6[d];
+        if constexpr (iface_times6<T, SCHEME>()) return SP<T>::half_inv_dx6(P, d);
         else return SP<T>::half_inv_dx(P, d);
     };
     const T h0 = half_inv(0), h1 = half_inv(1), hS = half_inv(SD);

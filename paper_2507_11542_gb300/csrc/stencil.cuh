@@ -222,6 +222,7 @@ template <> struct SP<double> {
     static __device__ __forceinline__ double dx(const StageParams& P, int d) { return P.g.dx[d]; }
     static __device__ __forceinline__ double inv_dx(const StageParams& P, int d) { return P.g.inv_dx[d]; }
     static __device__ __forceinline__ double half_inv_dx(const StageParams& P, int d) { return P.half_inv_dx[d]; }
+    static __device__ __forceinline__ double half_inv_dx6(const StageParams& P, int d) { return P.half_inv_dx6[d]; }
     static __device__ __forceinline__ double alpha_g(const StageParams& P, int d) { return P.alpha_g[d]; }
     static __device__ __forceinline__ double param(const StageParams& P, int k) { return P.params[k]; }
     static __device__ __forceinline__ double dt(const StageParams& P) { return P.dt; }
@@ -234,6 +235,7 @@ template <> struct SP<float> {
     static __device__ __forceinline__ float dx(const StageParams& P, int d) { return P.dx_f[d]; }
     static __device__ __forceinline__ float inv_dx(const StageParams& P, int d) { return P.inv_dx_f[d]; }
     static __device__ __forceinline__ float half_inv_dx(const StageParams& P, int d) { return P.half_inv_dx_f[d]; }
+    static __device__ __forceinline__ float half_inv_dx6(const StageParams& P, int d) { return P.half_inv_dx6_f[d]; }
     static __device__ __forceinline__ float alpha_g(const StageParams& P, int d) { return P.alpha_g_f[d]; }
     static __device__ __forceinline__ float param(const StageParams& P, int k) { return P.params_f[k]; }
     static __device__ __forceinline__ float dt(const StageParams& P) { return P.dt_f; }

@@ -18,10 +18,10 @@
 // Evaluated here in an equivalent form (the weights sum to one):
 //   p- = phi2 + (w1 T1/3 + w3 T2/6),   p+ = psi2 - (w1' T2/3 + w3' T1/6)
 // with the third differences T1 = e1-3e2+3e3-e4 = tA-tB and T2 = e2-3e3+3e4-e5
-// = tB-tC shared by both sides. The smoothness indicators are scaled by a
-// constant (FP32: 12/13, S~ = t^2 + 3/13 u^2; FP64: 4, below), eps alike,
-// which leaves every weight unchanged. All differences and both results are
-// raw (not divided by dx): the caller scales them once per node and dimension.
+// = tB-tC shared by both sides. The smoothness indicators are scaled by 4
+// (S' = 13/3 t^2 + u^2), eps alike, which leaves every weight unchanged. All
+// differences and both results are raw (not divided by dx): the caller scales
+// them once per node and dimension.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -38,38 +38,40 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return r;
 }
 
-// FP32. (S~ + eps~)^2 >= (12/13 * 1e-18)^2 stays a normal number, so the
-// approximate reciprocals neither overflow nor divide by zero.
+// FP32, in the rescaled form of the FP64 interface below (smoothness values
+// and epsilon times 4, ideal weights times 10, results times 6; the caller
+// divides the 6 out with 1/(2 dx)), with one reciprocal per weight and per
+// side: (S' + eps')^2 >= (4e-18)^2 stays a normal number, so the approximate
+// reciprocals neither overflow nor divide by zero. No a*b + c is left for the
+// compiler to contract, so every inlined copy rounds alike.
 __device__ __forceinline__ void weno_iface(float e1, float e2, float e3, float e4, float e5, float floor_raw,
                                            float& pp_j, float& pm_j1) {
-    const float k = 3.0f / 13.0f;
     const float tA = fmaf(-2.0f, e2, e1) + e3;
     const float tB = fmaf(-2.0f, e3, e2) + e4;
     const float tC = fmaf(-2.0f, e4, e3) + e5;
     const float uA = fmaf(2.0f, e3 - e2, tA);  // e1 - 4e2 + 3e3
     const float uB = e2 - e4;
     const float uC = fmaf(2.0f, e3 - e4, tC);  // 3e3 - 4e4 + e5
-    const float SA = fmaf(tA, tA, uA * (k * uA));
-    const float SB = fmaf(tB, tB, uB * (k * uB));
-    const float SC = fmaf(tC, tC, uC * (k * uC));
+    const float SA = fmaf(uA, uA, (13.0f / 3.0f * tA) * tA);
+    const float SB = fmaf(uB, uB, (13.0f / 3.0f * tB) * tB);
+    const float SC = fmaf(uC, uC, (13.0f / 3.0f * tC) * tC);
     const float amax = fmaxf(fmaxf(fmaxf(fabsf(e1), fabsf(e2)), fmaxf(fabsf(e3), fabsf(e4))), fabsf(e5));
-    const float eps = fmaf((12.0f / 13.0f) * 1e-6f, amax * amax, (12.0f / 13.0f) * floor_raw);
+    const float eps = fmaf(4e-6f, amax * amax, 4.0f * floor_raw);
     const float sA = SA + eps, sB = SB + eps, sC = SC + eps;
     const float rA = rcp_approx(sA * sA);
     const float rB = rcp_approx(sB * sB);
     const float rC = rcp_approx(sC * sC);
     const float T1 = tA - tB, T2 = tB - tC;
     const float X = rA * T1, Y = rC * T2;
-    const float b6 = 0.6f * rB;
-    const float denL = fmaf(0.1f, rA, fmaf(0.3f, rC, b6));
-    const float denR = fmaf(0.3f, rA, fmaf(0.1f, rC, b6));
-    const float numL = fmaf(1.0f / 30.0f, X, 0.05f * Y);
-    const float numR = fmaf(0.05f, X, (1.0f / 30.0f) * Y);
-    const float c5 = (5.0f / 6.0f) * e3;
-    const float phi2 = fmaf(1.0f / 3.0f, e4, fmaf(-1.0f / 6.0f, e2, c5));
-    const float psi2 = fmaf(0.5f, uB, phi2);  // psi2 - phi2 = (e2 - e4) / 2
-    pm_j1 = fmaf(numL, rcp_approx(denL), phi2);
-    pp_j = fmaf(-numR, rcp_approx(denR), psi2);
+    const float XY = __fadd_rn(X, Y);
+    const float numL = fmaf(2.0f, XY, Y);  // 2X + 3Y
+    const float numR = fmaf(2.0f, XY, X);  // 3X + 2Y
+    const float DL = fmaf(3.0f, rC, fmaf(6.0f, rB, rA));
+    const float DR = fmaf(3.0f, rA, fmaf(6.0f, rB, rC));
+    const float phi6 = fmaf(5.0f, e3, fmaf(2.0f, e4, -e2));  // 6 phi2
+    const float psi6 = fmaf(3.0f, uB, phi6);                 // 6 psi2
+    pm_j1 = fmaf(numL, rcp_approx(DL), phi6);
+    pp_j = fmaf(-numR, rcp_approx(DR), psi6);
 }
 
 // Integer maximum of non-negative doubles (their bit patterns order alike):
@@ -164,12 +166,12 @@ __device__ __forceinline__ void weno_iface(double e1, double e2, double e3, doub
     weno_core(e1, e2, e3, e4, e5, tA, tB, tC, curv_sq(tA), curv_sq(tB), curv_sq(tC), floor_raw, pp_j, pm_j1);
 }
 
-// The factor the caller applies, with 1/(2 dx), to an interface result: the
-// FP64 WENO5 evaluation returns six times the derivatives, every other
-// evaluation the derivatives themselves.
+// Whether an interface evaluation returns six times the derivatives (WENO5,
+// both precisions; the caller scales by 1/(12 dx) instead of 1/(2 dx)) or the
+// derivatives themselves (the ENO schemes).
 template <typename T, int SCHEME>
 __host__ __device__ constexpr bool iface_times6() {
-    return std::is_same<T, double>::value && SCHEME == HJ_WENO5;
+    return SCHEME == HJ_WENO5;
 }
 
 // FP64 WENO5 along a grid line, one interface after the other: the interface

@@ -90,6 +90,35 @@ def test_term_parity_fp64(ctx, dyn, scheme, brt):
     assert rel_err(to_host(y, spec.n), y_o) <= TOL64
 
 
+@pytest.mark.parametrize("dyn", [DI, AIR3D, DUBINS])
+@pytest.mark.parametrize("case", ["tiny", "huge", "plateaus", "flat_streamed"])
+def test_weno5_fp64_extreme_and_flat_windows(ctx, dyn, case):
+    # The FP64 interface scales its three smoothness sums by a power of two and
+    # forms its weights as products of fourth powers: data of magnitude 1e-30
+    # and 1e+30, exactly flat windows next to jumps, and a field constant along
+    # the streamed dimension but for a few 1e-20 bumps all take the one path and
+    # stay within the parity bar of the oracle's textbook weights.
+    from paper_2507_11542_gb300 import solver
+    spec = SPECS[dyn]
+    V = _field(spec, 40 + dyn)
+    if case == "tiny":
+        V = V * 1e-30
+    elif case == "huge":
+        V = V * 1e30
+    elif case == "plateaus":
+        V = np.maximum(V, np.median(V)) + (V > np.quantile(V, 0.8)) * 0.5   # flat regions and a jump
+    else:
+        base = V.take([0], axis=spec.ndim - 1)
+        V = np.repeat(base, spec.n[-1], axis=spec.ndim - 1)
+        bumps = np.zeros_like(V)
+        bumps.flat[::97] = 1e-20
+        V = V + bumps
+    V = np.asfortranarray(V)
+    y_o = O.term(spec, oracle_method(scheme=5, dynamics=dyn, brt=0), V)
+    y = solver.term(ctx, spec, lib_method(scheme=5, dynamics=dyn, brt=0), to_dev(V))
+    assert rel_err(to_host(y, spec.n), y_o) <= TOL64
+
+
 @pytest.mark.parametrize("dyn", [DI, AIR3D, DUBINS, NORM, ADVECT, ROTATE, ROCKETS])
 def test_step_bound_is_bit_exact(ctx, dyn):
     from paper_2507_11542_gb300 import solver
