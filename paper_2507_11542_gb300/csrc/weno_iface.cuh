@@ -108,15 +108,16 @@ __device__ __forceinline__ double rcp_newton(double x) {
 //     6 p+ = 6 phi2 + 3 (e2 - e4) - (3X + 2Y)/DR, X = PA T1, Y = PC T2
 //     (2X + 3Y = 2(X+Y) + Y, 3X + 2Y = 2(X+Y) + X).
 // The caller divides the factor 6 out with its 1/(2 dx) (iface_times6).
-// The core takes tA, tB, tC (the second differences of the windows' first
-// differences) and q = 13/3 t^2 for each, which consecutive interfaces along
-// a line share (Weno5Line).
+// The core takes what consecutive interfaces along a line share (Weno5Line):
+// tA, tB, tC (the second differences of the windows' first differences), q =
+// 13/3 t^2 for each, the differences d23 = e3 - e2 and d34 = e4 - e3 of the
+// first differences, and the third differences T1 = tA - tB, T2 = tB - tC.
 __device__ __forceinline__ void weno_core(double e1, double e2, double e3, double e4, double e5, double tA, double tB,
-                                          double tC, double qA, double qB, double qC, double floor_raw,
-                                          double& pp_j, double& pm_j1) {
-    const double uA = fma(2.0, e3 - e2, tA);
+                                          double tC, double qA, double qB, double qC, double d23, double d34,
+                                          double T1, double T2, double floor_raw, double& pp_j, double& pm_j1) {
+    const double uA = fma(2.0, d23, tA);   // e1 - 4e2 + 3e3
     const double uB = e2 - e4;
-    const double uC = fma(2.0, e3 - e4, tC);
+    const double uC = fma(-2.0, d34, tC);  // 3e3 - 4e4 + e5
     const double SA = fma(uA, uA, qA);
     const double SB = fma(uB, uB, qB);
     const double SC = fma(uC, uC, qC);
@@ -137,7 +138,6 @@ __device__ __forceinline__ void weno_core(double e1, double e2, double e3, doubl
                  sC = __longlong_as_double(bC - shift);
     const double dA = sA * sA, dB = sB * sB, dC = sC * sC;
     const double PA = dB * dC, PB = dA * dC, PC = dA * dB;
-    const double T1 = tA - tB, T2 = tB - tC;
     const double X = PA * T1, Y = PC * T2;
     // no a*b + c is left for the compiler to contract: every inlined copy of
     // this function rounds alike, so results do not depend on which thread
@@ -154,16 +154,17 @@ __device__ __forceinline__ void weno_core(double e1, double e2, double e3, doubl
     pp_j = fma(-numR * DL, r, psi6);
 }
 
-// a - 2b + c for three consecutive first differences (raw units).
-__device__ __forceinline__ double curv(double a, double b, double c) { return fma(-2.0, b, a) + c; }
 // 13/3 t^2, the share of t in the rescaled smoothness indicator
 __device__ __forceinline__ double curv_sq(double t) { return (13.0 / 3.0 * t) * t; }
 
-// Six times the FP64 one-sided derivatives (weno_core).
+// Six times the FP64 one-sided derivatives (weno_core), from the five first
+// differences: t as differences of the d = e_{k+1} - e_k.
 __device__ __forceinline__ void weno_iface(double e1, double e2, double e3, double e4, double e5, double floor_raw,
                                            double& pp_j, double& pm_j1) {
-    const double tA = curv(e1, e2, e3), tB = curv(e2, e3, e4), tC = curv(e3, e4, e5);
-    weno_core(e1, e2, e3, e4, e5, tA, tB, tC, curv_sq(tA), curv_sq(tB), curv_sq(tC), floor_raw, pp_j, pm_j1);
+    const double d12 = e2 - e1, d23 = e3 - e2, d34 = e4 - e3, d45 = e5 - e4;
+    const double tA = d23 - d12, tB = d34 - d23, tC = d45 - d34;
+    weno_core(e1, e2, e3, e4, e5, tA, tB, tC, curv_sq(tA), curv_sq(tB), curv_sq(tC), d23, d34, tA - tB, tB - tC,
+              floor_raw, pp_j, pm_j1);
 }
 
 // Whether an interface evaluation returns six times the derivatives (WENO5,
@@ -176,29 +177,36 @@ __host__ __device__ constexpr bool iface_times6() {
 
 // FP64 WENO5 along a grid line, one interface after the other: the interface
 // between nodes j and j+1 reuses four of the five first differences, two of
-// the three values tA, tB, tC and their squares of the interface before it,
+// the three differences d, two of the three values tA, tB, tC and their
+// squares, and one of the two third differences of the interface before it,
 // so each step computes one of each. The results are those of weno_iface,
 // bit for bit (the same operations on the same operands).
 struct Weno5Line {
     double e[5];   // first differences of the current window
+    double d[3];   // d23, d34, d45: differences of consecutive e
     double t[3];   // tA, tB, tC
     double sq[3];  // 13/3 of their squares
+    double T[2];   // T1, T2
     // the window of the values v0..v5 at nodes j-2 .. j+3
     __device__ __forceinline__ void start(double v0, double v1, double v2, double v3, double v4, double v5) {
         e[0] = v1 - v0; e[1] = v2 - v1; e[2] = v3 - v2; e[3] = v4 - v3; e[4] = v5 - v4;
-        t[0] = curv(e[0], e[1], e[2]);
-        t[1] = curv(e[1], e[2], e[3]);
-        t[2] = curv(e[2], e[3], e[4]);
+        const double d12 = e[1] - e[0];
+        d[0] = e[2] - e[1]; d[1] = e[3] - e[2]; d[2] = e[4] - e[3];
+        t[0] = d[0] - d12; t[1] = d[1] - d[0]; t[2] = d[2] - d[1];
         sq[0] = curv_sq(t[0]); sq[1] = curv_sq(t[1]); sq[2] = curv_sq(t[2]);
+        T[0] = t[0] - t[1]; T[1] = t[1] - t[2];
     }
     // slide by one node: v4, v5 are the values at the new window's last two nodes
     __device__ __forceinline__ void slide(double v4, double v5) {
         e[0] = e[1]; e[1] = e[2]; e[2] = e[3]; e[3] = e[4]; e[4] = v5 - v4;
-        t[0] = t[1]; t[1] = t[2]; t[2] = curv(e[2], e[3], e[4]);
+        d[0] = d[1]; d[1] = d[2]; d[2] = e[4] - e[3];
+        t[0] = t[1]; t[1] = t[2]; t[2] = d[2] - d[1];
         sq[0] = sq[1]; sq[1] = sq[2]; sq[2] = curv_sq(t[2]);
+        T[0] = T[1]; T[1] = t[1] - t[2];
     }
     __device__ __forceinline__ void eval(double floor_raw, double& pp_j, double& pm_j1) const {
-        weno_core(e[0], e[1], e[2], e[3], e[4], t[0], t[1], t[2], sq[0], sq[1], sq[2], floor_raw, pp_j, pm_j1);
+        weno_core(e[0], e[1], e[2], e[3], e[4], t[0], t[1], t[2], sq[0], sq[1], sq[2], d[0], d[1], T[0], T[1],
+                  floor_raw, pp_j, pm_j1);
     }
 };
 
