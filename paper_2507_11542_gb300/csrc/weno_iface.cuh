@@ -19,9 +19,10 @@
 //   p- = phi2 + (w1 T1/3 + w3 T2/6),   p+ = psi2 - (w1' T2/3 + w3' T1/6)
 // with the third differences T1 = e1-3e2+3e3-e4 = tA-tB and T2 = e2-3e3+3e4-e5
 // = tB-tC shared by both sides. The smoothness indicators are scaled by 4
-// (S' = 13/3 t^2 + u^2), eps alike, which leaves every weight unchanged. All
-// differences and both results are raw (not divided by dx): the caller scales
-// them once per node and dimension.
+// (S' = 13/3 t^2 + u^2), eps alike, and the ideal weights by 10, which leaves
+// every weight unchanged; both results come out times 6. All differences and
+// both results are raw (not divided by dx): the caller scales them once per
+// node and dimension, by 1/(12 dx) (iface_times6).
 #pragma once
 
 #include <cuda_runtime.h>
