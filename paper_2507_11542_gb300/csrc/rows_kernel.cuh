@@ -523,7 +523,7 @@ __global__ void __launch_bounds__(RowsBounds<T, OCC>::kThreads, OCC) rows_kernel
     const int chunk = (D == 3) ? (int)blockIdx.y : ((D == 4) ? (int)blockIdx.z : 0);
     // the interior body is compiled for the ENO schemes only: there it pays
     // (their per-node arithmetic is small beside the staging logic), while a
-    // second WENO5 body measured slower on every grid
+    // second WENO5 body measured slower in FP32 and no faster in FP64
     if constexpr (SCHEME != HJ_WENO5) {
         if (C.split && rows_interior<D>(P.g, C.ty, C.tz, blockIdx.x, chunk)) {
             rows_tile<T, D, DYN, SCHEME, KIND, true>(P, R, C.ty, C.nt, C.tz, blockIdx.x, i2, chunk, threadIdx.x,
